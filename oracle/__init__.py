@@ -1,0 +1,294 @@
+"""Plain double-precision CPU oracle for the MD hot path (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never calls it and
+shares no code with it.  The arithmetic lives in ``md_oracle.c`` (plain C,
+fp64, ``-ffp-contract=off``); this module only compiles it with gcc and
+marshals numpy arrays through ctypes.
+
+Functions and the passages of Mangiardi & Meyer they follow:
+
+* ``cell_grid``, ``bin_cells``   -- cell decomposition (Sec. 2.1)
+* ``neighbors_brute``, ``neighbors_cells`` -- Verlet lists with r_list =
+  r_c + skin (Sec. 2.1, Sec. 3.3)
+* ``lj_brute``, ``lj_list``      -- pair forces F = -(1/d) dPhi/dr R (Sec. 2.2)
+* ``sc_brute``, ``sc_list``      -- many-body energy Eq. 1-2 evaluated in three
+  steps (Sec. 3.1)
+* ``md_run``, ``forces_once``    -- velocity-Verlet with the half-skin rebuild
+  rule (Sec. 3.3)
+* ``mlp_forward``, ``mlp_loss_grad``, ``adam``, ``partition`` -- the per-cell
+  cost model and equal-cost partition (not in the paper; they address its
+  load-balance problem of inhomogeneous systems, Sec. 1 and Sec. 2.1)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "md_oracle.c")
+_LIB = os.path.join(_HERE, "_liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+POT_LJ = 0
+POT_SC = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile md_oracle.c with gcc (OpenMP, no fused multiply-add)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [("potential", C.c_int32), ("rebuild_every", C.c_int32),
+                ("eps", C.c_double), ("sigma", C.c_double), ("c", C.c_double),
+                ("n_exp", C.c_double), ("m_exp", C.c_double), ("rc", C.c_double),
+                ("skin", C.c_double), ("dt", C.c_double), ("mass", C.c_double)]
+
+
+def make_params(potential=POT_LJ, eps=1.0, sigma=1.0, c=0.0, n_exp=12.0, m_exp=6.0,
+                rc=2.5, skin=0.3, dt=0.005, mass=1.0, rebuild_every=0) -> Params:
+    return Params(potential, rebuild_every, eps, sigma, c, n_exp, m_exp, rc, skin, dt, mass)
+
+
+def _P(a, dtype):
+    return a.ctypes.data_as(C.POINTER(dtype))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            L = _lib
+            d, i64, i32 = C.c_double, C.c_int64, C.c_int32
+            pd, pi64, pi32 = C.POINTER(d), C.POINTER(i64), C.POINTER(i32)
+            L.orc_pair_r2.restype = d
+            L.orc_pair_r2.argtypes = [pd, pd, i64, i64]
+            L.orc_cell_grid.restype = C.c_int
+            L.orc_cell_grid.argtypes = [pd, d, pi32, pd]
+            L.orc_bin.restype = C.c_int
+            L.orc_bin.argtypes = [i64, pd, pi32, pd, pi32, pi64, pi64]
+            for fn in (L.orc_neighbors_brute, L.orc_neighbors_cells):
+                fn.restype = i64
+                fn.argtypes = [i64, pd, pd, d, C.c_int, pi64, pi32, i64]
+            L.orc_lj_brute.restype = d
+            L.orc_lj_brute.argtypes = [i64, pd, pd, d, d, d, pd]
+            L.orc_lj_list.restype = d
+            L.orc_lj_list.argtypes = [i64, pd, pd, d, d, d, pi64, pi32, pd, pd]
+            L.orc_sc_list.restype = d
+            L.orc_sc_list.argtypes = [i64, pd, pd, d, d, d, d, d, d, pi64, pi32, pd, pd, pd, pd]
+            L.orc_sc_brute.restype = d
+            L.orc_sc_brute.argtypes = [i64, pd, pd, d, d, d, d, d, d, pd, pd]
+            L.orc_md_run.restype = i64
+            L.orc_md_run.argtypes = [C.POINTER(Params), i64, pd, pd, pd, i64, pd, pd]
+            L.orc_forces_once.restype = d
+            L.orc_forces_once.argtypes = [C.POINTER(Params), i64, pd, pd, pd]
+            L.orc_mlp_nparams.restype = C.c_int
+            L.orc_mlp_forward.restype = None
+            L.orc_mlp_forward.argtypes = [i64, pd, pd, pd]
+            L.orc_mlp_loss_grad.restype = d
+            L.orc_mlp_loss_grad.argtypes = [i64, pd, pd, pd, pd]
+            L.orc_adam.restype = None
+            L.orc_adam.argtypes = [i64, pd, pd, pd, pd, i64, d, d, d, d]
+            L.orc_partition.restype = None
+            L.orc_partition.argtypes = [i64, pi64, i32, pi64]
+        return _lib
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def set_threads(n: int) -> None:
+    """Number of OpenMP threads the oracle's per-atom loops may use."""
+    os.environ["OMP_NUM_THREADS"] = str(int(n))
+    try:
+        libgomp = C.CDLL("libgomp.so.1")
+        libgomp.omp_set_num_threads(C.c_int(int(n)))
+    except OSError:
+        pass
+
+
+def pair_r2(pos, box, i, j) -> float:
+    pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
+    return lib().orc_pair_r2(_P(pos, C.c_double), _P(box, C.c_double), i, j)
+
+
+def cell_grid(box, r_list):
+    box = _f64(box, (3,))
+    ncell = np.zeros(3, np.int32)
+    inv_w = np.zeros(3, np.float64)
+    st = lib().orc_cell_grid(_P(box, C.c_double), float(r_list), _P(ncell, C.c_int32),
+                             _P(inv_w, C.c_double))
+    if st != 0:
+        raise ValueError("invalid box / r_list")
+    return ncell, inv_w
+
+
+def bin_cells(pos, box, r_list):
+    """Returns (ncell[3], cell_of_atom[n], cell_start[ncells+1], order[n])."""
+    pos = _f64(pos, (-1, 3))
+    n = pos.shape[0]
+    ncell, inv_w = cell_grid(box, r_list)
+    ncells = int(np.prod(ncell.astype(np.int64)))
+    cell_of = np.zeros(n, np.int32)
+    start = np.zeros(ncells + 1, np.int64)
+    order = np.zeros(n, np.int64)
+    lib().orc_bin(n, _P(pos, C.c_double), _P(ncell, C.c_int32), _P(inv_w, C.c_double),
+                  _P(cell_of, C.c_int32), _P(start, C.c_int64), _P(order, C.c_int64))
+    return ncell, cell_of, start, order
+
+
+def _neighbors(fn, pos, box, r_list, half):
+    pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
+    n = pos.shape[0]
+    offsets = np.zeros(n + 1, np.int64)
+    cap = max(1024, 96 * n)
+    while True:
+        ids = np.zeros(cap, np.int32)
+        t = fn(n, _P(pos, C.c_double), _P(box, C.c_double), float(r_list), int(bool(half)),
+               _P(offsets, C.c_int64), _P(ids, C.c_int32), cap)
+        if t >= 0:
+            return offsets, ids[:t].copy()
+        if t != -4:
+            raise ValueError("neighbour list failed (%d)" % t)
+        cap = int(offsets[-1]) + 1024 if offsets[-1] > cap else 2 * cap
+
+
+def neighbors_brute(pos, box, r_list, half=False):
+    """CSR (offsets[n+1], ids) of {j != i : r_ij^2 < r_list^2}, ascending j."""
+    return _neighbors(lib().orc_neighbors_brute, pos, box, r_list, half)
+
+
+def neighbors_cells(pos, box, r_list, half=False):
+    """Same set as neighbors_brute, found with the 27-cell stencil."""
+    return _neighbors(lib().orc_neighbors_cells, pos, box, r_list, half)
+
+
+def lj_brute(pos, box, eps=1.0, sigma=1.0, rc=2.5):
+    pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
+    f = np.zeros_like(pos)
+    U = lib().orc_lj_brute(pos.shape[0], _P(pos, C.c_double), _P(box, C.c_double), eps, sigma,
+                           rc, _P(f, C.c_double))
+    return U, f
+
+
+def lj_list(pos, box, offsets, ids, eps=1.0, sigma=1.0, rc=2.5, per_atom=False):
+    pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    ids = np.ascontiguousarray(ids, np.int32)
+    f = np.zeros_like(pos)
+    e = np.zeros(pos.shape[0]) if per_atom else None
+    U = lib().orc_lj_list(pos.shape[0], _P(pos, C.c_double), _P(box, C.c_double), eps, sigma,
+                          rc, _P(offsets, C.c_int64), _P(ids, C.c_int32), _P(f, C.c_double),
+                          _P(e, C.c_double) if per_atom else None)
+    return (U, f, e) if per_atom else (U, f)
+
+
+def sc_list(pos, box, offsets, ids, eps=1.0, a=1.0, c=39.432, n_exp=9.0, m_exp=6.0, rc=2.0):
+    """Returns (U, f, rho, dF) from a full list."""
+    pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    ids = np.ascontiguousarray(ids, np.int32)
+    n = pos.shape[0]
+    f = np.zeros_like(pos)
+    rho = np.zeros(n)
+    dF = np.zeros(n)
+    U = lib().orc_sc_list(n, _P(pos, C.c_double), _P(box, C.c_double), eps, a, c, n_exp, m_exp,
+                          rc, _P(offsets, C.c_int64), _P(ids, C.c_int32), _P(f, C.c_double),
+                          _P(rho, C.c_double), _P(dF, C.c_double), None)
+    return U, f, rho, dF
+
+
+def sc_brute(pos, box, eps=1.0, a=1.0, c=39.432, n_exp=9.0, m_exp=6.0, rc=2.0):
+    pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
+    f = np.zeros_like(pos)
+    rho = np.zeros(pos.shape[0])
+    U = lib().orc_sc_brute(pos.shape[0], _P(pos, C.c_double), _P(box, C.c_double), eps, a, c,
+                           n_exp, m_exp, rc, _P(f, C.c_double), _P(rho, C.c_double))
+    return U, f, rho
+
+
+def md_run(params: Params, pos, vel, box, nsteps, want_energies=True):
+    """nsteps velocity-Verlet steps on copies of pos/vel.
+
+    Returns dict(pos, vel, force, energies[(nsteps+1) x 3] = KE, PE, KE+PE,
+    builds)."""
+    pos = _f64(pos, (-1, 3)).copy()
+    vel = _f64(vel, (-1, 3)).copy()
+    box = _f64(box, (3,))
+    n = pos.shape[0]
+    E = np.zeros((nsteps + 1, 3)) if want_energies else None
+    f = np.zeros_like(pos)
+    b = lib().orc_md_run(C.byref(params), n, _P(pos, C.c_double), _P(vel, C.c_double),
+                         _P(box, C.c_double), int(nsteps),
+                         _P(E, C.c_double) if want_energies else None, _P(f, C.c_double))
+    if b < 0:
+        raise RuntimeError("oracle md_run failed (%d)" % b)
+    return {"pos": pos, "vel": vel, "force": f, "energies": E, "builds": int(b)}
+
+
+def forces_once(params: Params, pos, box):
+    pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
+    f = np.zeros_like(pos)
+    U = lib().orc_forces_once(C.byref(params), pos.shape[0], _P(pos, C.c_double),
+                              _P(box, C.c_double), _P(f, C.c_double))
+    return U, f
+
+
+# ---- cost model -----------------------------------------------------------
+
+MLP_HIDDEN = 32
+
+
+def mlp_nparams() -> int:
+    return int(lib().orc_mlp_nparams())
+
+
+def mlp_forward(X, P):
+    X = _f64(X, (-1, 3))
+    P = _f64(P)
+    y = np.zeros(X.shape[0])
+    lib().orc_mlp_forward(X.shape[0], _P(X, C.c_double), _P(P, C.c_double), _P(y, C.c_double))
+    return y
+
+
+def mlp_loss_grad(X, y, P):
+    X = _f64(X, (-1, 3))
+    y = _f64(y)
+    P = _f64(P)
+    G = np.zeros_like(P)
+    loss = lib().orc_mlp_loss_grad(X.shape[0], _P(X, C.c_double), _P(y, C.c_double),
+                                   _P(P, C.c_double), _P(G, C.c_double))
+    return loss, G
+
+
+def adam(P, G, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In-place Adam step on float64 arrays P, m, v."""
+    for a in (P, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    G = _f64(G)
+    lib().orc_adam(P.size, _P(P, C.c_double), _P(G, C.c_double), _P(m, C.c_double),
+                   _P(v, C.c_double), int(t), lr, beta1, beta2, eps)
+
+
+def partition(cost, nparts):
+    cost = np.ascontiguousarray(cost, np.int64)
+    bounds = np.zeros(nparts + 1, np.int64)
+    lib().orc_partition(cost.size, _P(cost, C.c_int64), int(nparts), _P(bounds, C.c_int64))
+    return bounds
