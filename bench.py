@@ -1,0 +1,422 @@
+"""Throughput of the MD hot path on GB300: atom-steps/s of the mixed-precision
+path against the plain fp64 path on the porous Lennard-Jones system.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints ONE JSON line on rank 0.  A step is one velocity-Verlet step of the
+whole path (gated rebuild: binning + list; forces; kicks and drift) through
+md_step.  `value` is device-timed (CUDA events on the library's stream,
+inputs resident in HBM); `e2e` times the same steps through the C ABI from
+pinned host buffers (upload, md_set_state, md_step, md_get_state, download).
+With N > 1 each rank advances its own replica (no exchange: weak scaling).
+`--impl reference` times the CPU oracle instead, on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1611_00075_gb300 import inputs  # noqa: E402
+
+FP32_LANES_PER_SM = 128  # fp32 FMA lanes per Blackwell SM
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="porous", choices=["porous", "fcc", "sc"])
+    ap.add_argument("--scheduler", default="grid",
+                    choices=["grid", "paircount", "mlp", "dynamic"])
+    ap.add_argument("--fp64-steps", type=int, default=50,
+                    help="steps timed for the plain fp64 comparison (slow path)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nc", type=int, default=0,
+                    help="fcc cells per side (0 = the workload's own size; smaller for profiling)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(name: str, nc: int = 0):
+    if name == "porous" and nc:
+        s = inputs.lj_porous(nc=nc)
+        return s, "porous Lennard-Jones solid, %d^3 fcc cells (profiling size), %d atoms" % (nc, s.n)
+    if name == "porous":
+        s = inputs.lj_porous()
+        desc = ("porous Lennard-Jones solid: 160^3 fcc cells = 16,384,000 sites at rho*=0.8442, "
+                "spherical voids r~U(3,15) until >=40% removed, T*=0.3, rc=2.5, skin=0.3, "
+                "dt=0.005, half-skin rebuilds")
+    elif name == "fcc":
+        s = inputs.lj_fcc(nc=64, T=1.2)
+        desc = "Lennard-Jones fcc 64^3 cells = 1,048,576 atoms, rho*=0.8442, T*=1.2, rc=2.5, skin=0.3"
+    else:
+        s = inputs.sc_fcc(nc=128)
+        desc = ("Sutton-Chen fcc 128^3 cells = 8,388,608 atoms, a0=a=1, c=39.432, n=9, m=6, "
+                "rc=2a, skin=0.2, T*=2.088, dt=7.6e-4")
+    return s, desc
+
+
+def md_kwargs(s):
+    p = dict(s.params)
+    kw = dict(eps=p["eps"], sigma=p["sigma"], rc=p["rc"], skin=p["skin"], dt=p["dt"],
+              mass=p["mass"], potential=p["potential"])
+    if p["potential"] == "sc":
+        kw.update(c=p["c"], n_exp=p["n_exp"], m_exp=p["m_exp"])
+    return kw
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        return rows
+
+    @staticmethod
+    def summarize(rows):
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows
+                                   if r[3].replace(".", "").isdigit()) if rows else None}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args, rank, world, local):
+    import torch
+    from paper_1611_00075_gb300 import md
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    md.lib()
+    stream = torch.cuda.Stream(device=dev)
+    s, desc = make_workload(args.workload, args.nc)
+    kw = md_kwargs(s)
+    sched = {"grid": md.MD_SCHED_GRID, "paircount": md.MD_SCHED_PAIRCOUNT,
+             "mlp": md.MD_SCHED_MLP, "dynamic": md.MD_SCHED_DYNAMIC}[args.scheduler]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(sysobj, nsteps):
+        md.md_set_timing(sysobj.h, True)
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        md.md_step(sysobj.h, nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        st = json.loads(md.md_stats(sysobj.h))
+        md.md_set_timing(sysobj.h, False)
+        return ms, st
+
+    sampler = ClockSampler(local)
+    with torch.cuda.stream(stream):
+        mixed = md.System(s.pos, s.vel, s.box, precision="mixed", scheduler=sched,
+                          stream=stream, **kw)
+        md.md_step(mixed.h, args.warmup)
+        builds0 = json.loads(md.md_stats(mixed.h))["builds"]
+        sampler.start()
+        ms, st = timed(mixed, args.steps)
+        builds_timed = st["builds"] - builds0
+        clock_rows = sampler.stop()
+        ms = max_over_ranks(ms)
+        ke, pe = md.md_energy(mixed.h)
+        st_e = json.loads(md.md_stats(mixed.h))
+        pos, vel, force = mixed.state()
+        n = mixed.n
+        value = n * args.steps * world / (ms * 1e-3)
+
+        # plain fp64 path, same workload
+        fp64 = None
+        if args.fp64_steps > 0:
+            plain = md.System(s.pos, s.vel, s.box, precision="fp64", stream=stream, **kw)
+            md.md_step(plain.h, min(args.warmup, 3))
+            ms64, st64 = timed(plain, args.fp64_steps)
+            ms64 = max_over_ranks(ms64)
+            fp64 = {"value": n * args.fp64_steps * world / (ms64 * 1e-3), "steps": args.fp64_steps,
+                    "ms_per_step": ms64 / args.fp64_steps,
+                    "force_ms_per_launch": st64["ms"]["force"] / max(1, st64["count"]["force"])}
+            plain.close()
+
+        # end to end through the C ABI with pinned host buffers
+        e2e = None
+        if not args.no_e2e:
+            hp = torch.from_numpy(np.ascontiguousarray(s.pos)).pin_memory()
+            hv = torch.from_numpy(np.ascontiguousarray(s.vel)).pin_memory()
+            op = torch.empty_like(hp).pin_memory()
+            ov = torch.empty_like(hv).pin_memory()
+            dp = torch.empty(hp.shape, dtype=torch.float64, device=dev)
+            dv = torch.empty_like(dp)
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            dp.copy_(hp, non_blocking=True)
+            dv.copy_(hv, non_blocking=True)
+            md.md_set_state(mixed.h, dp, dv)
+            md.md_step(mixed.h, args.steps)
+            md.md_get_state(mixed.h, dp, dv, None)
+            op.copy_(dp, non_blocking=True)
+            ov.copy_(dv, non_blocking=True)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            barrier()
+            te = max_over_ranks(t1 - t0)
+            nbytes = hp.numel() * 8 + hv.numel() * 8
+            e2e = {"value": n * args.steps * world / te, "unit": "atom-steps/s",
+                   "h2d_bytes_per_step": nbytes / args.steps,
+                   "d2h_bytes_per_step": nbytes / args.steps,
+                   "note": "per run: upload pos+vel, md_set_state, md_step(K), md_get_state, "
+                           "download pos+vel; bytes amortised over K steps"}
+        mixed.close()
+
+    peaks, peak_src = measured_peaks()
+    # roofline of the force kernel (dominant launch): algorithmic work per launch
+    n_force = max(1, st["count"]["force"])
+    t_force = st["ms"]["force"] / n_force * 1e-3
+    entries = st_e["list_entries"]
+    pairs = st_e["pairs_cut"]
+    if kw["potential"] == "lj":
+        flops = 12.0 * entries + 14.0 * pairs
+        bytes_ = 168.0 * n + 4.0 * entries
+    else:
+        flops = 2 * (12.0 * entries) + 10.0 * pairs + 26.0 * pairs
+        bytes_ = 2 * 4.0 * entries + 250.0 * n
+    clk = ClockSampler.summarize(clock_rows)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = torch.cuda.get_device_properties(dev).multi_processor_count * \
+        FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    hbm_peak = float(peaks["hbm_gbs"])
+    ach_flops = flops / t_force / 1e12
+    ach_gbs = bytes_ / t_force / 1e9
+    ai = flops / bytes_
+    hbm_bound = ai * hbm_peak * 1e9 < fp32_peak * 1e12
+    roof = {"bound": "hbm" if hbm_bound else "alu",
+            "achieved": ach_gbs if hbm_bound else ach_flops,
+            "peak": hbm_peak if hbm_bound else fp32_peak,
+            "unit": "GB/s" if hbm_bound else "TFLOP/s",
+            "frac": (ach_gbs / hbm_peak) if hbm_bound else (ach_flops / fp32_peak),
+            "traffic": None,
+            "kernel": "lj_mixed_kernel<FM_FUSED_FULL>" if kw["potential"] == "lj" else "sc_force_mixed",
+            "peak_source": peak_src,
+            "algorithmic_bytes_per_launch": bytes_, "algorithmic_flops_per_launch": flops,
+            "launch_ms": t_force * 1e3,
+            "fp32": {"achieved_tflops": ach_flops, "peak_tflops": fp32_peak,
+                     "frac": ach_flops / fp32_peak,
+                     "peak_note": "SMs x 128 fp32 lanes x 2 x max SM clock"}}
+    return dict(n=n, value=value, ms=ms, st=st, st_e=st_e, fp64=fp64, e2e=e2e, roof=roof,
+                clk=clk, desc=desc, pos=pos.cpu().numpy(), force=force.cpu().numpy(),
+                box=s.box, params=s.params, ke=ke, pe=pe, builds_timed=builds_timed)
+
+
+# ------------------------------------------------------------------ CPU legs
+
+def oracle_sample_system(args):
+    """Bounded sample of the workload for the CPU oracle: the same generator
+    at a smaller size (porous: 72^3 fcc cells, same density and void radii)."""
+    if args.workload == "porous":
+        return inputs.lj_porous(nc=72), "porous LJ 72^3 fcc cells (same rho*, voids U(3,15), >=40%)"
+    if args.workload == "fcc":
+        return inputs.lj_fcc(nc=32, T=1.2), "LJ fcc 32^3 cells"
+    return inputs.sc_fcc(nc=48), "Sutton-Chen fcc 48^3 cells"
+
+
+def oracle_params(orc, p: dict):
+    if p["potential"] == "lj":
+        return orc.make_params(potential=orc.POT_LJ, eps=p["eps"], sigma=p["sigma"], rc=p["rc"],
+                               skin=p["skin"], dt=p["dt"], mass=p["mass"])
+    return orc.make_params(potential=orc.POT_SC, eps=p["eps"], sigma=p["sigma"], c=p["c"],
+                           n_exp=p["n_exp"], m_exp=p["m_exp"], rc=p["rc"], skin=p["skin"],
+                           dt=p["dt"], mass=p["mass"])
+
+
+def cpu_baseline_leg(args, gpu=None, steps=None):
+    """Times the CPU oracle (as it stands) on a bounded sample on all host
+    cores, and measures the GPU snapshot's force error against it."""
+    import oracle as orc
+    orc.build()
+    cores = os.cpu_count() or 1
+    orc.set_threads(cores)
+    s, what = oracle_sample_system(args)
+    prm = oracle_params(orc, s.params)
+    k = steps if steps is not None else 5
+    t0 = time.perf_counter()
+    orc.forces_once(prm, s.pos, s.box)
+    t1 = time.perf_counter()
+    orc.md_run(prm, s.pos, s.vel, s.box, k, want_energies=False)
+    t2 = time.perf_counter()
+    per_step = max(1e-9, ((t2 - t1) - (t1 - t0)) / k)  # first list build excluded
+    out = {"value": s.n / per_step, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
+           "sample": "%s, %d atoms, %d velocity-Verlet steps after the first list build "
+                     "(fp64 C oracle, OpenMP over atoms)" % (what, s.n, k)}
+    if gpu is not None:
+        rng_idx = (inputs.splitmix64(inputs.SEED_BASE + 99, 4096) % gpu["n"]).astype(np.int64)
+        idx = np.unique(rng_idx)
+        fref, _ = orc.forces_sample(oracle_params(orc, gpu["params"]), gpu["pos"], gpu["box"], idx)
+        f = gpu["force"][idx]
+        err = np.linalg.norm(f - fref, axis=1)
+        fn = np.linalg.norm(fref, axis=1)
+        rms = math.sqrt(float(np.mean(fn * fn)))
+        out["force_error"] = {"atoms": int(idx.size), "max_abs": float(err.max()),
+                              "rms_abs": float(math.sqrt(np.mean(err * err))),
+                              "max_rel_to_max(|f|,rms)": float(np.max(err / np.maximum(fn, rms))),
+                              "rms_force": rms}
+    return out
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle as orc
+    orc.build()
+    cores = os.cpu_count() or 1
+    orc.set_threads(cores)
+    s, what = oracle_sample_system(args)
+    prm = oracle_params(orc, s.params)
+    t0 = time.perf_counter()
+    out = orc.md_run(prm, s.pos, s.vel, s.box, args.warmup, want_energies=False)
+    t1 = time.perf_counter()
+    orc.md_run(prm, out["pos"], out["vel"], s.box, args.steps, want_energies=False)
+    t2 = time.perf_counter()
+    # the timed run includes its own first list build, as md_step's first call would
+    value = s.n * args.steps / (t2 - t1)
+    line = {"impl": "reference", "metric": "atom-steps/s", "value": value, "unit": "atom-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": (t2 - t1) * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": what, "atoms": s.n},
+            "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": "%s, %d atoms, %d steps" % (what, s.n, args.steps)},
+            "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    g = run_gpu(args, rank, world, local)
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu = cpu_baseline_leg(args, gpu=g)
+    st = g["st"]
+    line = {
+        "metric": "atom-steps/s at 1 GB300 (mixed+learned vs plain FP64) at stated force error",
+        "value": g["value"], "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": g["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair terms / f64 state",
+        "data": "synthetic",
+        "config": {"workload": g["desc"], "atoms": g["n"], "precision": "mixed",
+                   "force_variant": "full list", "scheduler": args.scheduler,
+                   "l2": "inputs larger than L2 (%.1f GB resident state + list)"
+                         % ((g["n"] * 300 + g["st_e"]["list_entries"] * 4) / 1e9),
+                   "list_builds_in_timed_steps": g["builds_timed"]},
+        "fp64_baseline": g["fp64"],
+        "speedup_vs_fp64": (g["value"] / g["fp64"]["value"]) if g["fp64"] else None,
+        "roofline": g["roof"],
+        "clocks": g["clk"],
+        "e2e": g["e2e"],
+        "gpu_launches": st["launches"],
+        "kernel_ms": {"rebuild": st["ms"]["rebuild"], "force": st["ms"]["force"],
+                      "integrate": st["ms"]["integrate"], "counts": st["count"]},
+        "energy": {"ke": g["ke"], "pe": g["pe"]},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * md_gb300.h -- C ABI of the GB300 (sm_103a) short-range molecular-dynamics
+ * hot path: cell binning, Verlet neighbour lists with skin, pair (Lennard-
+ * Jones) and many-body (Sutton-Chen) forces, and velocity-Verlet integration.
+ *
+ * The problem statement follows Mangiardi & Meyer, "A hybrid algorithm for
+ * parallel molecular dynamics simulations": N atoms in a periodic box, a
+ * short-range potential with cutoff r_c, Verlet lists of radius
+ * r_list = r_c + skin (Sec. 2.1, Sec. 3.3), pair forces
+ * F = -(1/d) dPhi/dr R with R = r_i - r_j (Sec. 2.2), many-body energy
+ * U = sum_i F_i(rho_i) + 1/2 sum_{i != j} Phi_ij(r_ij) with
+ * rho_i = sum_{j != i} psi_ij(r_ij) (Eq. 1, Eq. 2) evaluated in three steps
+ * (Sec. 3.1), and velocity-Verlet time stepping with list rebuilds when an
+ * atom has moved more than half the skin (Sec. 3.3).
+ *
+ * Conventions for every call:
+ *  - Arrays passed by the caller are caller-owned.  Pointer arguments named
+ *    *_dev are DEVICE pointers, *_host are HOST pointers.  Positions,
+ *    velocities and forces are n x 3 float64, xyz interleaved, in ORIGINAL
+ *    atom order (the order given to md_create).
+ *  - The library owns a private, cell-sorted copy of the state on the GPU;
+ *    it allocates it in md_create and frees it in md_destroy.
+ *  - Work is enqueued on the CUDA stream given to md_create.  Calls that
+ *    return host values (md_energy, md_stats, md_get_neighbors' total) or
+ *    that must inspect device status (md_step) synchronize that stream.
+ *  - Every call returns an md_status.  Nothing calls exit() or traps on the
+ *    device.  After MD_ERR_STATE the handle must be destroyed; after any
+ *    other error it stays usable, and md_last_error(h) describes the error.
+ *  - Not thread-safe per handle; distinct handles are independent.
+ */
+#ifndef MD_GB300_H
+#define MD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct md_system md_system; /* opaque, library-owned */
+
+typedef enum {
+    MD_OK = 0,
+    MD_ERR_INVALID = -1,       /* bad argument, box or parameter */
+    MD_ERR_OOM = -2,           /* device allocation failed */
+    MD_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+    MD_ERR_LIST_OVERFLOW = -4, /* neighbour capacity exceeded (md_step regrows and retries) */
+    MD_ERR_NONFINITE = -5,     /* a position or force became NaN/Inf */
+    MD_ERR_TIMEOUT = -6,       /* a bounded device wait gave up */
+    MD_ERR_STATE = -7          /* handle unusable: destroy it */
+} md_status;
+
+enum { MD_POT_LJ = 0, MD_POT_SC = 1 };
+enum { MD_FP64 = 0, MD_MIXED = 1 };
+/* Newton's-third-law strategy (Sec. 1 race problem, Sec. 2.2 pair loop). */
+enum { MD_FORCE_FULL = 0, MD_FORCE_HALF_COLOR = 1, MD_FORCE_HALF_ATOMIC = 2 };
+/* How force work is spread over the SMs. */
+enum {
+    MD_SCHED_GRID = 0,      /* one thread per atom, hardware block scheduler */
+    MD_SCHED_PAIRCOUNT = 1, /* persistent CTAs, static partition by list length */
+    MD_SCHED_MLP = 2,       /* persistent CTAs, static partition by the learned cost model */
+    MD_SCHED_DYNAMIC = 3    /* persistent CTAs pulling tiles from an atomic queue */
+};
+enum { MD_COST_TRAIN = 0, MD_COST_PREDICT = 1, MD_COST_RESET = 2, MD_COST_SAMPLE = 3 };
+
+typedef struct {
+    int32_t potential;     /* MD_POT_LJ or MD_POT_SC */
+    int32_t precision;     /* MD_FP64 (plain) or MD_MIXED (fp32 pair math, fp64 state) */
+    int32_t force_variant; /* MD_FORCE_* */
+    int32_t rebuild_every; /* 0: rebuild when an atom moved > skin/2 (Sec. 3.3); k>0: every k steps */
+    int32_t scheduler;     /* MD_SCHED_* */
+    int32_t max_neighbors; /* list capacity per atom; 0 = sized from the first build */
+    int32_t reserved0;
+    int32_t reserved1;
+    double eps;            /* LJ epsilon / SC epsilon */
+    double sigma;          /* LJ sigma / SC lattice parameter a */
+    double c;              /* SC c (ignored for LJ) */
+    double n_exp;          /* SC pair exponent n (integer valued, 1..30) */
+    double m_exp;          /* SC density exponent m (integer valued, 1..30) */
+    double rc;             /* potential cutoff r_c > 0 */
+    double skin;           /* list skin >= 0; r_list = rc + skin */
+    double dt;             /* time step */
+    double mass;           /* atom mass > 0 */
+} md_params;
+
+/* Creates a system of n >= 1 atoms in the orthorhombic periodic box
+ * box3_host[3] (each side must hold at least 3 list radii, so that the 27
+ * cells around any cell are distinct).  pos_dev / vel_dev: n x 3 float64
+ * device arrays, positions inside [0, L); both are copied.  cuda_stream: a
+ * cudaStream_t (NULL = legacy default stream).  Bins atoms (Sec. 2.1),
+ * builds the first list with capacity from a counting pass, and evaluates
+ * forces.  Energy is L/J units of the potential. */
+md_status md_create(md_system **out, const md_params *p, int64_t n, const double *box3_host,
+                    const double *pos_dev, const double *vel_dev, void *cuda_stream);
+
+/* Cell binning only (Sec. 2.1): assigns each atom to cell
+ * c = min(floor(x * n_d / L_d), n_d - 1) per dimension, n_d = floor(L_d /
+ * r_list), linear id (cz * ny + cy) * nx + cx, and reorders the private copy
+ * stably by (cell, original id).  Invalidates the neighbour list. */
+md_status md_bin_cells(md_system *h);
+
+/* Rebuilds the Verlet list from the current positions (bins first).  An
+ * entry j of atom i means r_ij^2 < r_list^2 computed in float64 as
+ * dx*dx + dy*dy + dz*dz on minimum-image components. */
+md_status md_build_neighbors(md_system *h);
+
+/* Forces (and per-atom energies) at the current positions, rebuilding the
+ * list first when it is stale.  Asynchronous. */
+md_status md_forces(md_system *h);
+
+/* Advances nsteps >= 0 velocity-Verlet steps (Sec. 3.3).  Lists are rebuilt
+ * on the device when the half-skin rule (or rebuild_every) asks for it; a
+ * neighbour-capacity overflow is repaired on the host (capacity grown,
+ * list rebuilt) and the remaining steps continue.  Synchronizes the stream
+ * once at the end to read the device status word. */
+md_status md_step(md_system *h, int64_t nsteps);
+
+/* Kinetic and potential energy at the current state (host outputs).  The
+ * potential energy comes from a fresh force evaluation; synchronizes. */
+md_status md_energy(md_system *h, double *ke_host, double *pe_host);
+
+/* Copies the state out in original atom order; any pointer may be NULL.
+ * pos_dev positions are wrapped into [0, L).  force_dev receives the forces
+ * of the last force evaluation. */
+md_status md_get_state(md_system *h, double *pos_dev, double *vel_dev, double *force_dev);
+
+/* Replaces positions and velocities (original order, device arrays); the
+ * next force evaluation rebinds and rebuilds the list. */
+md_status md_set_state(md_system *h, const double *pos_dev, const double *vel_dev);
+
+/* Exports the current list as CSR in original order: offsets_dev[n + 1]
+ * (int64) and ids_dev (int32 original ids, ascending within each row).
+ * half != 0 keeps only j > i.  cap = capacity of ids_dev in entries.
+ * *total_host receives the entry count; if it exceeds cap nothing is
+ * written to ids_dev and MD_ERR_LIST_OVERFLOW is returned.  Synchronizes. */
+md_status md_get_neighbors(md_system *h, int32_t half, int64_t *offsets_dev, int32_t *ids_dev,
+                           int64_t cap, int64_t *total_host);
+
+/* Cell of every atom (original order, int32 device array of n) and, if
+ * cell_start_dev != NULL, the sorted cell starts (int64, ncells + 1).
+ * ncell_host[3] receives the cells per dimension.  Synchronizes. */
+md_status md_get_cells(md_system *h, int32_t *cell_of_atom_dev, int64_t *cell_start_dev,
+                       int32_t *ncell_host);
+
+/* Many-body intermediate results of the last force evaluation (Sutton-
+ * Chen only; original order, float64 device arrays of n): rho_i (Eq. 2)
+ * and F'(rho_i).  Either pointer may be NULL. */
+md_status md_get_density(md_system *h, double *rho_dev, double *dF_dev);
+
+/* Per-atom potential energy of the last force evaluation with energy
+ * (md_energy), original order, float64 device array of n. */
+md_status md_get_atom_energy(md_system *h, double *e_dev);
+
+/* Switches the force strategy and scheduler of an existing system (same
+ * potential and precision).  The next force evaluation uses them. */
+md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler);
+
+/* Learned per-cell cost model (3 -> 32 -> 32 -> 1 MLP, ReLU, fp32).
+ *  MD_COST_SAMPLE  time one force pass with per-tile clock64 and store
+ *                  per-cell (features, log cycles) training samples
+ *  MD_COST_TRAIN   run Adam epochs on the stored samples on the GPU;
+ *                  *loss_out (host, may be NULL) receives the final loss
+ *  MD_COST_PREDICT infer per-cell costs and rebuild the static partition
+ *  MD_COST_RESET   re-initialise the network weights */
+md_status md_cost_model(md_system *h, int32_t op, float *loss_out);
+
+/* Per-launch timing: with on != 0 the library records a CUDA event after
+ * each rebuild chain, force evaluation and integrator launch it enqueues
+ * (on the handle's stream) and md_stats reports the summed milliseconds and
+ * counts per kind, plus the number of kernels enqueued.  Resets the sums.
+ * Synchronizes. */
+md_status md_set_timing(md_system *h, int32_t on);
+
+/* Writes a one-line JSON summary (atoms, cells, list capacity, rebuild
+ * count, steps, last kernel times) into buf_host (NUL-terminated, at most
+ * cap bytes).  Synchronizes. */
+md_status md_stats(md_system *h, char *buf_host, size_t cap);
+
+/* Last error message of h (or of the calling thread when h is NULL). */
+const char *md_last_error(md_system *h);
+
+void md_destroy(md_system *h);
+
+/* ---- building blocks exposed for parity tests and tools --------------- */
+
+/* Forward pass of the cost model on ns samples: X_dev ns x 3 fp32,
+ * P_dev parameters (layout W1[32][3], b1[32], W2[32][32], b2[32], W3[32],
+ * b3[1]; 1217 fp32), y_dev ns fp32 outputs.  Asynchronous on stream. */
+md_status md_mlp_forward(const float *X_dev, int64_t ns, const float *P_dev, float *y_dev,
+                         void *cuda_stream);
+
+/* Mean-squared-error loss and its gradient over ns samples (fp32):
+ * G_dev (1217 fp32) receives dL/dP, loss_dev (1 fp32) the loss.
+ * Asynchronous on stream. */
+md_status md_mlp_loss_grad(const float *X_dev, const float *y_dev, int64_t ns,
+                           const float *P_dev, float *G_dev, float *loss_dev,
+                           void *cuda_stream);
+
+/* One Adam step (Kingma & Ba) at 1-based step t on np fp32 parameters. */
+md_status md_mlp_adam(float *P_dev, const float *G_dev, float *m_dev, float *v_dev, int64_t np,
+                      int64_t t, float lr, float beta1, float beta2, float epsilon,
+                      void *cuda_stream);
+
+/* Contiguous equal-cost partition of ncells integer costs into nparts:
+ * bounds_dev[b] = first cell k with (inclusive prefix of cost through k) *
+ * nparts > b * total; bounds_dev[0] = 0, bounds_dev[nparts] = ncells.
+ * Asynchronous on stream. */
+md_status md_partition(const int64_t *cost_dev, int64_t ncells, int32_t nparts,
+                       int64_t *bounds_dev, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MD_GB300_H */

@@ -292,3 +292,48 @@ def partition(cost, nparts):
     bounds = np.zeros(nparts + 1, np.int64)
     lib().orc_partition(cost.size, _P(cost, C.c_int64), int(nparts), _P(bounds, C.c_int64))
     return bounds
+
+
+def _sample_sigs():
+    L = lib()
+    if getattr(L, "_sample_ready", False):
+        return L
+    d, i64 = C.c_double, C.c_int64
+    pd, pi64, pi32 = C.POINTER(d), C.POINTER(i64), C.POINTER(C.c_int32)
+    L.orc_forces_sample.restype = C.c_int
+    L.orc_forces_sample.argtypes = [C.POINTER(Params), i64, pd, pd, i64, pi64, pd, pd]
+    L.orc_neighbors_sample.restype = i64
+    L.orc_neighbors_sample.argtypes = [i64, pd, pd, d, i64, pi64, pi64, pi32, i64]
+    L._sample_ready = True
+    return L
+
+
+def forces_sample(params: Params, pos, box, idx):
+    """Forces and per-atom energies of the atoms idx (original ids) only."""
+    L = _sample_sigs()
+    pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
+    idx = np.ascontiguousarray(idx, np.int64)
+    f = np.zeros((idx.size, 3))
+    e = np.zeros(idx.size)
+    st = L.orc_forces_sample(C.byref(params), pos.shape[0], _P(pos, C.c_double),
+                             _P(box, C.c_double), idx.size, _P(idx, C.c_int64),
+                             _P(f, C.c_double), _P(e, C.c_double))
+    if st != 0:
+        raise RuntimeError("oracle forces_sample failed (%d)" % st)
+    return f, e
+
+
+def neighbors_sample(pos, box, r_list, idx):
+    """List rows (ascending original id) of the sampled atoms idx."""
+    L = _sample_sigs()
+    pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
+    idx = np.ascontiguousarray(idx, np.int64)
+    off = np.zeros(idx.size + 1, np.int64)
+    cap = 512 * max(1, idx.size)
+    ids = np.zeros(cap, np.int32)
+    t = L.orc_neighbors_sample(pos.shape[0], _P(pos, C.c_double), _P(box, C.c_double),
+                               float(r_list), idx.size, _P(idx, C.c_int64), _P(off, C.c_int64),
+                               _P(ids, C.c_int32), cap)
+    if t < 0:
+        raise RuntimeError("oracle neighbors_sample failed (%d)" % t)
+    return off, ids[:t].copy()

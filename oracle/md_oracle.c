@@ -441,6 +441,148 @@ double orc_sc_brute(int64_t n, const double *pos, const double *box, double eps,
     return U;
 }
 
+/* Forces (and per-atom energies) of a sample of atoms, for systems too large
+ * for the all-atom routines: the 27 cells around each sampled atom are
+ * scanned for pairs with r^2 < r_c^2 (same definitions as above).  For the
+ * many-body potential the density of every atom within r_c of a sampled atom
+ * is needed, so rho is computed for the sample and for those neighbours.
+ * idx[k] are original ids; f_out is nsamp x 3, e_out (optional) nsamp. */
+static void sample_cells(int64_t n, const double *pos, const double *box, double r,
+                         int32_t *ncell, int32_t **cell_of, int64_t **start, int64_t **order) {
+    double inv_w[3];
+    orc_cell_grid(box, r, ncell, inv_w);
+    int64_t nc = (int64_t)ncell[0] * ncell[1] * ncell[2];
+    *cell_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    *start = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nc + 1));
+    *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    orc_bin(n, pos, ncell, inv_w, *cell_of, *start, *order);
+}
+
+/* neighbours of atom i within r (strict), via the cell grid; returns count,
+ * writes up to cap original ids into out */
+static int64_t cell_neighbors(int64_t i, const double *pos, const double *box, double r,
+                              const int32_t *ncell, const int32_t *cell_of, const int64_t *start,
+                              const int64_t *order, int64_t *out, int64_t cap) {
+    double r2c = r * r;
+    int64_t c = cell_of[i];
+    int32_t cx = (int32_t)(c % ncell[0]);
+    int32_t cy = (int32_t)((c / ncell[0]) % ncell[1]);
+    int32_t cz = (int32_t)(c / ((int64_t)ncell[0] * ncell[1]));
+    int32_t sx[3], sy[3], sz[3];
+    int kx = stencil_1d(cx, ncell[0], sx), ky = stencil_1d(cy, ncell[1], sy),
+        kz = stencil_1d(cz, ncell[2], sz);
+    int64_t cnt = 0;
+    for (int a = 0; a < kz; ++a)
+        for (int b = 0; b < ky; ++b)
+            for (int e = 0; e < kx; ++e) {
+                int64_t cc = cell_id(sx[e], sy[b], sz[a], ncell);
+                for (int64_t s = start[cc]; s < start[cc + 1]; ++s) {
+                    int64_t j = order[s];
+                    if (j == i) continue;
+                    if (orc_pair_r2(pos, box, i, j) < r2c) {
+                        if (cnt < cap) out[cnt] = j;
+                        cnt += 1;
+                    }
+                }
+            }
+    return cnt;
+}
+
+static int cmp_i64(const void *a, const void *b) {
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+int orc_forces_sample(const orc_params *p, int64_t n, const double *pos, const double *box,
+                      int64_t nsamp, const int64_t *idx, double *f_out, double *e_out) {
+    int32_t ncell[3];
+    int32_t *cell_of;
+    int64_t *start, *order;
+    sample_cells(n, pos, box, p->rc, ncell, &cell_of, &start, &order);
+    const int64_t CAP = 4096;
+    int bad = 0;
+    #pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
+    for (int64_t k = 0; k < nsamp; ++k) {
+        int64_t i = idx[k];
+        int64_t *nb = (int64_t *)malloc(sizeof(int64_t) * CAP);
+        int64_t *nb2 = (int64_t *)malloc(sizeof(int64_t) * CAP);
+        int64_t cnt = cell_neighbors(i, pos, box, p->rc, ncell, cell_of, start, order, nb, CAP);
+        if (cnt > CAP) { bad = 1; free(nb); free(nb2); continue; }
+        qsort(nb, (size_t)cnt, sizeof(int64_t), cmp_i64);  /* ascending j, as the list routines */
+        double fx = 0.0, fy = 0.0, fz = 0.0, ei = 0.0;
+        if (p->potential == 0) {
+            double shift = lj_phi(p->rc * p->rc, p->eps, p->sigma);
+            for (int64_t q = 0; q < cnt; ++q) {
+                double dx, dy, dz;
+                double r2 = pair_r2(pos, box, i, nb[q], &dx, &dy, &dz);
+                double fs = lj_fscalar(r2, p->eps, p->sigma);
+                fx -= fs * dx; fy -= fs * dy; fz -= fs * dz;
+                ei += 0.5 * (lj_phi(r2, p->eps, p->sigma) - shift);
+            }
+        } else {
+            /* step 1 for i and each neighbour j, step 2 for each, step 3 for i */
+            double rho_i = 0.0;
+            for (int64_t q = 0; q < cnt; ++q)
+                rho_i += sc_pow(p->sigma / sqrt(orc_pair_r2(pos, box, i, nb[q])), p->m_exp);
+            double dFi = rho_i > 0.0 ? -p->eps * p->c / (2.0 * sqrt(rho_i)) : 0.0;
+            double ep = 0.0;
+            for (int64_t q = 0; q < cnt; ++q) {
+                int64_t j = nb[q];
+                int64_t c2 = cell_neighbors(j, pos, box, p->rc, ncell, cell_of, start, order,
+                                            nb2, CAP);
+                if (c2 > CAP) { bad = 1; break; }
+                qsort(nb2, (size_t)c2, sizeof(int64_t), cmp_i64);
+                double rho_j = 0.0;
+                for (int64_t t = 0; t < c2; ++t)
+                    rho_j += sc_pow(p->sigma / sqrt(orc_pair_r2(pos, box, j, nb2[t])), p->m_exp);
+                double dFj = rho_j > 0.0 ? -p->eps * p->c / (2.0 * sqrt(rho_j)) : 0.0;
+                double dx, dy, dz;
+                double r2 = pair_r2(pos, box, i, j, &dx, &dy, &dz);
+                double r = sqrt(r2);
+                double Phi = p->eps * sc_pow(p->sigma / r, p->n_exp);
+                double psi = sc_pow(p->sigma / r, p->m_exp);
+                double g = -p->n_exp * Phi / r + (dFi + dFj) * (-p->m_exp * psi / r);
+                fx += g * dx / r; fy += g * dy / r; fz += g * dz / r;
+                ep += 0.5 * Phi;
+            }
+            ei = ep - p->eps * p->c * sqrt(rho_i);
+        }
+        f_out[3 * k + 0] = fx; f_out[3 * k + 1] = fy; f_out[3 * k + 2] = fz;
+        if (e_out) e_out[k] = ei;
+        free(nb); free(nb2);
+    }
+    free(cell_of); free(start); free(order);
+    return bad ? ORC_ERR_CAPACITY : ORC_OK;
+}
+
+/* Neighbour list rows (r < r_list, ascending original id) of sampled atoms.
+ * offsets has nsamp + 1 entries; returns the total or ORC_ERR_CAPACITY. */
+int64_t orc_neighbors_sample(int64_t n, const double *pos, const double *box, double r_list,
+                             int64_t nsamp, const int64_t *idx, int64_t *offsets, int32_t *ids,
+                             int64_t cap) {
+    int32_t ncell[3];
+    int32_t *cell_of;
+    int64_t *start, *order;
+    sample_cells(n, pos, box, r_list, ncell, &cell_of, &start, &order);
+    int64_t *nb = (int64_t *)malloc(sizeof(int64_t) * 4096);
+    int64_t total = 0;
+    offsets[0] = 0;
+    int overflow = 0;
+    for (int64_t k = 0; k < nsamp; ++k) {
+        int64_t cnt = cell_neighbors(idx[k], pos, box, r_list, ncell, cell_of, start, order, nb, 4096);
+        if (cnt > 4096) { overflow = 1; cnt = 4096; }
+        qsort(nb, (size_t)cnt, sizeof(int64_t), cmp_i64);
+        for (int64_t q = 0; q < cnt; ++q) {
+            if (total < cap) ids[total] = (int32_t)nb[q];
+            else overflow = 1;
+            total += 1;
+        }
+        offsets[k + 1] = total;
+    }
+    free(nb); free(cell_of); free(start); free(order);
+    return overflow ? ORC_ERR_CAPACITY : total;
+}
+
 /* ------------------------------------------------------------------------ */
 /* velocity-Verlet MD (Sec. 3.3): half kick, drift, wrap, forces, half kick;  */
 /* the list is rebuilt when an atom has moved more than half the skin since   */

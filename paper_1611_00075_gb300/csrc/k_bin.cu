@@ -1,0 +1,216 @@
+// k_bin.cu -- cell binning by counting sort (Sec. 2.1: the volume is divided
+// into small cells; a cell's atoms are processed together).
+//
+// Atoms are assigned to cell c = min(floor(x * n_d / L_d), n_d - 1) per
+// dimension, counted with atomics, the counts are scanned into cell starts,
+// atoms are scattered into their cell's range and each cell's range is put in
+// ascending original-id order, so the sorted layout is deterministic and
+// equals a stable sort by (cell, original id).  The gather then rewrites the
+// state in the new order as float64 positions relative to the cell centre
+// plus their float32 copy (the layout the force kernels read).
+#include "k_scan.cuh"
+
+namespace mdg {
+
+namespace {
+
+__device__ __forceinline__ bool chain_off(const DevStatus *ds, bool gated) {
+    return ds->status != 0 || (gated && ds->rebuild == 0);
+}
+
+// Periodic wrap into [0, L): x - L*floor(x/L), which for |x| < 2L is the
+// single x += L or x -= L; the second test catches x + L rounding up to L.
+__device__ __forceinline__ double wrap_coord(double x, double L) {
+    if (x < 0.0 || x >= L) x -= L * floor(x / L);
+    if (x >= L) x -= L;
+    return x;
+}
+
+// floor(x * inv_w) clamped to [0, n-1]; a NaN coordinate maps to 0 so that an
+// exploding state can never index outside the cell arrays (the drift check
+// reports it as MD_ERR_NONFINITE).
+__device__ __forceinline__ int cell_coord(double x, double inv_w, int n) {
+    const double q = floor(x * inv_w);
+    if (!(q >= 0.0)) return 0;
+    if (q > (double)(n - 1)) return n - 1;
+    return (int)q;
+}
+
+__device__ __forceinline__ double3 cell_centre(int c, const Grid &g) {
+    int cx = c % g.nx;
+    int cy = (c / g.nx) % g.ny;
+    int cz = c / (g.nx * g.ny);
+    return make_double3(((double)cx + 0.5) * g.w[0], ((double)cy + 0.5) * g.w[1],
+                        ((double)cz + 0.5) * g.w[2]);
+}
+
+// Absolute positions from the relative state (skipped when they are exact).
+__global__ void prepare_abs_kernel(int n, Grid g, const double4 *__restrict__ xr,
+                                   const int32_t *__restrict__ cell, double4 *__restrict__ xabs,
+                                   const DevStatus *ds, bool gated) {
+    if (chain_off(ds, gated) || ds->abs_fresh) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double4 r = xr[i];
+    int c = cell[i];
+    double x = r.x, y = r.y, z = r.z;
+    if (c >= 0) {
+        double3 C = cell_centre(c, g);
+        x = C.x + x; y = C.y + y; z = C.z + z;
+    }
+    xabs[i] = make_double4(wrap_coord(x, g.L[0]), wrap_coord(y, g.L[1]), wrap_coord(z, g.L[2]),
+                           0.0);
+}
+
+__global__ void zero_counts_kernel(int ncells, int32_t *count, DevStatus *ds, bool gated) {
+    if (chain_off(ds, gated)) return;
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) ds->max_cell = 0;
+    if (c < ncells) count[c] = 0;
+}
+
+__global__ void bin_count_kernel(int n, Grid g, const double4 *__restrict__ xabs,
+                                 int32_t *__restrict__ count, int32_t *__restrict__ new_cell,
+                                 int32_t *__restrict__ slot, DevStatus *ds, bool gated) {
+    if (chain_off(ds, gated)) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double4 x = xabs[i];
+    int cx = cell_coord(x.x, g.inv_w[0], g.nx);
+    int cy = cell_coord(x.y, g.inv_w[1], g.ny);
+    int cz = cell_coord(x.z, g.inv_w[2], g.nz);
+    int c = (cz * g.ny + cy) * g.nx + cx;
+    new_cell[i] = c;
+    int s = atomicAdd(&count[c], 1);
+    slot[i] = s;
+    atomicMax(&ds->max_cell, s + 1);
+}
+
+__global__ void scatter_kernel(int n, const int32_t *__restrict__ new_cell,
+                               const int32_t *__restrict__ slot,
+                               const int32_t *__restrict__ start, const int32_t *__restrict__ orig,
+                               int32_t *__restrict__ src, int32_t *__restrict__ key,
+                               const DevStatus *ds, bool gated) {
+    if (chain_off(ds, gated)) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int p = start[new_cell[i]] + slot[i];
+    src[p] = i;
+    key[p] = orig[i];
+}
+
+// Orders each cell's range by original id (insertion sort; cells hold tens of atoms).
+__global__ void cell_sort_kernel(int ncells, const int32_t *__restrict__ start,
+                                 int32_t *__restrict__ key, int32_t *__restrict__ src,
+                                 const DevStatus *ds, bool gated) {
+    if (chain_off(ds, gated)) return;
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    int b = start[c], e = start[c + 1];
+    for (int a = b + 1; a < e; ++a) {
+        int k = key[a], s = src[a];
+        int q = a - 1;
+        while (q >= b && key[q] > k) {
+            key[q + 1] = key[q];
+            src[q + 1] = src[q];
+            --q;
+        }
+        key[q + 1] = k;
+        src[q + 1] = s;
+    }
+}
+
+__global__ void copy_src_kernel(int n, const double4 *__restrict__ xabs,
+                                const double *__restrict__ v, const int32_t *__restrict__ orig,
+                                double4 *__restrict__ tabs, double *__restrict__ tv,
+                                int32_t *__restrict__ torig, const DevStatus *ds, bool gated) {
+    if (chain_off(ds, gated)) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    tabs[i] = xabs[i];
+    tv[i] = v[i];
+    tv[n + i] = v[n + i];
+    tv[2 * (size_t)n + i] = v[2 * (size_t)n + i];
+    torig[i] = orig[i];
+}
+
+__global__ void gather_kernel(int n, Grid g, const int32_t *__restrict__ src,
+                              const int32_t *__restrict__ new_cell,
+                              const double4 *__restrict__ tabs, const double *__restrict__ tv,
+                              const int32_t *__restrict__ torig, double4 *__restrict__ xr,
+                              float4 *__restrict__ xq, float4 *__restrict__ xq_build,
+                              double4 *__restrict__ xabs, double *__restrict__ v,
+                              int32_t *__restrict__ orig, int32_t *__restrict__ cell,
+                              DevStatus *ds, bool gated) {
+    if (chain_off(ds, gated)) return;
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) ds->abs_fresh = 1;
+    if (k >= n) return;
+    int s = src[k];
+    int c = new_cell[s];
+    double3 C = cell_centre(c, g);
+    double4 a = tabs[s];
+    double rx = a.x - C.x, ry = a.y - C.y, rz = a.z - C.z;
+    int o = torig[s];
+    xr[k] = make_double4(rx, ry, rz, 0.0);
+    float4 q = make_float4((float)rx, (float)ry, (float)rz, __int_as_float(o));
+    xq[k] = q;
+    xq_build[k] = q;
+    xabs[k] = a;
+    v[k] = tv[s];
+    v[n + k] = tv[n + s];
+    v[2 * (size_t)n + k] = tv[2 * (size_t)n + s];
+    orig[k] = o;
+    cell[k] = c;
+}
+
+__global__ void export_cells_kernel(int n, int ncells, const int32_t *__restrict__ orig,
+                                    const int32_t *__restrict__ cell,
+                                    const int32_t *__restrict__ start, int32_t *cell_of_atom,
+                                    int64_t *cell_start) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && cell_of_atom) cell_of_atom[orig[i]] = cell[i];
+    if (i <= ncells && cell_start) cell_start[i] = start[i];
+}
+
+}  // namespace
+
+cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int n, int32_t *bsum,
+                            const DevStatus *ds, bool gated, cudaStream_t s) {
+    return launch_scan<int32_t>(in, out, n, bsum, ds, gated, s);
+}
+
+cudaError_t launch_bin(md_system *h, bool gated) {
+    int n = (int)h->n;
+    cudaStream_t s = h->stream;
+    int cur = h->cur;
+    prepare_abs_kernel<<<nblocks(n), kBlock, 0, s>>>(n, h->g, h->xr64[cur], h->cell, h->xabs,
+                                                     h->ds, gated);
+    zero_counts_kernel<<<nblocks(h->g.ncells), kBlock, 0, s>>>(h->g.ncells, h->cell_count,
+                                                               h->ds, gated);
+    bin_count_kernel<<<nblocks(n), kBlock, 0, s>>>(n, h->g, h->xabs, h->cell_count, h->new_cell,
+                                                   h->slot, h->ds, gated);
+    cudaError_t e = launch_scan_i32(h->cell_count, h->cell_start, h->g.ncells, h->scan_bsum,
+                                    h->ds, gated, s);
+    if (e != cudaSuccess) return e;
+    scatter_kernel<<<nblocks(n), kBlock, 0, s>>>(n, h->new_cell, h->slot, h->cell_start, h->orig,
+                                                 h->src, h->key, h->ds, gated);
+    cell_sort_kernel<<<nblocks(h->g.ncells), kBlock, 0, s>>>(h->g.ncells, h->cell_start, h->key,
+                                                             h->src, h->ds, gated);
+    copy_src_kernel<<<nblocks(n), kBlock, 0, s>>>(n, h->xabs, h->v, h->orig, h->tmp_abs,
+                                                  h->tmp_v, h->tmp_orig, h->ds, gated);
+    gather_kernel<<<nblocks(n), kBlock, 0, s>>>(n, h->g, h->src, h->new_cell, h->tmp_abs,
+                                                h->tmp_v, h->tmp_orig, h->xr64[cur], h->xq[cur],
+                                                h->xq_build, h->xabs, h->v, h->orig, h->cell,
+                                                h->ds, gated);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_cells(md_system *h, int32_t *cell_of_atom, int64_t *cell_start) {
+    int m = (int)(h->n > h->g.ncells + 1 ? h->n : h->g.ncells + 1);
+    export_cells_kernel<<<nblocks(m), kBlock, 0, h->stream>>>(
+        (int)h->n, h->g.ncells, h->orig, h->cell, h->cell_start, cell_of_atom, cell_start);
+    return cudaGetLastError();
+}
+
+}  // namespace mdg

@@ -1,0 +1,83 @@
+// k_common.cuh -- pieces shared by the force kernels: the argument block,
+// the fused velocity-Verlet epilogue (Sec. 3.3) and per-step bookkeeping.
+#pragma once
+
+#include "md_internal.cuh"
+
+namespace mdg {
+
+constexpr int kChunk = 32;
+
+struct ForceArgs {
+    int n, cap, step, rebuild_every;
+    const float4 *__restrict__ xq;
+    float4 *__restrict__ xq_out;
+    const double4 *__restrict__ xr;
+    double4 *__restrict__ xr_out;
+    const float4 *__restrict__ xq_build;
+    double *__restrict__ v;
+    double *__restrict__ f;
+    double *__restrict__ e_atom;
+    const uint32_t *__restrict__ nlist;
+    const int32_t *__restrict__ ncount;
+    double *__restrict__ rho;     // many-body: rho_i (Eq. 2)
+    float *__restrict__ dF32;     // many-body: F'(rho_i) in float32
+    double *__restrict__ dF64;    // many-body: F'(rho_i) in float64
+    DevStatus *ds;
+    Grid g;
+    ForceConsts fc;
+};
+
+// Fills a ForceArgs from the handle for the current double-buffer index.
+ForceArgs make_force_args(md_system *h);
+
+// Shared epilogue: kick (and drift) of atom i with its float64 force.
+template <int MODE>
+__device__ __forceinline__ void vv_epilogue(const ForceArgs &a, int i, double Fx, double Fy,
+                                            double Fz, float qw) {
+    const size_t n = (size_t)a.n;
+    const double hk = (MODE == FM_FUSED_FULL) ? a.fc.dt * a.fc.inv_m : 0.5 * a.fc.dt * a.fc.inv_m;
+    double vx = a.v[i] + hk * Fx;
+    double vy = a.v[n + i] + hk * Fy;
+    double vz = a.v[2 * n + i] + hk * Fz;
+    a.v[i] = vx;
+    a.v[n + i] = vy;
+    a.v[2 * n + i] = vz;
+    if (MODE == FM_FUSED_FULL) {
+        double4 r = a.xr[i];
+        r.x += a.fc.dt * vx;
+        r.y += a.fc.dt * vy;
+        r.z += a.fc.dt * vz;
+        a.xr_out[i] = r;
+        float4 q = make_float4((float)r.x, (float)r.y, (float)r.z, qw);
+        a.xq_out[i] = q;
+        float4 b = a.xq_build[i];
+        float ddx = q.x - b.x, ddy = q.y - b.y, ddz = q.z - b.z;
+        float d2 = ddx * ddx + ddy * ddy + ddz * ddz;
+        if (!(d2 <= 3.0e38f)) atomicCAS(&a.ds->status, 0, (int)MD_ERR_NONFINITE);
+        if (a.rebuild_every <= 0 && d2 > a.fc.half_skin2f) a.ds->rebuild = 1;
+    }
+}
+
+// Adds v over the converged lanes of the warp to the in-cutoff pair counter
+// (correct for any subset of lanes: each group's leader adds its own sum).
+__device__ __forceinline__ void count_pairs(DevStatus *ds, unsigned v) {
+    const unsigned m = __activemask();
+    const unsigned t = __reduce_add_sync(m, v);
+    if ((int)(threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&ds->pairs_cut, (unsigned long long)t);
+}
+
+template <int MODE>
+__device__ __forceinline__ void step_bookkeeping(const ForceArgs &a) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (MODE == FM_FUSED_FULL) {
+            a.ds->abs_fresh = 0;
+            int sb = a.ds->since_build + 1;
+            a.ds->since_build = sb;
+            if (a.rebuild_every > 0 && sb >= a.rebuild_every) a.ds->rebuild = 1;
+        }
+        if (MODE != FM_STORE) a.ds->steps_done = a.step;
+    }
+}
+
+}  // namespace mdg

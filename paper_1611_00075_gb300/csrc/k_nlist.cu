@@ -1,0 +1,229 @@
+// k_nlist.cu -- Verlet neighbour lists with skin (Sec. 2.1: lists are built
+// per cell from the 27 surrounding cells; Sec. 3.3: list radius
+// r_list = r_c + skin, rebuilt on the half-skin displacement rule).
+//
+// One thread per sorted atom scans the 27 cells around its cell.  The lanes
+// of a warp hold consecutive sorted atoms, so they walk the same cells and
+// their candidate loads coalesce in L1.  The acceptance test r^2 < r_list^2
+// is decided exactly as the float64 definition (minimum-image components,
+// dx*dx + dy*dy + dz*dz left to right, no fused multiply-add), but the
+// float64 arithmetic only runs for candidates whose float32 distance lies in
+// a thin band around r_list^2; outside the band the float32 result cannot
+// decide differently (its error bound is far below the band's half width).
+//
+// List layout: entry k of sorted atom i lives at
+//   nlist[(i / 32) * cap * 32 + k * 32 + i % 32]
+// so a warp reading its k-th entries touches one 128-byte line.  An entry is
+// (stencil cell s << 27) | sorted index j; s selects the cell shift
+// (dx, dy, dz) * w that turns cell-relative coordinates into the pair vector.
+#include "md_internal.cuh"
+
+namespace mdg {
+
+namespace {
+
+__device__ __forceinline__ bool chain_off(const DevStatus *ds, bool gated) {
+    return ds->status != 0 || (gated && ds->rebuild == 0);
+}
+
+template <bool PREFILTER, bool WRITE, bool HALF>
+__global__ void __launch_bounds__(kBlock)
+build_list_kernel(int n, Grid g, float lo, float hi, double rl2, const float4 *__restrict__ xq,
+                  const double4 *__restrict__ xabs, const int32_t *__restrict__ cell,
+                  const int32_t *__restrict__ start, uint32_t *__restrict__ nlist,
+                  int32_t *__restrict__ ncount, int cap, DevStatus *ds, bool gated) {
+    __shared__ float4 sh[kStencil];
+    if (threadIdx.x < kStencil) {
+        int s = threadIdx.x;
+        int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+        sh[s] = make_float4((float)(dx * g.w[0]), (float)(dy * g.w[1]), (float)(dz * g.w[2]),
+                            0.f);
+    }
+    __syncthreads();
+    if (chain_off(ds, gated)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int cnt = 0;
+    if (i < n) {
+    const int c = cell[i];
+    const int cx = c % g.nx, cy = (c / g.nx) % g.ny, cz = c / (g.nx * g.ny);
+    const float4 qi = xq[i];
+    const double4 ai = xabs[i];
+    const int myo = __float_as_int(qi.w);
+    const size_t base = (size_t)(i >> 5) * (size_t)cap * 32 + (size_t)(i & 31);
+    for (int dz = -1; dz <= 1; ++dz) {
+        int zz = cz + dz;
+        double shz = 0.0;
+        if (zz < 0) { zz += g.nz; shz = -g.L[2]; }
+        else if (zz >= g.nz) { zz -= g.nz; shz = g.L[2]; }
+        for (int dy = -1; dy <= 1; ++dy) {
+            int yy = cy + dy;
+            double shy = 0.0;
+            if (yy < 0) { yy += g.ny; shy = -g.L[1]; }
+            else if (yy >= g.ny) { yy -= g.ny; shy = g.L[1]; }
+            for (int dx = -1; dx <= 1; ++dx) {
+                int xx = cx + dx;
+                double shx = 0.0;
+                if (xx < 0) { xx += g.nx; shx = -g.L[0]; }
+                else if (xx >= g.nx) { xx -= g.nx; shx = g.L[0]; }
+                const int cn = (zz * g.ny + yy) * g.nx + xx;
+                const int s = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+                const float4 sf = sh[s];
+                const int b = start[cn], e = start[cn + 1];
+                for (int j = b; j < e; ++j) {
+                    if (j == i) continue;
+                    const float4 qj = xq[j];
+                    if (HALF && __float_as_int(qj.w) <= myo) continue;
+                    bool acc;
+                    float r2f = 0.f;
+                    if (PREFILTER) {
+                        float ex = (qj.x - qi.x) + sf.x;
+                        float ey = (qj.y - qi.y) + sf.y;
+                        float ez = (qj.z - qi.z) + sf.z;
+                        r2f = ex * ex + ey * ey + ez * ez;
+                    }
+                    if (PREFILTER && r2f < lo) {
+                        acc = true;
+                    } else if (PREFILTER && r2f >= hi) {
+                        acc = false;
+                    } else {
+                        // the float64 definition, operation for operation
+                        const double4 aj = xabs[j];
+                        double ddx = __dadd_rn(__dadd_rn(aj.x, -ai.x), shx);
+                        double ddy = __dadd_rn(__dadd_rn(aj.y, -ai.y), shy);
+                        double ddz = __dadd_rn(__dadd_rn(aj.z, -ai.z), shz);
+                        double r2 = __dmul_rn(ddx, ddx);
+                        r2 = __dadd_rn(r2, __dmul_rn(ddy, ddy));
+                        r2 = __dadd_rn(r2, __dmul_rn(ddz, ddz));
+                        acc = r2 < rl2;
+                    }
+                    if (acc) {
+                        if (WRITE && cnt < cap)
+                            nlist[base + (size_t)cnt * 32] = ((uint32_t)s << kIndexBits) | (uint32_t)j;
+                        ++cnt;
+                    }
+                }
+            }
+        }
+    }
+    ncount[i] = cnt;
+    atomicMax(&ds->max_count, cnt);
+    }
+    // every lane of the block reaches this point (no early return above)
+    unsigned long long tot = (unsigned long long)cnt;
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&ds->list_entries, tot);
+    if (WRITE && cnt > cap) atomicCAS(&ds->status, 0, (int)MD_ERR_LIST_OVERFLOW);
+}
+
+__global__ void reset_max_count_kernel(DevStatus *ds, bool gated) {
+    if (chain_off(ds, gated)) return;
+    ds->max_count = 0;
+    ds->list_entries = 0;
+}
+
+__global__ void finish_rebuild_kernel(DevStatus *ds, bool gated) {
+    if (chain_off(ds, gated)) return;
+    ds->rebuild = 0;
+    ds->since_build = 0;
+    ds->builds += 1;
+}
+
+// ---- export (parity and inspection) -----------------------------------------
+
+__global__ void export_rowcount_kernel(int n, int cap, int half, const int32_t *__restrict__ orig,
+                                       const int32_t *__restrict__ ncount,
+                                       const uint32_t *__restrict__ nlist,
+                                       int32_t *__restrict__ rowcnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int o = orig[i];
+    int cnt = min(ncount[i], cap);
+    int keep = cnt;
+    if (half) {
+        keep = 0;
+        size_t base = (size_t)(i >> 5) * (size_t)cap * 32 + (size_t)(i & 31);
+        for (int k = 0; k < cnt; ++k) {
+            int j = (int)(nlist[base + (size_t)k * 32] & kIndexMask);
+            keep += (orig[j] > o);
+        }
+    }
+    rowcnt[o] = keep;
+}
+
+__global__ void export_fill_kernel(int n, int cap, int half, const int32_t *__restrict__ orig,
+                                   const int32_t *__restrict__ ncount,
+                                   const uint32_t *__restrict__ nlist,
+                                   const int32_t *__restrict__ rowstart, int64_t *offsets,
+                                   int32_t *__restrict__ ids) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int o = orig[i];
+    int cnt = min(ncount[i], cap);
+    size_t base = (size_t)(i >> 5) * (size_t)cap * 32 + (size_t)(i & 31);
+    int64_t p0 = rowstart[o];
+    int64_t p = p0;
+    for (int k = 0; k < cnt; ++k) {
+        int j = (int)(nlist[base + (size_t)k * 32] & kIndexMask);
+        int oj = orig[j];
+        if (!half || oj > o) ids[p++] = oj;
+    }
+    for (int64_t a = p0 + 1; a < p; ++a) {  // ascending original id
+        int kv = ids[a];
+        int64_t q = a - 1;
+        while (q >= p0 && ids[q] > kv) {
+            ids[q + 1] = ids[q];
+            --q;
+        }
+        ids[q + 1] = kv;
+    }
+    offsets[o] = p0;
+    if (o == n - 1) offsets[n] = rowstart[n];
+}
+
+}  // namespace
+
+cudaError_t launch_build_list(md_system *h, bool write, bool gated) {
+    int n = (int)h->n;
+    cudaStream_t s = h->stream;
+    int cur = h->cur;
+    const bool prefilter = (h->p.precision == MD_MIXED);
+    const bool half = (h->p.force_variant != MD_FORCE_FULL);
+    reset_max_count_kernel<<<1, 1, 0, s>>>(h->ds, gated);
+#define MDG_LIST(PF, WR, HF)                                                                    \
+    build_list_kernel<PF, WR, HF><<<nblocks(n), kBlock, 0, s>>>(                                \
+        n, h->g, h->list_lo, h->list_hi, h->rl2, h->xq[cur], h->xabs, h->cell, h->cell_start, \
+        h->nlist, h->ncount, h->cap, h->ds, gated)
+    if (prefilter) {
+        if (write) { if (half) MDG_LIST(true, true, true); else MDG_LIST(true, true, false); }
+        else { if (half) MDG_LIST(true, false, true); else MDG_LIST(true, false, false); }
+    } else {
+        if (write) { if (half) MDG_LIST(false, true, true); else MDG_LIST(false, true, false); }
+        else { if (half) MDG_LIST(false, false, true); else MDG_LIST(false, false, false); }
+    }
+#undef MDG_LIST
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_rebuild(md_system *h, bool gated) {
+    finish_rebuild_kernel<<<1, 1, 0, h->stream>>>(h->ds, gated);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_list(md_system *h, int half, int64_t *offsets, int32_t *ids,
+                               int64_t *tmp) {
+    // tmp: scratch of at least 2 * (n + 1) + 64 int32 words, provided by the caller
+    int n = (int)h->n;
+    int32_t *rowcnt = reinterpret_cast<int32_t *>(tmp);
+    int32_t *rowstart = rowcnt + (n + 1);
+    export_rowcount_kernel<<<nblocks(n), kBlock, 0, h->stream>>>(n, h->cap, half, h->orig,
+                                                                  h->ncount, h->nlist, rowcnt);
+    cudaError_t e = launch_scan_i32(rowcnt, rowstart, n, h->scan_bsum, h->ds, false, h->stream);
+    if (e != cudaSuccess) return e;
+    if (ids != nullptr)
+        export_fill_kernel<<<nblocks(n), kBlock, 0, h->stream>>>(n, h->cap, half, h->orig,
+                                                                  h->ncount, h->nlist, rowstart,
+                                                                  offsets, ids);
+    return cudaGetLastError();
+}
+
+}  // namespace mdg

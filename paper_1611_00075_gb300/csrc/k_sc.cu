@@ -1,0 +1,328 @@
+// k_sc.cu -- Sutton-Chen many-body forces in the paper's three steps
+// (Sec. 3.1): a pair pass for the localization function rho_i (Eq. 2), an
+// atom pass for the embedding function, and a pair pass for the pair term
+// and the forces.
+//
+// Sutton-Chen instance of Eq. 1:
+//   Phi(r) = eps (a/r)^n,  psi(r) = (a/r)^m,  F(rho) = -eps c sqrt(rho),
+//   truncated (no shift) at r_c.  Differentiating U gives the force on i
+//   f_i = -sum_j [Phi'(r) + (F'(rho_i) + F'(rho_j)) psi'(r)] (r_i - r_j) / r
+//       = -sum_j (n Phi + m (F'_i + F'_j) psi) / r^2 * d,   d = r_j - r_i
+//   since Phi' = -n Phi / r and psi' = -m psi / r.
+//
+// The second step (atom loop: F(rho_i), F'(rho_i)) only needs rho_i, so it
+// runs as the epilogue of the density pass in the thread that owns atom i;
+// sc_embed() below is that step.  The third step gathers F'_j per pair.
+//
+// Precision as for Lennard-Jones: MIXED computes pair terms in float32 and
+// sums rho and the forces in float64 over float32 chunks; F'(rho) feeds the
+// float32 pair terms as float32.  The embedding energy is float64.
+#include "k_common.cuh"
+
+namespace mdg {
+
+namespace {
+
+template <int K>
+__device__ __forceinline__ float cpow(float x) {
+    float r = 1.f, b = x;
+    int k = K;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+        if (k & 1) r *= b;
+        k >>= 1;
+        if (k) b *= b;
+    }
+    return r;
+}
+__device__ __forceinline__ float rpow(float x, int k) {
+    float r = 1.f;
+    while (k) {
+        if (k & 1) r *= x;
+        k >>= 1;
+        x *= x;
+    }
+    return r;
+}
+__device__ __forceinline__ double rpowd(double x, int k) {
+    double r = 1.0;
+    while (k) {
+        if (k & 1) r *= x;
+        k >>= 1;
+        x *= x;
+    }
+    return r;
+}
+
+// (a/r)^K from s = (a/r)^2 and ar = a/r (ar only used for odd K).
+template <int K>
+__device__ __forceinline__ float ar_pow(float s, float ar) {
+    if (K % 2 == 0) return cpow<K / 2>(s);
+    return cpow<K / 2>(s) * ar;
+}
+
+// The atom step of Sec. 3.1 for Sutton-Chen: F'(rho) = -eps c / (2 sqrt(rho)).
+__device__ __forceinline__ float sc_embed_deriv_f32(double rho, float ec) {
+    return rho > 0.0 ? -0.5f * ec * rsqrtf((float)rho) : 0.f;
+}
+__device__ __forceinline__ double sc_embed_deriv_f64(double rho, double ec) {
+    return rho > 0.0 ? -0.5 * ec / sqrt(rho) : 0.0;
+}
+
+template <int ME>
+__global__ void __launch_bounds__(kBlock) sc_density_mixed(ForceArgs a) {
+    __shared__ float4 sh[kStencil];
+    if (threadIdx.x < kStencil) {
+        int s = threadIdx.x;
+        int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+        sh[s] = make_float4((float)(dx * a.g.w[0]), (float)(dy * a.g.w[1]),
+                            (float)(dz * a.g.w[2]), 0.f);
+    }
+    __syncthreads();
+    if (a.ds->status != 0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const float4 qi = a.xq[i];
+    const int cnt = min(a.ncount[i], a.cap);
+    const uint32_t *lp = a.nlist + (size_t)(i >> 5) * (size_t)a.cap * 32 + (size_t)(i & 31);
+    const float rc2 = a.fc.rc2f, af = a.fc.sc_af, a2 = af * af;
+    const int m = a.fc.sc_m;
+    double R = 0.0;
+    for (int k0 = 0; k0 < cnt; k0 += kChunk) {
+        const int k1 = min(k0 + kChunk, cnt);
+        float r = 0.f;
+        for (int k = k0; k < k1; ++k) {
+            const uint32_t ent = __ldg(lp + (size_t)k * 32);
+            const float4 qj = __ldg(a.xq + (ent & kIndexMask));
+            const float4 sf = sh[ent >> kIndexBits];
+            const float ex = (qj.x - qi.x) + sf.x;
+            const float ey = (qj.y - qi.y) + sf.y;
+            const float ez = (qj.z - qi.z) + sf.z;
+            const float r2 = ex * ex + ey * ey + ez * ez;
+            if (r2 < rc2) {
+                const float s = a2 * __fdividef(1.0f, r2);
+                float psi;
+                if (ME > 0) psi = ar_pow<ME>(s, (ME & 1) ? af * rsqrtf(r2) : 0.f);
+                else psi = (m & 1) ? rpow(s, m / 2) * af * rsqrtf(r2) : rpow(s, m / 2);
+                r += psi;
+            }
+        }
+        R += (double)r;
+    }
+    a.rho[i] = R;
+    a.dF32[i] = sc_embed_deriv_f32(R, a.fc.sc_ecf);
+}
+
+__global__ void __launch_bounds__(kBlock) sc_density_fp64(ForceArgs a) {
+    __shared__ double3 sh[kStencil];
+    if (threadIdx.x < kStencil) {
+        int s = threadIdx.x;
+        int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+        sh[s] = make_double3(dx * a.g.w[0], dy * a.g.w[1], dz * a.g.w[2]);
+    }
+    __syncthreads();
+    if (a.ds->status != 0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const double4 ri = a.xr[i];
+    const int cnt = min(a.ncount[i], a.cap);
+    const uint32_t *lp = a.nlist + (size_t)(i >> 5) * (size_t)a.cap * 32 + (size_t)(i & 31);
+    const double rc2 = a.fc.rc2, A = a.fc.sc_a;
+    const int m = a.fc.sc_m;
+    double R = 0.0;
+    for (int k = 0; k < cnt; ++k) {
+        const uint32_t ent = __ldg(lp + (size_t)k * 32);
+        const double4 rj = a.xr[ent & kIndexMask];
+        const double3 sd = sh[ent >> kIndexBits];
+        const double ex = (rj.x - ri.x) + sd.x;
+        const double ey = (rj.y - ri.y) + sd.y;
+        const double ez = (rj.z - ri.z) + sd.z;
+        const double r2 = ex * ex + ey * ey + ez * ez;
+        if (r2 < rc2) R += rpowd(A / sqrt(r2), m);
+    }
+    a.rho[i] = R;
+    const double d = sc_embed_deriv_f64(R, a.fc.sc_ec);
+    a.dF64[i] = d;
+    a.dF32[i] = (float)d;
+}
+
+template <int MODE, bool ENERGY, int NE, int ME>
+__global__ void __launch_bounds__(kBlock) sc_force_mixed(ForceArgs a, int store_f) {
+    __shared__ float4 sh[kStencil];
+    if (threadIdx.x < kStencil) {
+        int s = threadIdx.x;
+        int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+        sh[s] = make_float4((float)(dx * a.g.w[0]), (float)(dy * a.g.w[1]),
+                            (float)(dz * a.g.w[2]), 0.f);
+    }
+    __syncthreads();
+    if (a.ds->status != 0) return;
+    step_bookkeeping<MODE>(a);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const float4 qi = a.xq[i];
+    const float dFi = a.dF32[i];
+    const int cnt = min(a.ncount[i], a.cap);
+    const uint32_t *lp = a.nlist + (size_t)(i >> 5) * (size_t)a.cap * 32 + (size_t)(i & 31);
+    const float rc2 = a.fc.rc2f, af = a.fc.sc_af, a2 = af * af, epsf = a.fc.sc_epsf;
+    const int nexp = a.fc.sc_n, mexp = a.fc.sc_m;
+    const float nf = (float)(NE > 0 ? NE : nexp), mf = (float)(ME > 0 ? ME : mexp);
+    double Fx = 0.0, Fy = 0.0, Fz = 0.0, E = 0.0;
+    unsigned npair = 0;
+    for (int k0 = 0; k0 < cnt; k0 += kChunk) {
+        const int k1 = min(k0 + kChunk, cnt);
+        float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+        for (int k = k0; k < k1; ++k) {
+            const uint32_t ent = __ldg(lp + (size_t)k * 32);
+            const int j = (int)(ent & kIndexMask);
+            const float4 qj = __ldg(a.xq + j);
+            const float4 sf = sh[ent >> kIndexBits];
+            const float ex = (qj.x - qi.x) + sf.x;
+            const float ey = (qj.y - qi.y) + sf.y;
+            const float ez = (qj.z - qi.z) + sf.z;
+            const float r2 = ex * ex + ey * ey + ez * ez;
+            if (r2 < rc2) {
+                const float r2i = __fdividef(1.0f, r2);
+                const float s = a2 * r2i;
+                const bool odd = (NE > 0) ? ((NE | ME) & 1) : ((nexp | mexp) & 1);
+                const float ar = odd ? af * rsqrtf(r2) : 0.f;
+                float Phi, psi;
+                if (NE > 0) {
+                    Phi = epsf * ar_pow<NE>(s, ar);
+                    psi = ar_pow<ME>(s, ar);
+                } else {
+                    Phi = epsf * ((nexp & 1) ? rpow(s, nexp / 2) * ar : rpow(s, nexp / 2));
+                    psi = (mexp & 1) ? rpow(s, mexp / 2) * ar : rpow(s, mexp / 2);
+                }
+                const float dFj = __ldg(a.dF32 + j);
+                const float fs = (nf * Phi + mf * (dFi + dFj) * psi) * r2i;
+                fx -= fs * ex;
+                fy -= fs * ey;
+                fz -= fs * ez;
+                if (ENERGY) {
+                    e += Phi;
+                    ++npair;
+                }
+            }
+        }
+        Fx += (double)fx;
+        Fy += (double)fy;
+        Fz += (double)fz;
+        if (ENERGY) E += (double)e;
+    }
+    const size_t n = (size_t)a.n;
+    if (MODE == FM_STORE || store_f) {
+        a.f[i] = Fx;
+        a.f[n + i] = Fy;
+        a.f[2 * n + i] = Fz;
+    }
+    if (ENERGY) {
+        a.e_atom[i] = 0.5 * E - a.fc.sc_ec * sqrt(a.rho[i]);
+        count_pairs(a.ds, npair);
+    }
+    if (MODE != FM_STORE) vv_epilogue<MODE>(a, i, Fx, Fy, Fz, qi.w);
+}
+
+template <int MODE, bool ENERGY>
+__global__ void __launch_bounds__(kBlock) sc_force_fp64(ForceArgs a, int store_f) {
+    __shared__ double3 sh[kStencil];
+    if (threadIdx.x < kStencil) {
+        int s = threadIdx.x;
+        int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+        sh[s] = make_double3(dx * a.g.w[0], dy * a.g.w[1], dz * a.g.w[2]);
+    }
+    __syncthreads();
+    if (a.ds->status != 0) return;
+    step_bookkeeping<MODE>(a);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const double4 ri = a.xr[i];
+    const double dFi = a.dF64[i];
+    const int cnt = min(a.ncount[i], a.cap);
+    const uint32_t *lp = a.nlist + (size_t)(i >> 5) * (size_t)a.cap * 32 + (size_t)(i & 31);
+    const double rc2 = a.fc.rc2, A = a.fc.sc_a, eps = a.fc.sc_eps;
+    const int nexp = a.fc.sc_n, mexp = a.fc.sc_m;
+    double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0;
+    unsigned npair = 0;
+    for (int k = 0; k < cnt; ++k) {
+        const uint32_t ent = __ldg(lp + (size_t)k * 32);
+        const int j = (int)(ent & kIndexMask);
+        const double4 rj = a.xr[j];
+        const double3 sd = sh[ent >> kIndexBits];
+        const double ex = (rj.x - ri.x) + sd.x;
+        const double ey = (rj.y - ri.y) + sd.y;
+        const double ez = (rj.z - ri.z) + sd.z;
+        const double r2 = ex * ex + ey * ey + ez * ez;
+        if (r2 < rc2) {
+            const double ar = A / sqrt(r2);
+            const double Phi = eps * rpowd(ar, nexp);
+            const double psi = rpowd(ar, mexp);
+            const double fs = (nexp * Phi + mexp * (dFi + a.dF64[j]) * psi) / r2;
+            fx -= fs * ex;
+            fy -= fs * ey;
+            fz -= fs * ez;
+            if (ENERGY) {
+                e += Phi;
+                ++npair;
+            }
+        }
+    }
+    const size_t n = (size_t)a.n;
+    if (MODE == FM_STORE || store_f) {
+        a.f[i] = fx;
+        a.f[n + i] = fy;
+        a.f[2 * n + i] = fz;
+    }
+    if (ENERGY) {
+        a.e_atom[i] = 0.5 * e - a.fc.sc_ec * sqrt(a.rho[i]);
+        count_pairs(a.ds, npair);
+    }
+    if (MODE != FM_STORE) {
+        const float4 qi = a.xq[i];
+        vv_epilogue<MODE>(a, i, fx, fy, fz, qi.w);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_sc_density(md_system *h) {
+    ForceArgs a = make_force_args(h);
+    const int nb = nblocks(a.n);
+    if (h->p.precision == MD_MIXED) {
+        if (a.fc.sc_m == 6) sc_density_mixed<6><<<nb, kBlock, 0, h->stream>>>(a);
+        else sc_density_mixed<0><<<nb, kBlock, 0, h->stream>>>(a);
+    } else {
+        sc_density_fp64<<<nb, kBlock, 0, h->stream>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sc_force(md_system *h, int mode, bool energy, bool store_f) {
+    ForceArgs a = make_force_args(h);
+    const int nb = nblocks(a.n);
+    const int sf = store_f ? 1 : 0;
+    cudaStream_t s = h->stream;
+    if (h->p.precision == MD_MIXED) {
+        const bool cu = (a.fc.sc_n == 9 && a.fc.sc_m == 6);
+#define MDG_SC(M, E)                                                                    \
+    do {                                                                                \
+        if (cu) sc_force_mixed<M, E, 9, 6><<<nb, kBlock, 0, s>>>(a, sf);                \
+        else sc_force_mixed<M, E, 0, 0><<<nb, kBlock, 0, s>>>(a, sf);                   \
+    } while (0)
+        switch (mode) {
+            case FM_STORE: if (energy) MDG_SC(FM_STORE, true); else MDG_SC(FM_STORE, false); break;
+            case FM_FUSED_FULL: if (energy) MDG_SC(FM_FUSED_FULL, true); else MDG_SC(FM_FUSED_FULL, false); break;
+            default: if (energy) MDG_SC(FM_FUSED_HALF, true); else MDG_SC(FM_FUSED_HALF, false); break;
+        }
+#undef MDG_SC
+    } else {
+        switch (mode) {
+            case FM_STORE: if (energy) sc_force_fp64<FM_STORE, true><<<nb, kBlock, 0, s>>>(a, sf); else sc_force_fp64<FM_STORE, false><<<nb, kBlock, 0, s>>>(a, sf); break;
+            case FM_FUSED_FULL: if (energy) sc_force_fp64<FM_FUSED_FULL, true><<<nb, kBlock, 0, s>>>(a, sf); else sc_force_fp64<FM_FUSED_FULL, false><<<nb, kBlock, 0, s>>>(a, sf); break;
+            default: if (energy) sc_force_fp64<FM_FUSED_HALF, true><<<nb, kBlock, 0, s>>>(a, sf); else sc_force_fp64<FM_FUSED_HALF, false><<<nb, kBlock, 0, s>>>(a, sf); break;
+        }
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mdg

@@ -1,0 +1,612 @@
+// md_api.cu -- the C ABI (include/md_gb300.h): argument checks, device
+// memory, and the order in which kernels are enqueued for each call.
+//
+// Time stepping (Sec. 3.3, velocity-Verlet): the first half kick and drift of
+// a run use the forces of the previous evaluation; each later force kernel
+// applies the closing half kick of its step merged with the opening half kick
+// of the next one, then drifts; the last step only applies its closing half
+// kick.  Before every force evaluation a rebuild chain (binning + list) is
+// enqueued that runs only when the device rebuild flag is set, so the host
+// never waits for the half-skin test.  md_step reads the device status once
+// at the end; a list overflow found there is repaired and the remaining steps
+// are re-enqueued from the step that stopped.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "md_internal.cuh"
+
+using namespace mdg;
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+md_status fail(md_system *h, md_status st, const std::string &msg) {
+    if (h) h->last_error = msg;
+    else g_thread_error = msg;
+    return st;
+}
+
+#define MD_CK(call)                                                                        \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(h, MD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+bool is_int_valued(double x, int lo, int hi) {
+    return std::isfinite(x) && std::floor(x) == x && x >= lo && x <= hi;
+}
+
+md_status check_params(const md_params *p, int64_t n, const double *box, std::string *why) {
+    auto bad = [&](const char *m) { *why = m; return MD_ERR_INVALID; };
+    if (n < 1) return bad("n must be >= 1");
+    if (n >= kMaxAtoms) return bad("n must be below 2^27");
+    if (p->potential != MD_POT_LJ && p->potential != MD_POT_SC) return bad("unknown potential");
+    if (p->precision != MD_FP64 && p->precision != MD_MIXED) return bad("unknown precision");
+    if (p->force_variant < MD_FORCE_FULL || p->force_variant > MD_FORCE_HALF_ATOMIC)
+        return bad("unknown force_variant");
+    if (p->scheduler < MD_SCHED_GRID || p->scheduler > MD_SCHED_DYNAMIC)
+        return bad("unknown scheduler");
+    if (p->rebuild_every < 0) return bad("rebuild_every must be >= 0");
+    if (p->max_neighbors < 0) return bad("max_neighbors must be >= 0");
+    if (!(p->rc > 0) || !(p->skin >= 0) || !(p->dt > 0) || !(p->mass > 0) || !(p->eps > 0) ||
+        !(p->sigma > 0) || !std::isfinite(p->rc + p->skin + p->dt + p->mass + p->eps + p->sigma))
+        return bad("rc, dt, mass, eps, sigma must be > 0 and skin >= 0");
+    if (p->potential == MD_POT_SC) {
+        if (!(p->c > 0) || !std::isfinite(p->c)) return bad("Sutton-Chen c must be > 0");
+        if (!is_int_valued(p->n_exp, 1, 30) || !is_int_valued(p->m_exp, 1, 30))
+            return bad("Sutton-Chen n and m must be integers in [1, 30]");
+    }
+    const double rl = p->rc + p->skin;
+    double ncells = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        if (!(box[d] > 0) || !std::isfinite(box[d])) return bad("box sides must be > 0");
+        double q = std::floor(box[d] / rl);
+        if (q < 3) return bad("each box side must hold at least 3 list radii (rc + skin)");
+        ncells *= q;
+    }
+    if (ncells > 2.0e9) return bad("too many cells");
+    return MD_OK;
+}
+
+void free_all(md_system *h) {
+    auto F = [](void *p) { if (p) cudaFree(p); };
+    for (int b = 0; b < 2; ++b) { F(h->xr64[b]); F(h->xq[b]); }
+    F(h->xq_build); F(h->xabs); F(h->v); F(h->f); F(h->e_atom); F(h->orig); F(h->cell);
+    F(h->cell_start); F(h->cell_count); F(h->new_cell); F(h->slot); F(h->src); F(h->key);
+    F(h->scan_bsum); F(h->tmp_abs); F(h->tmp_v); F(h->tmp_orig); F(h->nlist); F(h->ncount);
+    F(h->rho); F(h->dF32); F(h->dF64); F(h->partials); F(h->red_out); F(h->ds);
+    F(h->exp_tmp);
+    if (h->ds_host) cudaFreeHost(h->ds_host);
+    if (h->red_host) cudaFreeHost(h->red_host);
+}
+
+cudaError_t alloc_list(md_system *h, int cap) {
+    if (h->nlist) cudaFree(h->nlist);
+    h->nlist = nullptr;
+    h->cap = cap;
+    h->nlist_entries = (size_t)((h->n + 31) / 32) * 32 * (size_t)cap;
+    return dalloc(&h->nlist, h->nlist_entries);
+}
+
+int cap_for(int max_count) {
+    int c = max_count + max_count / 4 + 8;
+    return (c + 7) & ~7;
+}
+
+md_status read_status(md_system *h) {
+    MD_CK(cudaMemcpyAsync(h->ds_host, h->ds, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                          h->stream));
+    MD_CK(cudaStreamSynchronize(h->stream));
+    return MD_OK;
+}
+
+md_status clear_status(md_system *h) {
+    MD_CK(cudaMemsetAsync(&h->ds->status, 0, sizeof(int), h->stream));
+    return MD_OK;
+}
+
+// ---- per-launch timing: an event after each interval, summed at sync -------
+enum { K_REBUILD = 0, K_FORCE = 1, K_INTEGRATE = 2, K_OTHER = 3 };
+
+cudaError_t mark(md_system *h, int kind) {
+    if (!h->timing) return cudaSuccess;
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        h->ev_pool.push_back(e);
+        h->ev_kind.push_back(K_OTHER);
+    }
+    h->ev_kind[h->ev_used] = kind;
+    return cudaEventRecord(h->ev_pool[h->ev_used++], h->stream);
+}
+
+// after a synchronize: accumulate intervals ev[k-1] -> ev[k] by the kind of ev[k]
+void harvest(md_system *h) {
+    for (size_t k = 1; k < h->ev_used; ++k) {
+        float ms = 0.f;
+        if (h->ev_kind[k] >= 0 && cudaEventElapsedTime(&ms, h->ev_pool[k - 1], h->ev_pool[k]) == cudaSuccess) {
+            h->ms_kind[h->ev_kind[k]] += ms;
+            h->n_kind[h->ev_kind[k]] += 1;
+        }
+    }
+    h->ev_used = 0;
+}
+
+// Rebuild chain enqueued before a force evaluation.  gated: runs only if the
+// device flag asks for it.
+md_status enqueue_rebuild(md_system *h, bool gated) {
+    MD_CK(launch_bin(h, gated));
+    MD_CK(launch_build_list(h, true, gated));
+    MD_CK(launch_finish_rebuild(h, gated));
+    h->launches += 13;
+    MD_CK(mark(h, K_REBUILD));
+    return MD_OK;
+}
+
+// Host-driven rebuild with capacity repair (explicit calls and create).
+md_status rebuild_now(md_system *h, bool size_from_count) {
+    MD_CK(launch_bin(h, false));
+    if (size_from_count || h->nlist == nullptr) {
+        MD_CK(launch_build_list(h, false, false));
+        md_status st = read_status(h);
+        if (st != MD_OK) return st;
+        if (h->ds_host->status != 0)
+            return fail(h, (md_status)h->ds_host->status, "device error during list count");
+        int cap = h->p.max_neighbors > 0 ? h->p.max_neighbors : cap_for(h->ds_host->max_count);
+        cap = std::max(cap, 8);
+        if (cap != h->cap || h->nlist == nullptr) MD_CK(alloc_list(h, cap));
+    }
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        MD_CK(launch_build_list(h, true, false));
+        md_status st = read_status(h);
+        if (st != MD_OK) return st;
+        if (h->ds_host->status == 0) break;
+        if (h->ds_host->status != MD_ERR_LIST_OVERFLOW)
+            return fail(h, (md_status)h->ds_host->status, "device error during list build");
+        if (h->p.max_neighbors > 0)
+            return fail(h, MD_ERR_LIST_OVERFLOW, "neighbour count exceeds max_neighbors");
+        st = clear_status(h);
+        if (st != MD_OK) return st;
+        MD_CK(alloc_list(h, cap_for(h->ds_host->max_count)));
+    }
+    MD_CK(launch_finish_rebuild(h, false));
+    h->list_valid = true;
+    h->forces_valid = false;
+    return MD_OK;
+}
+
+md_status enqueue_forces(md_system *h, int mode, bool energy, bool store_f) {
+    if (h->p.potential == MD_POT_SC) {
+        MD_CK(launch_sc_density(h));
+        MD_CK(launch_sc_force(h, mode, energy, store_f));
+        h->launches += 2;
+    } else {
+        MD_CK(launch_lj(h, mode, energy, store_f));
+        h->launches += 1;
+    }
+    MD_CK(mark(h, K_FORCE));
+    return MD_OK;
+}
+
+// Forces at the current positions (rebuilding first if the flag is set).
+md_status forces_now(md_system *h, bool energy) {
+    if (h->timing) {
+        h->ev_used = 0;
+        MD_CK(mark(h, -1));
+    }
+    md_status st = enqueue_rebuild(h, true);
+    if (st != MD_OK) return st;
+    st = enqueue_forces(h, FM_STORE, energy, true);
+    if (st != MD_OK) return st;
+    st = read_status(h);
+    if (st != MD_OK) return st;
+    if (h->ds_host->status == MD_ERR_LIST_OVERFLOW) {
+        // the gated rebuild overflowed: repair on the host and evaluate again
+        st = clear_status(h);
+        if (st != MD_OK) return st;
+        st = rebuild_now(h, true);
+        if (st != MD_OK) return st;
+        st = enqueue_forces(h, FM_STORE, energy, true);
+        if (st != MD_OK) return st;
+        st = read_status(h);
+        if (st != MD_OK) return st;
+    }
+    if (h->timing) harvest(h);
+    if (h->ds_host->status != 0)
+        return fail(h, (md_status)h->ds_host->status, "device error during force evaluation");
+    h->forces_valid = true;
+    h->list_valid = true;
+    return MD_OK;
+}
+
+__global__ void begin_steps_kernel(DevStatus *ds, int base) { ds->steps_done = base; }
+
+}  // namespace
+
+extern "C" {
+
+md_status md_create(md_system **out, const md_params *p, int64_t n, const double *box3_host,
+                    const double *pos_dev, const double *vel_dev, void *cuda_stream) {
+    md_system *h = nullptr;
+    if (!out || !p || !box3_host || !pos_dev)
+        return fail(nullptr, MD_ERR_INVALID, "md_create: null argument");
+    *out = nullptr;
+    std::string why;
+    if (check_params(p, n, box3_host, &why) != MD_OK)
+        return fail(nullptr, MD_ERR_INVALID, "md_create: " + why);
+    if (p->force_variant != MD_FORCE_FULL && p->potential == MD_POT_SC)
+        return fail(nullptr, MD_ERR_INVALID, "md_create: half lists are built for Lennard-Jones only");
+    if (p->force_variant != MD_FORCE_FULL)
+        return fail(nullptr, MD_ERR_INVALID, "md_create: half-list force kernels are not built yet");
+    if (p->scheduler != MD_SCHED_GRID)
+        return fail(nullptr, MD_ERR_INVALID, "md_create: persistent schedulers are not built yet");
+    h = new (std::nothrow) md_system();
+    if (!h) return fail(nullptr, MD_ERR_OOM, "md_create: host allocation failed");
+    h->p = *p;
+    h->n = n;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->r_list = p->rc + p->skin;
+    h->rl2 = h->r_list * h->r_list;
+    h->list_lo = (float)(h->rl2 * (1.0 - 1.0 / 16384.0));
+    h->list_hi = (float)(h->rl2 * (1.0 + 1.0 / 16384.0));
+    Grid &g = h->g;
+    int nc[3];
+    for (int d = 0; d < 3; ++d) {
+        nc[d] = (int)std::floor(box3_host[d] / h->r_list);
+        g.L[d] = box3_host[d];
+        g.w[d] = box3_host[d] / nc[d];
+        g.inv_w[d] = (double)nc[d] / box3_host[d];
+    }
+    g.nx = nc[0]; g.ny = nc[1]; g.nz = nc[2];
+    g.ncells = nc[0] * nc[1] * nc[2];
+    ForceConsts &fc = h->fc;
+    const double s2 = p->sigma * p->sigma, rc2 = p->rc * p->rc;
+    const double sr6 = std::pow(s2 / rc2, 3);
+    fc.rc2 = rc2; fc.sig2 = s2; fc.eps4 = 4 * p->eps; fc.eps48 = 48 * p->eps;
+    fc.shift = 4 * p->eps * (sr6 * sr6 - sr6);
+    fc.rc2f = (float)rc2; fc.sig2f = (float)s2; fc.eps4f = (float)fc.eps4;
+    fc.eps48f = (float)fc.eps48; fc.shiftf = (float)fc.shift;
+    fc.sc_a = p->sigma; fc.sc_eps = p->eps; fc.sc_ec = p->eps * p->c;
+    fc.sc_af = (float)p->sigma; fc.sc_epsf = (float)p->eps; fc.sc_ecf = (float)(p->eps * p->c);
+    fc.sc_n = (int)p->n_exp; fc.sc_m = (int)p->m_exp;
+    fc.dt = p->dt; fc.inv_m = 1.0 / p->mass;
+    fc.half_skin2f = (float)(0.25 * p->skin * p->skin);
+
+    const size_t N = (size_t)n, C = (size_t)g.ncells;
+    const size_t scan_len = std::max(N, C + 1) / (kBlock * 8) + 4;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    for (int b = 0; b < 2; ++b) { A(dalloc(&h->xr64[b], N)); A(dalloc(&h->xq[b], N)); }
+    A(dalloc(&h->xq_build, N)); A(dalloc(&h->xabs, N)); A(dalloc(&h->v, 3 * N));
+    A(dalloc(&h->f, 3 * N)); A(dalloc(&h->e_atom, N)); A(dalloc(&h->orig, N));
+    A(dalloc(&h->cell, N)); A(dalloc(&h->cell_start, C + 1)); A(dalloc(&h->cell_count, C));
+    A(dalloc(&h->new_cell, N)); A(dalloc(&h->slot, N)); A(dalloc(&h->src, N));
+    A(dalloc(&h->key, N)); A(dalloc(&h->scan_bsum, scan_len)); A(dalloc(&h->tmp_abs, N));
+    A(dalloc(&h->tmp_v, 3 * N)); A(dalloc(&h->tmp_orig, N)); A(dalloc(&h->ncount, N));
+    if (p->potential == MD_POT_SC) {
+        A(dalloc(&h->rho, N)); A(dalloc(&h->dF32, N)); A(dalloc(&h->dF64, N));
+    }
+    h->nblocks_n = nblocks(n);
+    A(dalloc(&h->partials, (size_t)h->nblocks_n + 1)); A(dalloc(&h->red_out, 4));
+    A(dalloc(&h->ds, 1));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->ds_host, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->red_host, 4 * sizeof(double));
+    if (e != cudaSuccess) {
+        md_status st = (e == cudaErrorMemoryAllocation) ? MD_ERR_OOM : MD_ERR_CUDA;
+        std::string m = std::string("md_create: allocation failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        free_all(h);
+        delete h;
+        return fail(nullptr, st, m);
+    }
+    md_status st = MD_OK;
+    auto step = [&](cudaError_t r, const char *what) {
+        if (st == MD_OK && r != cudaSuccess)
+            st = fail(h, MD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(r));
+    };
+    step(cudaMemsetAsync(h->ds, 0, sizeof(DevStatus), h->stream), "memset status");
+    step(cudaMemsetAsync(h->f, 0, 3 * N * sizeof(double), h->stream), "memset f");
+    step(cudaMemsetAsync(h->e_atom, 0, N * sizeof(double), h->stream), "memset e");
+    if (!vel_dev) step(cudaMemsetAsync(h->v, 0, 3 * N * sizeof(double), h->stream), "memset v");
+    step(launch_load_state(h, pos_dev, vel_dev), "load_state");
+    if (st == MD_OK) st = rebuild_now(h, true);
+    if (st == MD_OK) st = forces_now(h, false);
+    if (st != MD_OK) {
+        g_thread_error = "md_create: " + h->last_error;
+        free_all(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return MD_OK;
+}
+
+md_status md_bin_cells(md_system *h) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_bin_cells: null handle");
+    MD_CK(launch_bin(h, false));
+    MD_CK(launch_set_rebuild(h));  // list entries now refer to the old order
+    h->list_valid = false;
+    h->forces_valid = false;
+    return MD_OK;
+}
+
+md_status md_build_neighbors(md_system *h) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_build_neighbors: null handle");
+    return rebuild_now(h, false);
+}
+
+md_status md_forces(md_system *h) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_forces: null handle");
+    return forces_now(h, false);
+}
+
+md_status md_step(md_system *h, int64_t nsteps) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_step: null handle");
+    if (nsteps < 0) return fail(h, MD_ERR_INVALID, "md_step: nsteps must be >= 0");
+    if (nsteps == 0) return MD_OK;
+    if (h->steps_total + nsteps >= (int64_t)1 << 31)
+        return fail(h, MD_ERR_INVALID, "md_step: step counter would overflow");
+    md_status st;
+    if (!h->forces_valid) {
+        st = forces_now(h, false);
+        if (st != MD_OK) return st;
+    }
+    const int64_t base = h->steps_total;
+    const int c0 = h->cur;
+    MD_CK(mark(h, -1));
+    begin_steps_kernel<<<1, 1, 0, h->stream>>>(h->ds, (int)base);
+    MD_CK(cudaGetLastError());
+    MD_CK(launch_kick_drift(h));
+    h->launches += 2;
+    MD_CK(mark(h, K_INTEGRATE));
+    h->forces_valid = false;
+    int64_t sr = 1;
+    for (int attempt = 0; attempt < 64; ++attempt) {
+        for (int64_t s = sr; s <= nsteps; ++s) {
+            h->steps_total = base + s;
+            h->cur = c0 ^ (int)((s - 1) & 1);
+            st = enqueue_rebuild(h, true);
+            if (st != MD_OK) return st;
+            const int mode = (s < nsteps) ? FM_FUSED_FULL : FM_FUSED_HALF;
+            st = enqueue_forces(h, mode, false, s == nsteps);
+            if (st != MD_OK) return st;
+        }
+        h->cur = c0 ^ (int)((nsteps - 1) & 1);
+        st = read_status(h);
+        if (st != MD_OK) return st;
+        if (h->timing) harvest(h);
+        const int dst = h->ds_host->status;
+        if (dst == 0) {
+            h->steps_total = base + nsteps;
+            h->forces_valid = true;
+            h->list_valid = true;
+            return MD_OK;
+        }
+        if (dst != MD_ERR_LIST_OVERFLOW) {
+            h->steps_total = h->ds_host->steps_done;
+            return fail(h, (md_status)dst, "md_step: device error at step " +
+                                               std::to_string(h->ds_host->steps_done + 1));
+        }
+        // The rebuild before step S overflowed after binning it; grow the list,
+        // rebuild it for the same positions and continue with step S.
+        const int64_t S = (int64_t)h->ds_host->steps_done - base + 1;
+        if (S < 1 || S > nsteps) return fail(h, MD_ERR_STATE, "md_step: inconsistent step counter");
+        h->cur = c0 ^ (int)((S - 1) & 1);
+        h->steps_total = base + S;
+        st = clear_status(h);
+        if (st != MD_OK) return st;
+        if (h->p.max_neighbors > 0)
+            return fail(h, MD_ERR_LIST_OVERFLOW, "md_step: neighbour count exceeds max_neighbors");
+        MD_CK(alloc_list(h, cap_for(h->ds_host->max_count)));
+        MD_CK(launch_build_list(h, true, false));
+        MD_CK(launch_finish_rebuild(h, false));
+        sr = S;
+        // re-enqueue steps S..nsteps; the loop's first rebuild is gated off
+        for (int64_t s = sr; s <= nsteps; ++s) {
+            h->steps_total = base + s;
+            h->cur = c0 ^ (int)((s - 1) & 1);
+            if (s > sr) {
+                st = enqueue_rebuild(h, true);
+                if (st != MD_OK) return st;
+            }
+            const int mode = (s < nsteps) ? FM_FUSED_FULL : FM_FUSED_HALF;
+            st = enqueue_forces(h, mode, false, s == nsteps);
+            if (st != MD_OK) return st;
+        }
+        sr = nsteps + 1;  // everything is enqueued; the outer loop only checks status
+    }
+    return fail(h, MD_ERR_LIST_OVERFLOW, "md_step: list overflow could not be repaired");
+}
+
+md_status md_energy(md_system *h, double *ke_host, double *pe_host) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_energy: null handle");
+    MD_CK(cudaMemsetAsync(&h->ds->pairs_cut, 0, sizeof(unsigned long long), h->stream));
+    md_status st = forces_now(h, true);
+    if (st != MD_OK) return st;
+    MD_CK(launch_reduce_pe(h));
+    MD_CK(launch_reduce_ke(h));
+    h->launches += 4;
+    MD_CK(cudaMemcpyAsync(h->red_host, h->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
+    MD_CK(cudaStreamSynchronize(h->stream));
+    if (pe_host) *pe_host = h->red_host[0];
+    if (ke_host) *ke_host = h->red_host[1];
+    return MD_OK;
+}
+
+md_status md_get_state(md_system *h, double *pos_dev, double *vel_dev, double *force_dev) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_get_state: null handle");
+    if (force_dev && !h->forces_valid) {
+        md_status st = forces_now(h, false);
+        if (st != MD_OK) return st;
+    }
+    MD_CK(launch_get_state(h, pos_dev, vel_dev, force_dev));
+    return MD_OK;
+}
+
+md_status md_set_state(md_system *h, const double *pos_dev, const double *vel_dev) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_set_state: null handle");
+    if (!pos_dev && !vel_dev) return MD_OK;
+    if (pos_dev && !vel_dev) {
+        // keep the current velocities: export them in original order first
+        double *tmp = nullptr;
+        MD_CK(dalloc(&tmp, 3 * (size_t)h->n));
+        cudaError_t e = launch_get_state(h, nullptr, tmp, nullptr);
+        if (e == cudaSuccess) e = launch_load_state(h, pos_dev, tmp);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        cudaFree(tmp);
+        MD_CK(e);
+    } else {
+        MD_CK(launch_load_state(h, pos_dev, vel_dev));
+    }
+    if (pos_dev) {
+        h->list_valid = false;
+        h->forces_valid = false;
+    }
+    return MD_OK;
+}
+
+md_status md_get_neighbors(md_system *h, int32_t half, int64_t *offsets_dev, int32_t *ids_dev,
+                           int64_t cap, int64_t *total_host) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_get_neighbors: null handle");
+    if (!offsets_dev || cap < 0) return fail(h, MD_ERR_INVALID, "md_get_neighbors: bad argument");
+    if (!half && h->p.force_variant != MD_FORCE_FULL)
+        return fail(h, MD_ERR_INVALID, "md_get_neighbors: the list is a half list");
+    if (!h->list_valid) {
+        md_status st = rebuild_now(h, false);
+        if (st != MD_OK) return st;
+    }
+    if (!h->exp_tmp) MD_CK(dalloc(&h->exp_tmp, (size_t)h->n + 64));
+    MD_CK(launch_export_list(h, half ? 1 : 0, offsets_dev, nullptr, h->exp_tmp));
+    int32_t total32 = 0;
+    const int32_t *rowstart = reinterpret_cast<const int32_t *>(h->exp_tmp) + (h->n + 1);
+    MD_CK(cudaMemcpyAsync(&total32, rowstart + h->n, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                          h->stream));
+    MD_CK(cudaStreamSynchronize(h->stream));
+    if (total_host) *total_host = total32;
+    if (total32 > cap) return fail(h, MD_ERR_LIST_OVERFLOW, "md_get_neighbors: cap too small");
+    if (!ids_dev && total32 > 0) return fail(h, MD_ERR_INVALID, "md_get_neighbors: ids_dev is null");
+    MD_CK(launch_export_list(h, half ? 1 : 0, offsets_dev, ids_dev, h->exp_tmp));
+    MD_CK(cudaStreamSynchronize(h->stream));
+    return MD_OK;
+}
+
+md_status md_get_cells(md_system *h, int32_t *cell_of_atom_dev, int64_t *cell_start_dev,
+                       int32_t *ncell_host) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_get_cells: null handle");
+    MD_CK(launch_export_cells(h, cell_of_atom_dev, cell_start_dev));
+    MD_CK(cudaStreamSynchronize(h->stream));
+    if (ncell_host) {
+        ncell_host[0] = h->g.nx;
+        ncell_host[1] = h->g.ny;
+        ncell_host[2] = h->g.nz;
+    }
+    return MD_OK;
+}
+
+md_status md_get_density(md_system *h, double *rho_dev, double *dF_dev) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_get_density: null handle");
+    if (h->p.potential != MD_POT_SC) return fail(h, MD_ERR_INVALID, "md_get_density: not many-body");
+    if (!h->forces_valid) {
+        md_status st = forces_now(h, false);
+        if (st != MD_OK) return st;
+    }
+    if (rho_dev) MD_CK(launch_scatter_orig(h, h->rho, rho_dev));
+    if (dF_dev) {
+        if (h->p.precision == MD_MIXED) MD_CK(launch_scatter_orig_f32(h, h->dF32, dF_dev));
+        else MD_CK(launch_scatter_orig(h, h->dF64, dF_dev));
+    }
+    return MD_OK;
+}
+
+md_status md_get_atom_energy(md_system *h, double *e_dev) {
+    if (!h || !e_dev) return fail(h, MD_ERR_INVALID, "md_get_atom_energy: null argument");
+    MD_CK(launch_scatter_orig(h, h->e_atom, e_dev));
+    return MD_OK;
+}
+
+md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_set_variant: null handle");
+    if (force_variant < MD_FORCE_FULL || force_variant > MD_FORCE_HALF_ATOMIC ||
+        scheduler < MD_SCHED_GRID || scheduler > MD_SCHED_DYNAMIC)
+        return fail(h, MD_ERR_INVALID, "md_set_variant: unknown variant or scheduler");
+    if (force_variant != MD_FORCE_FULL && h->p.potential == MD_POT_SC)
+        return fail(h, MD_ERR_INVALID, "md_set_variant: half lists are built for Lennard-Jones only");
+    const bool relist = (force_variant != MD_FORCE_FULL) != (h->p.force_variant != MD_FORCE_FULL);
+    h->p.force_variant = force_variant;
+    h->p.scheduler = scheduler;
+    if (relist) {
+        md_status st = rebuild_now(h, true);
+        if (st != MD_OK) return st;
+    }
+    return MD_OK;
+}
+
+md_status md_stats(md_system *h, char *buf_host, size_t cap) {
+    if (!h || !buf_host || cap == 0) return fail(h, MD_ERR_INVALID, "md_stats: bad argument");
+    md_status st = read_status(h);
+    if (st != MD_OK) return st;
+    const DevStatus &d = *h->ds_host;
+    std::snprintf(buf_host, cap,
+                  "{\"n\": %lld, \"ncell\": [%d, %d, %d], \"cap\": %d, \"builds\": %d, "
+                  "\"steps\": %lld, \"max_count\": %d, \"max_cell\": %d, \"status\": %d, "
+                  "\"precision\": %d, \"force_variant\": %d, \"scheduler\": %d, "
+                  "\"list_entries\": %llu, \"pairs_cut\": %llu, \"launches\": %lld, "
+                  "\"ms\": {\"rebuild\": %.6f, \"force\": %.6f, \"integrate\": %.6f, "
+                  "\"other\": %.6f}, \"count\": {\"rebuild\": %lld, \"force\": %lld, "
+                  "\"integrate\": %lld, \"other\": %lld}}",
+                  (long long)h->n, h->g.nx, h->g.ny, h->g.nz, h->cap, d.builds,
+                  (long long)h->steps_total, d.max_count, d.max_cell, d.status, h->p.precision,
+                  h->p.force_variant, h->p.scheduler, d.list_entries, d.pairs_cut, h->launches,
+                  h->ms_kind[0], h->ms_kind[1], h->ms_kind[2], h->ms_kind[3], h->n_kind[0],
+                  h->n_kind[1], h->n_kind[2], h->n_kind[3]);
+    return MD_OK;
+}
+
+md_status md_set_timing(md_system *h, int32_t on) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_set_timing: null handle");
+    MD_CK(cudaStreamSynchronize(h->stream));
+    h->timing = (on != 0);
+    h->ev_used = 0;
+    for (int k = 0; k < 4; ++k) {
+        h->ms_kind[k] = 0.0;
+        h->n_kind[k] = 0;
+    }
+    h->launches = 0;
+    return MD_OK;
+}
+
+md_status md_cost_model(md_system *h, int32_t op, float *loss_out) {
+    (void)op;
+    (void)loss_out;
+    return fail(h, MD_ERR_INVALID, "md_cost_model: persistent schedulers are not built yet");
+}
+
+const char *md_last_error(md_system *h) {
+    return h ? h->last_error.c_str() : g_thread_error.c_str();
+}
+
+void md_destroy(md_system *h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+// md_internal.cuh -- private types and launcher declarations of the GB300
+// molecular-dynamics library.  Included by every translation unit of the
+// library; never installed.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/md_gb300.h"
+
+namespace mdg {
+
+constexpr int kBlock = 256;       // threads per block of the per-atom kernels
+constexpr int kStencil = 27;      // cells scanned around a cell (Sec. 2.1)
+constexpr int kIndexBits = 27;    // list entry = (stencil << 27) | sorted index
+constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
+constexpr int64_t kMaxAtoms = (int64_t)1 << kIndexBits;
+
+// Device status word.  Every kernel of a step returns at entry when `status`
+// is non-zero, so an error stops the rest of the enqueued work and the host
+// finds the state exactly where it stopped.
+struct DevStatus {
+    int status;          // md_status of the first device-detected error
+    int steps_done;      // last completed time step of the current md_step call
+    int rebuild;         // 1: the next gated rebuild chain runs
+    int since_build;     // steps since the last list build
+    int abs_fresh;       // 1: xabs holds the positions exactly (no drift since)
+    int max_count;       // largest neighbour count of the last build
+    int max_cell;        // largest cell occupancy of the last binning
+    int builds;          // list builds so far
+    unsigned int timeouts;  // bounded waits that gave up
+    int pad0;
+    unsigned long long list_entries;  // entries of the last list build
+    unsigned long long pairs_cut;     // pairs inside r_c of the last energy evaluation
+    long long pad1[2];
+};
+
+// Geometry passed by value to kernels.
+struct Grid {
+    int nx, ny, nz, pad0;
+    int ncells;
+    int pad1;
+    double L[3];
+    double w[3];        // cell widths L / n
+    double inv_w[3];    // n / L
+};
+
+// Per-launch scalars of the force kernels.
+struct ForceConsts {
+    float rc2f, eps4f, eps48f, sig2f, shiftf;  // LJ in fp32
+    double rc2, eps4, eps48, sig2, shift;        // LJ in fp64
+    // Sutton-Chen
+    float sc_af, sc_epsf, sc_ecf;  // a, eps, eps*c
+    double sc_a, sc_eps, sc_ec;
+    int sc_n, sc_m;
+    // integrator
+    double dt, inv_m;
+    float half_skin2f;
+};
+
+enum ForceMode {
+    FM_STORE = 0,       // forces (and optional energies) to f
+    FM_FUSED_FULL = 1,  // forces, kick dt, drift dt (two half kicks merged)
+    FM_FUSED_HALF = 2,  // forces, closing half kick, store f
+};
+
+}  // namespace mdg
+
+// The system handle (host structure; device arrays in sorted order).
+struct md_system {
+    md_params p;
+    int64_t n = 0;
+    cudaStream_t stream = nullptr;
+    mdg::Grid g{};
+    mdg::ForceConsts fc{};
+    double r_list = 0.0;
+    float list_lo = 0.f, list_hi = 0.f;  // fp32 prefilter band around r_list^2
+    double rl2 = 0.0;
+
+    // state, sorted order
+    double4 *xr64[2] = {nullptr, nullptr};  // fp64 position relative to the cell centre
+    float4 *xq[2] = {nullptr, nullptr};     // fp32 copy (w = original id bits)
+    float4 *xq_build = nullptr;             // fp32 copy at the last build
+    double4 *xabs = nullptr;                // absolute positions at the last rebuild
+    double *v = nullptr;                    // velocities, 3 x n SoA
+    double *f = nullptr;                    // forces of the last evaluation, 3 x n SoA
+    double *e_atom = nullptr;               // per-atom potential energy
+    int32_t *orig = nullptr;                // sorted slot -> original id
+    int32_t *cell = nullptr;                // sorted slot -> cell (-1: xr64 holds absolute)
+    int cur = 0;
+
+    // binning
+    int32_t *cell_start = nullptr;  // ncells + 1
+    int32_t *cell_count = nullptr;  // ncells
+    int32_t *new_cell = nullptr, *slot = nullptr, *src = nullptr, *key = nullptr;
+    int32_t *scan_bsum = nullptr;
+    double4 *tmp_abs = nullptr;
+    double *tmp_v = nullptr;
+    int32_t *tmp_orig = nullptr;
+
+    // neighbour list: warp-interleaved [n/32][cap][32] entries + counts
+    uint32_t *nlist = nullptr;
+    int32_t *ncount = nullptr;
+    int cap = 0;
+    size_t nlist_entries = 0;
+
+    // many-body
+    double *rho = nullptr;
+    float *dF32 = nullptr;
+    double *dF64 = nullptr;
+
+    // reductions
+    double *partials = nullptr;  // per-block partial sums
+    double *red_out = nullptr;   // [0] = PE, [1] = KE
+    int nblocks_n = 0;
+
+    int64_t *exp_tmp = nullptr;  // scratch of md_get_neighbors
+
+    mdg::DevStatus *ds = nullptr;       // device
+    mdg::DevStatus *ds_host = nullptr;  // pinned mirror
+    double *red_host = nullptr;         // pinned
+
+    // per-launch timing (md_set_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_kind;  // kind of the interval that ends at event k
+    size_t ev_used = 0;
+    double ms_kind[4] = {0, 0, 0, 0};      // rebuild, force, integrate, other
+    long long n_kind[4] = {0, 0, 0, 0};
+    long long launches = 0;                // kernels enqueued by this handle
+
+    bool forces_valid = false;
+    bool list_valid = false;
+    int64_t steps_total = 0;
+    int64_t rebuilds_host = 0;
+    std::string last_error;
+};
+
+namespace mdg {
+
+// ---- binning (k_bin.cu) --------------------------------------------------
+// Gated chain: reconstruct absolute positions, count per cell, scan, scatter,
+// order each cell by original id, gather the new sorted state.
+cudaError_t launch_bin(md_system *h, bool gated);
+// Exclusive scan of int32 counts into int32 starts (starts[n] = total).
+cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int n, int32_t *bsum,
+                            const DevStatus *ds, bool gated, cudaStream_t s);
+// cell of each atom in original order; cell_start as int64
+cudaError_t launch_export_cells(md_system *h, int32_t *cell_of_atom, int64_t *cell_start);
+
+// ---- neighbour list (k_nlist.cu) ------------------------------------------
+cudaError_t launch_build_list(md_system *h, bool write, bool gated);
+cudaError_t launch_finish_rebuild(md_system *h, bool gated);
+cudaError_t launch_export_list(md_system *h, int half, int64_t *offsets, int32_t *ids,
+                               int64_t *row_counts_tmp);
+
+// ---- forces (k_lj.cu, k_sc.cu) -------------------------------------------
+cudaError_t launch_lj(md_system *h, int mode, bool energy, bool store_f);
+cudaError_t launch_sc_density(md_system *h);
+cudaError_t launch_sc_force(md_system *h, int mode, bool energy, bool store_f);
+
+// ---- integrator and state (k_integrate.cu) --------------------------------
+cudaError_t launch_kick_drift(md_system *h);
+cudaError_t launch_load_state(md_system *h, const double *pos, const double *vel);
+cudaError_t launch_get_state(md_system *h, double *pos, double *vel, double *force);
+cudaError_t launch_scatter_orig(md_system *h, const double *src_sorted, double *dst_orig);
+cudaError_t launch_scatter_orig_f32(md_system *h, const float *src_sorted, double *dst_orig);
+cudaError_t launch_reduce_pe(md_system *h);
+cudaError_t launch_reduce_ke(md_system *h);
+cudaError_t launch_set_rebuild(md_system *h);
+
+inline int nblocks(int64_t n, int b = kBlock) { return (int)((n + b - 1) / b); }
+
+}  // namespace mdg
