@@ -41,7 +41,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="porous", choices=["porous", "fcc", "sc"])
-    ap.add_argument("--scheduler", default="grid",
+    ap.add_argument("--compare-steps", type=int, default=100,
+                    help="steps timed for each other scheduler (0 = skip the comparison)")
+    ap.add_argument("--scheduler", default="mlp",
                     choices=["grid", "paircount", "mlp", "dynamic"])
     ap.add_argument("--fp64-steps", type=int, default=50,
                     help="steps timed for the plain fp64 comparison (slow path)")
@@ -181,6 +183,9 @@ def run_gpu(args, rank, world, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    def n_of(sysobj):
+        return sysobj.n * world
+
     def timed(sysobj, nsteps):
         md.md_set_timing(sysobj.h, True)
         torch.cuda.synchronize()
@@ -199,9 +204,32 @@ def run_gpu(args, rank, world, local):
 
     sampler = ClockSampler(local)
     with torch.cuda.stream(stream):
-        mixed = md.System(s.pos, s.vel, s.box, precision="mixed", scheduler=sched,
-                          stream=stream, **kw)
+        mixed = md.System(s.pos, s.vel, s.box, precision="mixed", stream=stream, **kw)
         md.md_step(mixed.h, args.warmup)
+        sched_info = {}
+        # the other schedulers on the same state, for comparison (short runs)
+        if args.compare_steps > 0 and kw["potential"] == "lj":
+            for name, code in (("grid", md.MD_SCHED_GRID), ("paircount", md.MD_SCHED_PAIRCOUNT),
+                               ("dynamic", md.MD_SCHED_DYNAMIC)):
+                md.md_set_variant(mixed.h, md.MD_FORCE_FULL, code)
+                msx, stx = timed(mixed, args.compare_steps)
+                sched_info[name] = {"atom_steps_per_s": n_of(mixed) * args.compare_steps / (msx * 1e-3),
+                                    "force_ms_per_launch": stx["ms"]["force"] / max(1, stx["count"]["force"])}
+                if code != md.MD_SCHED_GRID:
+                    sched_info[name]["cta_imbalance"] = md.md_cost_model(mixed.h, md.MD_COST_PROFILE)
+        if args.scheduler == "mlp" and kw["potential"] == "lj":
+            # the learned part: per-cell clock64 timings of this run -> GPU training
+            md.md_set_variant(mixed.h, md.MD_FORCE_FULL, md.MD_SCHED_DYNAMIC)
+            t0 = time.perf_counter()
+            nsamp = md.md_cost_model(mixed.h, md.MD_COST_SAMPLE)
+            loss = md.md_cost_model(mixed.h, md.MD_COST_TRAIN)
+            t1 = time.perf_counter()
+            md.md_set_variant(mixed.h, md.MD_FORCE_FULL, md.MD_SCHED_MLP)
+            sched_info["mlp_training"] = {"samples": int(nsamp), "final_mse": loss,
+                                          "sample_and_train_s": t1 - t0}
+            sched_info["mlp_cta_imbalance"] = md.md_cost_model(mixed.h, md.MD_COST_PROFILE)
+        else:
+            md.md_set_variant(mixed.h, md.MD_FORCE_FULL, sched)
         builds0 = json.loads(md.md_stats(mixed.h))["builds"]
         sampler.start()
         ms, st = timed(mixed, args.steps)
@@ -284,7 +312,8 @@ def run_gpu(args, rank, world, local):
             "unit": "GB/s" if hbm_bound else "TFLOP/s",
             "frac": (ach_gbs / hbm_peak) if hbm_bound else (ach_flops / fp32_peak),
             "traffic": None,
-            "kernel": "lj_mixed_kernel<FM_FUSED_FULL>" if kw["potential"] == "lj" else "sc_force_mixed",
+            "kernel": ("lj_mixed_persist<FM_FUSED_FULL> (%s)" % args.scheduler if args.scheduler != "grid"
+                       else "lj_mixed_kernel<FM_FUSED_FULL>") if kw["potential"] == "lj" else "sc_force_mixed",
             "peak_source": peak_src,
             "algorithmic_bytes_per_launch": bytes_, "algorithmic_flops_per_launch": flops,
             "launch_ms": t_force * 1e3,
@@ -293,7 +322,8 @@ def run_gpu(args, rank, world, local):
                      "peak_note": "SMs x 128 fp32 lanes x 2 x max SM clock"}}
     return dict(n=n, value=value, ms=ms, st=st, st_e=st_e, fp64=fp64, e2e=e2e, roof=roof,
                 clk=clk, desc=desc, pos=pos.cpu().numpy(), force=force.cpu().numpy(),
-                box=s.box, params=s.params, ke=ke, pe=pe, builds_timed=builds_timed)
+                box=s.box, params=s.params, ke=ke, pe=pe, builds_timed=builds_timed,
+                sched_info=sched_info)
 
 
 # ------------------------------------------------------------------ CPU legs
@@ -410,6 +440,7 @@ def main():
         "clocks": g["clk"],
         "e2e": g["e2e"],
         "gpu_launches": st["launches"],
+        "schedulers": g["sched_info"],
         "kernel_ms": {"rebuild": st["ms"]["rebuild"], "force": st["ms"]["force"],
                       "integrate": st["ms"]["integrate"], "counts": st["count"]},
         "energy": {"ke": g["ke"], "pe": g["pe"]},

@@ -62,7 +62,13 @@ enum {
     MD_SCHED_MLP = 2,       /* persistent CTAs, static partition by the learned cost model */
     MD_SCHED_DYNAMIC = 3    /* persistent CTAs pulling tiles from an atomic queue */
 };
-enum { MD_COST_TRAIN = 0, MD_COST_PREDICT = 1, MD_COST_RESET = 2, MD_COST_SAMPLE = 3 };
+enum {
+    MD_COST_TRAIN = 0,   /* Adam epochs on the stored samples */
+    MD_COST_PREDICT = 1, /* infer per-cell costs, rebuild the partition */
+    MD_COST_RESET = 2,   /* re-initialise the weights */
+    MD_COST_SAMPLE = 3,  /* timed force passes -> per-cell training samples */
+    MD_COST_PROFILE = 4  /* one timed force pass: max / mean CTA busy cycles */
+};
 
 typedef struct {
     int32_t potential;     /* MD_POT_LJ or MD_POT_SC */
@@ -153,8 +159,21 @@ md_status md_get_density(md_system *h, double *rho_dev, double *dF_dev);
 md_status md_get_atom_energy(md_system *h, double *e_dev);
 
 /* Switches the force strategy and scheduler of an existing system (same
- * potential and precision).  The next force evaluation uses them. */
+ * potential and precision) and rebuilds what the new choice needs (the list
+ * when switching between full and half lists, the cell partition for the
+ * static schedulers).  Half lists (Newton's third law, each pair once, owned
+ * by the lower original id) are built for the mixed-precision Lennard-Jones
+ * path; the persistent schedulers drive the mixed full-list Lennard-Jones
+ * pass, and every other combination runs one thread per atom. */
 md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler);
+
+/* Colour of every cell of an ncell_host[0] x [1] x [2] grid (each >= 3) as
+ * used by MD_FORCE_HALF_COLOR: same-colour cells have disjoint 27-cell
+ * neighbourhoods, so their force tasks never touch the same atom (the
+ * conflict-free schedule of Sec. 2.1).  color_host (may be NULL) receives
+ * one int32 per cell in linear cell order; *ncolors_host the colour count.
+ * Host-only; touches no GPU. */
+md_status md_color_cells(const int32_t *ncell_host, int32_t *color_host, int32_t *ncolors_host);
 
 /* Learned per-cell cost model (3 -> 32 -> 32 -> 1 MLP, ReLU, fp32).
  *  MD_COST_SAMPLE  time one force pass with per-tile clock64 and store

@@ -49,8 +49,7 @@ __global__ void prepare_abs_kernel(int n, Grid g, const double4 *__restrict__ xr
                                    const int32_t *__restrict__ cell, double4 *__restrict__ xabs,
                                    const DevStatus *ds, bool gated) {
     if (chain_off(ds, gated) || ds->abs_fresh) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double4 r = xr[i];
     int c = cell[i];
     double x = r.x, y = r.y, z = r.z;
@@ -60,21 +59,21 @@ __global__ void prepare_abs_kernel(int n, Grid g, const double4 *__restrict__ xr
     }
     xabs[i] = make_double4(wrap_coord(x, g.L[0]), wrap_coord(y, g.L[1]), wrap_coord(z, g.L[2]),
                            0.0);
+    }
 }
 
 __global__ void zero_counts_kernel(int ncells, int32_t *count, DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c == 0) ds->max_cell = 0;
-    if (c < ncells) count[c] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ds->max_cell = 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x)
+        count[c] = 0;
 }
 
 __global__ void bin_count_kernel(int n, Grid g, const double4 *__restrict__ xabs,
                                  int32_t *__restrict__ count, int32_t *__restrict__ new_cell,
                                  int32_t *__restrict__ slot, DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double4 x = xabs[i];
     int cx = cell_coord(x.x, g.inv_w[0], g.nx);
     int cy = cell_coord(x.y, g.inv_w[1], g.ny);
@@ -84,6 +83,7 @@ __global__ void bin_count_kernel(int n, Grid g, const double4 *__restrict__ xabs
     int s = atomicAdd(&count[c], 1);
     slot[i] = s;
     atomicMax(&ds->max_cell, s + 1);
+    }
 }
 
 __global__ void scatter_kernel(int n, const int32_t *__restrict__ new_cell,
@@ -92,11 +92,11 @@ __global__ void scatter_kernel(int n, const int32_t *__restrict__ new_cell,
                                int32_t *__restrict__ src, int32_t *__restrict__ key,
                                const DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int p = start[new_cell[i]] + slot[i];
-    src[p] = i;
-    key[p] = orig[i];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int p = start[new_cell[i]] + slot[i];
+        src[p] = i;
+        key[p] = orig[i];
+    }
 }
 
 // Orders each cell's range by original id (insertion sort; cells hold tens of atoms).
@@ -104,8 +104,7 @@ __global__ void cell_sort_kernel(int ncells, const int32_t *__restrict__ start,
                                  int32_t *__restrict__ key, int32_t *__restrict__ src,
                                  const DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncells) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
     int b = start[c], e = start[c + 1];
     for (int a = b + 1; a < e; ++a) {
         int k = key[a], s = src[a];
@@ -118,6 +117,7 @@ __global__ void cell_sort_kernel(int ncells, const int32_t *__restrict__ start,
         key[q + 1] = k;
         src[q + 1] = s;
     }
+    }
 }
 
 __global__ void copy_src_kernel(int n, const double4 *__restrict__ xabs,
@@ -125,13 +125,13 @@ __global__ void copy_src_kernel(int n, const double4 *__restrict__ xabs,
                                 double4 *__restrict__ tabs, double *__restrict__ tv,
                                 int32_t *__restrict__ torig, const DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     tabs[i] = xabs[i];
     tv[i] = v[i];
     tv[n + i] = v[n + i];
     tv[2 * (size_t)n + i] = v[2 * (size_t)n + i];
     torig[i] = orig[i];
+    }
 }
 
 __global__ void gather_kernel(int n, Grid g, const int32_t *__restrict__ src,
@@ -143,9 +143,8 @@ __global__ void gather_kernel(int n, Grid g, const int32_t *__restrict__ src,
                               int32_t *__restrict__ orig, int32_t *__restrict__ cell,
                               DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k == 0) ds->abs_fresh = 1;
-    if (k >= n) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ds->abs_fresh = 1;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     int s = src[k];
     int c = new_cell[s];
     double3 C = cell_centre(c, g);
@@ -162,6 +161,7 @@ __global__ void gather_kernel(int n, Grid g, const int32_t *__restrict__ src,
     v[2 * (size_t)n + k] = tv[2 * (size_t)n + s];
     orig[k] = o;
     cell[k] = c;
+    }
 }
 
 __global__ void export_cells_kernel(int n, int ncells, const int32_t *__restrict__ orig,
@@ -184,22 +184,22 @@ cudaError_t launch_bin(md_system *h, bool gated) {
     int n = (int)h->n;
     cudaStream_t s = h->stream;
     int cur = h->cur;
-    prepare_abs_kernel<<<nblocks(n), kBlock, 0, s>>>(n, h->g, h->xr64[cur], h->cell, h->xabs,
+    prepare_abs_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->g, h->xr64[cur], h->cell, h->xabs,
                                                      h->ds, gated);
-    zero_counts_kernel<<<nblocks(h->g.ncells), kBlock, 0, s>>>(h->g.ncells, h->cell_count,
+    zero_counts_kernel<<<gs_blocks(h->g.ncells), kBlock, 0, s>>>(h->g.ncells, h->cell_count,
                                                                h->ds, gated);
-    bin_count_kernel<<<nblocks(n), kBlock, 0, s>>>(n, h->g, h->xabs, h->cell_count, h->new_cell,
+    bin_count_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->g, h->xabs, h->cell_count, h->new_cell,
                                                    h->slot, h->ds, gated);
     cudaError_t e = launch_scan_i32(h->cell_count, h->cell_start, h->g.ncells, h->scan_bsum,
                                     h->ds, gated, s);
     if (e != cudaSuccess) return e;
-    scatter_kernel<<<nblocks(n), kBlock, 0, s>>>(n, h->new_cell, h->slot, h->cell_start, h->orig,
+    scatter_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->new_cell, h->slot, h->cell_start, h->orig,
                                                  h->src, h->key, h->ds, gated);
-    cell_sort_kernel<<<nblocks(h->g.ncells), kBlock, 0, s>>>(h->g.ncells, h->cell_start, h->key,
+    cell_sort_kernel<<<gs_blocks(h->g.ncells), kBlock, 0, s>>>(h->g.ncells, h->cell_start, h->key,
                                                              h->src, h->ds, gated);
-    copy_src_kernel<<<nblocks(n), kBlock, 0, s>>>(n, h->xabs, h->v, h->orig, h->tmp_abs,
+    copy_src_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->xabs, h->v, h->orig, h->tmp_abs,
                                                   h->tmp_v, h->tmp_orig, h->ds, gated);
-    gather_kernel<<<nblocks(n), kBlock, 0, s>>>(n, h->g, h->src, h->new_cell, h->tmp_abs,
+    gather_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->g, h->src, h->new_cell, h->tmp_abs,
                                                 h->tmp_v, h->tmp_orig, h->xr64[cur], h->xq[cur],
                                                 h->xq_build, h->xabs, h->v, h->orig, h->cell,
                                                 h->ds, gated);

@@ -6,7 +6,9 @@
 
 namespace mdg {
 
-constexpr int kChunk = 32;
+// float32 partial sums cover kChunkQ quads (64 list entries) before they are
+// added to the float64 accumulators
+constexpr int kChunkQ = 16;
 
 struct ForceArgs {
     int n, cap, step, rebuild_every;

@@ -14,8 +14,10 @@
 //   MIXED  the pair vector, r^2, 1/r^2, (s/r)^6 and the force scalar are
 //          float32, computed from cell-relative float32 coordinates plus the
 //          float32 cell shift of the entry's stencil cell; each chunk of
-//          kChunk entries is summed in float32 and the chunk sums are added
-//          in float64 (the GPU form of the paper's blocked pair loop).
+//          64 entries is summed in float32 and the chunk sums are added in
+//          float64 (the GPU form of the paper's blocked pair loop).  Entries
+//          arrive four at a time (one 16-byte load), so four gathers are in
+//          flight before the arithmetic that needs them.
 //   FP64   everything in float64 (the plain path).
 //
 // Modes (ForceMode): FM_STORE writes forces; FM_FUSED_FULL also applies the
@@ -28,31 +30,31 @@
 
 namespace mdg {
 
-template <int MODE, bool ENERGY>
-__global__ void __launch_bounds__(kBlock) lj_mixed_kernel(ForceArgs a, int store_f) {
-    __shared__ float4 sh[kStencil];
+// Float32 cell shifts (dx, dy, dz) * w of the 27 stencil cells, in shared memory.
+__device__ __forceinline__ void load_shifts_f32(const ForceArgs &a, float4 *sh) {
     if (threadIdx.x < kStencil) {
         int s = threadIdx.x;
         int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
         sh[s] = make_float4((float)(dx * a.g.w[0]), (float)(dy * a.g.w[1]),
                             (float)(dz * a.g.w[2]), 0.f);
     }
-    __syncthreads();
-    if (a.ds->status != 0) return;
-    step_bookkeeping<MODE>(a);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+}
+
+// The whole per-atom job of the mixed path for sorted atom i: pair loop over
+// its list, stores, and the velocity-Verlet epilogue.
+template <int MODE, bool ENERGY>
+__device__ __forceinline__ void lj_mixed_atom(const ForceArgs &a, const float4 *sh, int i,
+                                              int store_f) {
     const float4 qi = a.xq[i];
-    const int cnt = min(a.ncount[i], a.cap);
-    const uint32_t *lp = a.nlist + (size_t)(i >> 5) * (size_t)a.cap * 32 + (size_t)(i & 31);
+    const int nq = (min(a.ncount[i], a.cap) + 3) >> 2;
+    const uint4 *lq = reinterpret_cast<const uint4 *>(a.nlist + list_group(i, a.cap)) + (i & 31);
     const float rc2 = a.fc.rc2f, sig2 = a.fc.sig2f, e48 = a.fc.eps48f;
     double Fx = 0.0, Fy = 0.0, Fz = 0.0, E = 0.0;
     unsigned npair = 0;
-    for (int k0 = 0; k0 < cnt; k0 += kChunk) {
-        const int k1 = min(k0 + kChunk, cnt);
+    for (int q0 = 0; q0 < nq; q0 += kChunkQ) {
+        const int q1 = min(q0 + kChunkQ, nq);
         float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
-        for (int k = k0; k < k1; ++k) {
-            const uint32_t ent = __ldg(lp + (size_t)k * 32);
+        auto pair = [&](uint32_t ent) {
             const float4 qj = __ldg(a.xq + (ent & kIndexMask));
             const float4 sf = sh[ent >> kIndexBits];
             const float ex = (qj.x - qi.x) + sf.x;
@@ -72,6 +74,14 @@ __global__ void __launch_bounds__(kBlock) lj_mixed_kernel(ForceArgs a, int store
                     ++npair;
                 }
             }
+        };
+#pragma unroll 2
+        for (int q = q0; q < q1; ++q) {
+            const uint4 e4 = __ldg(lq + (size_t)q * 32);
+            pair(e4.x);
+            pair(e4.y);
+            pair(e4.z);
+            pair(e4.w);
         }
         Fx += (double)fx;
         Fy += (double)fy;
@@ -91,6 +101,93 @@ __global__ void __launch_bounds__(kBlock) lj_mixed_kernel(ForceArgs a, int store
     if (MODE != FM_STORE) vv_epilogue<MODE>(a, i, Fx, Fy, Fz, qi.w);
 }
 
+// One thread per sorted atom; the hardware block scheduler spreads the work.
+template <int MODE, bool ENERGY>
+__global__ void __launch_bounds__(kBlock) lj_mixed_kernel(ForceArgs a, int store_f) {
+    __shared__ float4 sh[kStencil];
+    load_shifts_f32(a, sh);
+    __syncthreads();
+    if (a.ds->status != 0) return;
+    step_bookkeeping<MODE>(a);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) lj_mixed_atom<MODE, ENERGY>(a, sh, i, store_f);
+}
+
+// Persistent variant: gridDim.x CTAs stay resident; each warp processes tiles
+// of 32 consecutive sorted atoms (tile t = atoms 32t .. 32t+31, aligned with
+// the list layout).
+//   STATIC:  CTA b owns atoms [cell_start[bounds[b]], cell_start[bounds[b+1]])
+//            -- a contiguous range of whole cells from an equal-cost
+//            partition -- and its warps take that range's tiles round-robin.
+//   DYNAMIC: warps claim tiles from a global counter until none are left; the
+//            last CTA to finish resets the counter for the next launch.
+// TIMING adds clock64 per tile: the tile's cycles are shared equally by its
+// active atoms and added to their cells (cell_cycles), and each CTA's busy
+// cycles go to cta_cycles -- the training data of the cost model.
+constexpr int kClaim = 8;  // tiles claimed per atomic by the dynamic queue
+
+template <int MODE, bool ENERGY, bool DYNAMIC, bool TIMING>
+__global__ void __launch_bounds__(kBlock, 5)
+lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
+    __shared__ float4 sh[kStencil];
+    load_shifts_f32(a, sh);
+    __syncthreads();
+    if (a.ds->status != 0) return;
+    step_bookkeeping<MODE>(a);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int ntiles = (a.n + 31) >> 5;
+    long long cta_t0 = 0;
+    if (TIMING) cta_t0 = clock64();
+    int A = 0, B = a.n;
+    int t = 0, tend = ntiles, tstep = nwarp;
+    int claim_end = 0;
+    if (!DYNAMIC) {
+        A = sa.cell_start[sa.bounds[blockIdx.x]];
+        B = sa.cell_start[sa.bounds[blockIdx.x + 1]];
+        t = (A >> 5) + warp;
+        tend = (B + 31) >> 5;
+    }
+    for (;;) {
+        if (DYNAMIC) {
+            if (t >= claim_end) {
+                int claimed = 0;
+                if (lane == 0) claimed = atomicAdd(&a.ds->tile_counter, kClaim);
+                t = __shfl_sync(0xffffffffu, claimed, 0);
+                claim_end = t + kClaim;
+            }
+        }
+        if (t >= tend) break;
+        const int i = (t << 5) + lane;
+        const bool active = (i >= A) && (i < B);
+        long long t0 = 0;
+        if (TIMING) {
+            __syncwarp();
+            t0 = clock64();
+        }
+        if (active) lj_mixed_atom<MODE, ENERGY>(a, sh, i, store_f);
+        if (TIMING) {
+            __syncwarp();
+            const long long dt = clock64() - t0;
+            const unsigned act = __ballot_sync(0xffffffffu, active);
+            if (active) atomicAdd(&sa.cell_cycles[sa.cell[i]], (float)dt / (float)__popc(act));
+        }
+        t += DYNAMIC ? 1 : tstep;
+    }
+    if (TIMING || DYNAMIC) __syncthreads();
+    if (threadIdx.x == 0) {
+        if (TIMING) sa.cta_cycles[blockIdx.x] = (float)(clock64() - cta_t0);
+        if (DYNAMIC) {
+            __threadfence();
+            const unsigned prev = atomicAdd(&a.ds->done_ctas, 1u);
+            if (prev == gridDim.x - 1) {
+                a.ds->tile_counter = 0;
+                a.ds->done_ctas = 0;
+                __threadfence();
+            }
+        }
+    }
+}
+
 template <int MODE, bool ENERGY>
 __global__ void __launch_bounds__(kBlock) lj_fp64_kernel(ForceArgs a, int store_f) {
     __shared__ double3 sh[kStencil];
@@ -106,12 +203,11 @@ __global__ void __launch_bounds__(kBlock) lj_fp64_kernel(ForceArgs a, int store_
     if (i >= a.n) return;
     const double4 ri = a.xr[i];
     const int cnt = min(a.ncount[i], a.cap);
-    const uint32_t *lp = a.nlist + (size_t)(i >> 5) * (size_t)a.cap * 32 + (size_t)(i & 31);
     const double rc2 = a.fc.rc2, sig2 = a.fc.sig2, e48 = a.fc.eps48;
     double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0;
     unsigned npair = 0;
     for (int k = 0; k < cnt; ++k) {
-        const uint32_t ent = __ldg(lp + (size_t)k * 32);
+        const uint32_t ent = __ldg(a.nlist + list_idx(i, k, a.cap));
         const double4 rj = a.xr[ent & kIndexMask];
         const double3 sd = sh[ent >> kIndexBits];
         const double ex = (rj.x - ri.x) + sd.x;
@@ -194,6 +290,48 @@ cudaError_t launch_lj(md_system *h, int mode, bool energy, bool store_f) {
         }
     }
 #undef MDG_LJ
+    return cudaGetLastError();
+}
+
+}  // namespace mdg
+
+namespace mdg {
+
+int persist_ctas_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, lj_mixed_persist<FM_FUSED_FULL, false, false, false>, kBlock, 0) != cudaSuccess)
+        nb = 1;
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_lj_persist(md_system *h, int mode, bool store_f, bool dynamic, bool timing) {
+    ForceArgs a = make_force_args(h);
+    SchedArgs sa;
+    sa.cell_start = h->cell_start;
+    sa.bounds = h->part_bounds;
+    sa.cell = h->cell;
+    sa.cell_cycles = h->cell_cycles;
+    sa.cta_cycles = h->cta_cycles;
+    const int G = h->sched_ctas;
+    const int sf = store_f ? 1 : 0;
+    cudaStream_t s = h->stream;
+    if (timing) {
+        if (dynamic) lj_mixed_persist<FM_STORE, false, true, true><<<G, kBlock, 0, s>>>(a, 1, sa);
+        else lj_mixed_persist<FM_STORE, false, false, true><<<G, kBlock, 0, s>>>(a, 1, sa);
+        return cudaGetLastError();
+    }
+#define MDG_P(M)                                                                       \
+    do {                                                                               \
+        if (dynamic) lj_mixed_persist<M, false, true, false><<<G, kBlock, 0, s>>>(a, sf, sa); \
+        else lj_mixed_persist<M, false, false, false><<<G, kBlock, 0, s>>>(a, sf, sa);        \
+    } while (0)
+    switch (mode) {
+        case FM_STORE: MDG_P(FM_STORE); break;
+        case FM_FUSED_FULL: MDG_P(FM_FUSED_FULL); break;
+        default: MDG_P(FM_FUSED_HALF); break;
+    }
+#undef MDG_P
     return cudaGetLastError();
 }
 

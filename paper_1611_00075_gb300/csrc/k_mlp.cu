@@ -24,7 +24,9 @@ constexpr int kGradThreads = 128;
 namespace {
 
 __global__ void mlp_forward_kernel(const float *__restrict__ X, long long ns,
-                                   const float *__restrict__ P, float *__restrict__ y) {
+                                   const float *__restrict__ P, float *__restrict__ y,
+                                   const DevStatus *ds, bool gated) {
+    if (scan_off(ds, gated)) return;
     __shared__ float sP[kNP];
     for (int k = threadIdx.x; k < kNP; k += blockDim.x) sP[k] = P[k];
     __syncthreads();
@@ -168,7 +170,9 @@ __global__ void adam_kernel(float *__restrict__ P, const float *__restrict__ G,
 
 // bounds[b] = first k with inclusive_prefix[k] * nparts > b * total.
 __global__ void partition_kernel(const long long *__restrict__ excl, long long ncells, int nparts,
-                                 long long *__restrict__ bounds) {
+                                 long long *__restrict__ bounds, const DevStatus *ds,
+                                 bool gated) {
+    if (scan_off(ds, gated)) return;
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b > nparts) return;
     if (b == 0) { bounds[0] = 0; return; }
@@ -184,14 +188,41 @@ __global__ void partition_kernel(const long long *__restrict__ excl, long long n
     bounds[b] = lo;
 }
 
+// He-uniform initial weights (bound sqrt(6 / fan_in)), zero biases.  The
+// uniform deviates come from splitmix64 of (seed, parameter index).
+__global__ void mlp_init_kernel(float *P, unsigned long long seed) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kNP) return;
+    int fan_in = 0;
+    if (k < kOffB1) fan_in = 3;
+    else if (k >= kOffW2 && k < kOffB2) fan_in = kH;
+    else if (k >= kOffW3 && k < kOffB3) fan_in = kH;
+    if (fan_in == 0) {
+        P[k] = 0.f;
+        return;
+    }
+    unsigned long long z = seed + (unsigned long long)(k + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double u = ((double)(z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    const double b = sqrt(6.0 / fan_in);
+    P[k] = (float)((2.0 * u - 1.0) * b);
+}
+
 }  // namespace
 
+cudaError_t launch_mlp_init(float *P, unsigned long long seed, cudaStream_t s) {
+    mlp_init_kernel<<<(kNP + kBlock - 1) / kBlock, kBlock, 0, s>>>(P, seed);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mlp_forward(const float *X, long long ns, const float *P, float *y,
-                               cudaStream_t s) {
+                               cudaStream_t s, const DevStatus *ds, bool gated) {
     if (ns <= 0) return cudaSuccess;
     long long nb = (ns + kBlock - 1) / kBlock;
     int grid = (int)(nb < 152 * 16 ? nb : 152 * 16);
-    mlp_forward_kernel<<<grid, kBlock, 0, s>>>(X, ns, P, y);
+    mlp_forward_kernel<<<grid, kBlock, 0, s>>>(X, ns, P, y, ds, gated);
     return cudaGetLastError();
 }
 
@@ -223,13 +254,14 @@ cudaError_t launch_adam(float *P, const float *G, float *m, float *v, long long 
 
 // scratch: at least ncells + 1 + ncells / kScanTile + 4 int64
 cudaError_t launch_partition(const long long *cost, long long ncells, int nparts,
-                             long long *bounds, long long *scratch, cudaStream_t s) {
+                             long long *bounds, long long *scratch, cudaStream_t s,
+                             const DevStatus *ds, bool gated) {
     long long *excl = scratch;
     long long *bsum = scratch + ncells + 1;
-    cudaError_t e = launch_scan<long long>(cost, excl, (int)ncells, bsum, nullptr, false, s);
+    cudaError_t e = launch_scan<long long>(cost, excl, (int)ncells, bsum, ds, gated, s);
     if (e != cudaSuccess) return e;
     partition_kernel<<<(nparts + 1 + kBlock - 1) / kBlock, kBlock, 0, s>>>(excl, ncells, nparts,
-                                                                          bounds);
+                                                                          bounds, ds, gated);
     return cudaGetLastError();
 }
 

@@ -11,9 +11,8 @@
 // a thin band around r_list^2; outside the band the float32 result cannot
 // decide differently (its error bound is far below the band's half width).
 //
-// List layout: entry k of sorted atom i lives at
-//   nlist[(i / 32) * cap * 32 + k * 32 + i % 32]
-// so a warp reading its k-th entries touches one 128-byte line.  An entry is
+// List layout: see list_idx() -- per warp group of 32 atoms, quads of four
+// entries per atom, written here with one 16-byte store per quad.  An entry is
 // (stencil cell s << 27) | sorted index j; s selects the cell shift
 // (dx, dy, dz) * w that turns cell-relative coordinates into the pair vector.
 #include "md_internal.cuh"
@@ -41,78 +40,106 @@ build_list_kernel(int n, Grid g, float lo, float hi, double rl2, const float4 *_
     }
     __syncthreads();
     if (chain_off(ds, gated)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int cnt = 0;
-    if (i < n) {
-    const int c = cell[i];
-    const int cx = c % g.nx, cy = (c / g.nx) % g.ny, cz = c / (g.nx * g.ny);
-    const float4 qi = xq[i];
-    const double4 ai = xabs[i];
-    const int myo = __float_as_int(qi.w);
-    const size_t base = (size_t)(i >> 5) * (size_t)cap * 32 + (size_t)(i & 31);
-    for (int dz = -1; dz <= 1; ++dz) {
-        int zz = cz + dz;
-        double shz = 0.0;
-        if (zz < 0) { zz += g.nz; shz = -g.L[2]; }
-        else if (zz >= g.nz) { zz -= g.nz; shz = g.L[2]; }
-        for (int dy = -1; dy <= 1; ++dy) {
-            int yy = cy + dy;
-            double shy = 0.0;
-            if (yy < 0) { yy += g.ny; shy = -g.L[1]; }
-            else if (yy >= g.ny) { yy -= g.ny; shy = g.L[1]; }
-            for (int dx = -1; dx <= 1; ++dx) {
-                int xx = cx + dx;
-                double shx = 0.0;
-                if (xx < 0) { xx += g.nx; shx = -g.L[0]; }
-                else if (xx >= g.nx) { xx -= g.nx; shx = g.L[0]; }
-                const int cn = (zz * g.ny + yy) * g.nx + xx;
-                const int s = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
-                const float4 sf = sh[s];
-                const int b = start[cn], e = start[cn + 1];
-                for (int j = b; j < e; ++j) {
-                    if (j == i) continue;
-                    const float4 qj = xq[j];
-                    if (HALF && __float_as_int(qj.w) <= myo) continue;
-                    bool acc;
-                    float r2f = 0.f;
-                    if (PREFILTER) {
-                        float ex = (qj.x - qi.x) + sf.x;
-                        float ey = (qj.y - qi.y) + sf.y;
-                        float ez = (qj.z - qi.z) + sf.z;
-                        r2f = ex * ex + ey * ey + ez * ez;
-                    }
-                    if (PREFILTER && r2f < lo) {
-                        acc = true;
-                    } else if (PREFILTER && r2f >= hi) {
-                        acc = false;
-                    } else {
-                        // the float64 definition, operation for operation
-                        const double4 aj = xabs[j];
-                        double ddx = __dadd_rn(__dadd_rn(aj.x, -ai.x), shx);
-                        double ddy = __dadd_rn(__dadd_rn(aj.y, -ai.y), shy);
-                        double ddz = __dadd_rn(__dadd_rn(aj.z, -ai.z), shz);
-                        double r2 = __dmul_rn(ddx, ddx);
-                        r2 = __dadd_rn(r2, __dmul_rn(ddy, ddy));
-                        r2 = __dadd_rn(r2, __dmul_rn(ddz, ddz));
-                        acc = r2 < rl2;
-                    }
-                    if (acc) {
-                        if (WRITE && cnt < cap)
-                            nlist[base + (size_t)cnt * 32] = ((uint32_t)s << kIndexBits) | (uint32_t)j;
-                        ++cnt;
+    unsigned long long tot = 0;
+    int overflow = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int cnt = 0;
+        const int c = cell[i];
+        const int cx = c % g.nx, cy = (c / g.nx) % g.ny, cz = c / (g.nx * g.ny);
+        const float4 qi = xq[i];
+        const double4 ai = xabs[i];
+        const int myo = __float_as_int(qi.w);
+        uint4 *quads = reinterpret_cast<uint4 *>(nlist + list_group(i, cap)) + (i & 31);
+        uint4 pend = make_uint4(0u, 0u, 0u, 0u);
+        for (int dz = -1; dz <= 1; ++dz) {
+            int zz = cz + dz;
+            double shz = 0.0;
+            if (zz < 0) { zz += g.nz; shz = -g.L[2]; }
+            else if (zz >= g.nz) { zz -= g.nz; shz = g.L[2]; }
+            for (int dy = -1; dy <= 1; ++dy) {
+                int yy = cy + dy;
+                double shy = 0.0;
+                if (yy < 0) { yy += g.ny; shy = -g.L[1]; }
+                else if (yy >= g.ny) { yy -= g.ny; shy = g.L[1]; }
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int xx = cx + dx;
+                    double shx = 0.0;
+                    if (xx < 0) { xx += g.nx; shx = -g.L[0]; }
+                    else if (xx >= g.nx) { xx -= g.nx; shx = g.L[0]; }
+                    const int cn = (zz * g.ny + yy) * g.nx + xx;
+                    const int s = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+                    const float4 sf = sh[s];
+                    const int b = start[cn], e = start[cn + 1];
+                    for (int j0 = b; j0 < e; j0 += 4) {
+                        // four candidate loads in flight before the tests
+                        float4 qj[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            qj[u] = (j0 + u < e) ? xq[j0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int j = j0 + u;
+                            if (j >= e || j == i) continue;
+                            if (HALF && __float_as_int(qj[u].w) <= myo) continue;
+                            bool acc;
+                            float r2f = 0.f;
+                            if (PREFILTER) {
+                                const float ex = (qj[u].x - qi.x) + sf.x;
+                                const float ey = (qj[u].y - qi.y) + sf.y;
+                                const float ez = (qj[u].z - qi.z) + sf.z;
+                                r2f = ex * ex + ey * ey + ez * ez;
+                            }
+                            if (PREFILTER && r2f < lo) {
+                                acc = true;
+                            } else if (PREFILTER && r2f >= hi) {
+                                acc = false;
+                            } else {
+                                // the float64 definition, operation for operation
+                                const double4 aj = xabs[j];
+                                double ddx = __dadd_rn(__dadd_rn(aj.x, -ai.x), shx);
+                                double ddy = __dadd_rn(__dadd_rn(aj.y, -ai.y), shy);
+                                double ddz = __dadd_rn(__dadd_rn(aj.z, -ai.z), shz);
+                                double r2 = __dmul_rn(ddx, ddx);
+                                r2 = __dadd_rn(r2, __dmul_rn(ddy, ddy));
+                                r2 = __dadd_rn(r2, __dmul_rn(ddz, ddz));
+                                acc = r2 < rl2;
+                            }
+                            if (acc) {
+                                if (WRITE && cnt < cap) {
+                                    const uint32_t ent = ((uint32_t)s << kIndexBits) | (uint32_t)j;
+                                    switch (cnt & 3) {
+                                        case 0: pend.x = ent; break;
+                                        case 1: pend.y = ent; break;
+                                        case 2: pend.z = ent; break;
+                                        default:
+                                            pend.w = ent;
+                                            quads[(size_t)(cnt >> 2) * 32] = pend;
+                                    }
+                                }
+                                ++cnt;
+                            }
+                        }
                     }
                 }
             }
         }
+        if (WRITE && cnt <= cap && (cnt & 3)) {
+            // pad the last quad with self-entries that no cutoff accepts
+            const uint32_t pad = (kPadStencil << kIndexBits) | (uint32_t)i;
+            if ((cnt & 3) <= 1) pend.y = pad;
+            if ((cnt & 3) <= 2) pend.z = pad;
+            pend.w = pad;
+            quads[(size_t)(cnt >> 2) * 32] = pend;
+        }
+        ncount[i] = cnt;
+        atomicMax(&ds->max_count, cnt);
+        tot += (unsigned long long)cnt;
+        overflow |= (cnt > cap);
     }
-    ncount[i] = cnt;
-    atomicMax(&ds->max_count, cnt);
-    }
-    // every lane of the block reaches this point (no early return above)
-    unsigned long long tot = (unsigned long long)cnt;
+    // every lane of the block reaches this point (grid-stride loop, no early exit)
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&ds->list_entries, tot);
-    if (WRITE && cnt > cap) atomicCAS(&ds->status, 0, (int)MD_ERR_LIST_OVERFLOW);
+    if (WRITE && overflow) atomicCAS(&ds->status, 0, (int)MD_ERR_LIST_OVERFLOW);
 }
 
 __global__ void reset_max_count_kernel(DevStatus *ds, bool gated) {
@@ -141,9 +168,8 @@ __global__ void export_rowcount_kernel(int n, int cap, int half, const int32_t *
     int keep = cnt;
     if (half) {
         keep = 0;
-        size_t base = (size_t)(i >> 5) * (size_t)cap * 32 + (size_t)(i & 31);
         for (int k = 0; k < cnt; ++k) {
-            int j = (int)(nlist[base + (size_t)k * 32] & kIndexMask);
+            int j = (int)(nlist[list_idx(i, k, cap)] & kIndexMask);
             keep += (orig[j] > o);
         }
     }
@@ -159,11 +185,10 @@ __global__ void export_fill_kernel(int n, int cap, int half, const int32_t *__re
     if (i >= n) return;
     int o = orig[i];
     int cnt = min(ncount[i], cap);
-    size_t base = (size_t)(i >> 5) * (size_t)cap * 32 + (size_t)(i & 31);
     int64_t p0 = rowstart[o];
     int64_t p = p0;
     for (int k = 0; k < cnt; ++k) {
-        int j = (int)(nlist[base + (size_t)k * 32] & kIndexMask);
+        int j = (int)(nlist[list_idx(i, k, cap)] & kIndexMask);
         int oj = orig[j];
         if (!half || oj > o) ids[p++] = oj;
     }
@@ -190,7 +215,7 @@ cudaError_t launch_build_list(md_system *h, bool write, bool gated) {
     const bool half = (h->p.force_variant != MD_FORCE_FULL);
     reset_max_count_kernel<<<1, 1, 0, s>>>(h->ds, gated);
 #define MDG_LIST(PF, WR, HF)                                                                    \
-    build_list_kernel<PF, WR, HF><<<nblocks(n), kBlock, 0, s>>>(                                \
+    build_list_kernel<PF, WR, HF><<<gs_blocks(n), kBlock, 0, s>>>(                                \
         n, h->g, h->list_lo, h->list_hi, h->rl2, h->xq[cur], h->xabs, h->cell, h->cell_start, \
         h->nlist, h->ncount, h->cap, h->ds, gated)
     if (prefilter) {

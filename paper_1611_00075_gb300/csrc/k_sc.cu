@@ -83,16 +83,15 @@ __global__ void __launch_bounds__(kBlock) sc_density_mixed(ForceArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const float4 qi = a.xq[i];
-    const int cnt = min(a.ncount[i], a.cap);
-    const uint32_t *lp = a.nlist + (size_t)(i >> 5) * (size_t)a.cap * 32 + (size_t)(i & 31);
+    const int nq = (min(a.ncount[i], a.cap) + 3) >> 2;
+    const uint4 *lq = reinterpret_cast<const uint4 *>(a.nlist + list_group(i, a.cap)) + (i & 31);
     const float rc2 = a.fc.rc2f, af = a.fc.sc_af, a2 = af * af;
     const int m = a.fc.sc_m;
     double R = 0.0;
-    for (int k0 = 0; k0 < cnt; k0 += kChunk) {
-        const int k1 = min(k0 + kChunk, cnt);
+    for (int q0 = 0; q0 < nq; q0 += kChunkQ) {
+        const int q1 = min(q0 + kChunkQ, nq);
         float r = 0.f;
-        for (int k = k0; k < k1; ++k) {
-            const uint32_t ent = __ldg(lp + (size_t)k * 32);
+        auto pair = [&](uint32_t ent) {
             const float4 qj = __ldg(a.xq + (ent & kIndexMask));
             const float4 sf = sh[ent >> kIndexBits];
             const float ex = (qj.x - qi.x) + sf.x;
@@ -106,6 +105,14 @@ __global__ void __launch_bounds__(kBlock) sc_density_mixed(ForceArgs a) {
                 else psi = (m & 1) ? rpow(s, m / 2) * af * rsqrtf(r2) : rpow(s, m / 2);
                 r += psi;
             }
+        };
+#pragma unroll 2
+        for (int q = q0; q < q1; ++q) {
+            const uint4 e4 = __ldg(lq + (size_t)q * 32);
+            pair(e4.x);
+            pair(e4.y);
+            pair(e4.z);
+            pair(e4.w);
         }
         R += (double)r;
     }
@@ -126,12 +133,11 @@ __global__ void __launch_bounds__(kBlock) sc_density_fp64(ForceArgs a) {
     if (i >= a.n) return;
     const double4 ri = a.xr[i];
     const int cnt = min(a.ncount[i], a.cap);
-    const uint32_t *lp = a.nlist + (size_t)(i >> 5) * (size_t)a.cap * 32 + (size_t)(i & 31);
     const double rc2 = a.fc.rc2, A = a.fc.sc_a;
     const int m = a.fc.sc_m;
     double R = 0.0;
     for (int k = 0; k < cnt; ++k) {
-        const uint32_t ent = __ldg(lp + (size_t)k * 32);
+        const uint32_t ent = __ldg(a.nlist + list_idx(i, k, a.cap));
         const double4 rj = a.xr[ent & kIndexMask];
         const double3 sd = sh[ent >> kIndexBits];
         const double ex = (rj.x - ri.x) + sd.x;
@@ -162,18 +168,17 @@ __global__ void __launch_bounds__(kBlock) sc_force_mixed(ForceArgs a, int store_
     if (i >= a.n) return;
     const float4 qi = a.xq[i];
     const float dFi = a.dF32[i];
-    const int cnt = min(a.ncount[i], a.cap);
-    const uint32_t *lp = a.nlist + (size_t)(i >> 5) * (size_t)a.cap * 32 + (size_t)(i & 31);
+    const int nq = (min(a.ncount[i], a.cap) + 3) >> 2;
+    const uint4 *lq = reinterpret_cast<const uint4 *>(a.nlist + list_group(i, a.cap)) + (i & 31);
     const float rc2 = a.fc.rc2f, af = a.fc.sc_af, a2 = af * af, epsf = a.fc.sc_epsf;
     const int nexp = a.fc.sc_n, mexp = a.fc.sc_m;
     const float nf = (float)(NE > 0 ? NE : nexp), mf = (float)(ME > 0 ? ME : mexp);
     double Fx = 0.0, Fy = 0.0, Fz = 0.0, E = 0.0;
     unsigned npair = 0;
-    for (int k0 = 0; k0 < cnt; k0 += kChunk) {
-        const int k1 = min(k0 + kChunk, cnt);
+    for (int q0 = 0; q0 < nq; q0 += kChunkQ) {
+        const int q1 = min(q0 + kChunkQ, nq);
         float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
-        for (int k = k0; k < k1; ++k) {
-            const uint32_t ent = __ldg(lp + (size_t)k * 32);
+        auto pair = [&](uint32_t ent) {
             const int j = (int)(ent & kIndexMask);
             const float4 qj = __ldg(a.xq + j);
             const float4 sf = sh[ent >> kIndexBits];
@@ -204,6 +209,14 @@ __global__ void __launch_bounds__(kBlock) sc_force_mixed(ForceArgs a, int store_
                     ++npair;
                 }
             }
+        };
+#pragma unroll 2
+        for (int q = q0; q < q1; ++q) {
+            const uint4 e4 = __ldg(lq + (size_t)q * 32);
+            pair(e4.x);
+            pair(e4.y);
+            pair(e4.z);
+            pair(e4.w);
         }
         Fx += (double)fx;
         Fy += (double)fy;
@@ -239,13 +252,12 @@ __global__ void __launch_bounds__(kBlock) sc_force_fp64(ForceArgs a, int store_f
     const double4 ri = a.xr[i];
     const double dFi = a.dF64[i];
     const int cnt = min(a.ncount[i], a.cap);
-    const uint32_t *lp = a.nlist + (size_t)(i >> 5) * (size_t)a.cap * 32 + (size_t)(i & 31);
     const double rc2 = a.fc.rc2, A = a.fc.sc_a, eps = a.fc.sc_eps;
     const int nexp = a.fc.sc_n, mexp = a.fc.sc_m;
     double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0;
     unsigned npair = 0;
     for (int k = 0; k < cnt; ++k) {
-        const uint32_t ent = __ldg(lp + (size_t)k * 32);
+        const uint32_t ent = __ldg(a.nlist + list_idx(i, k, a.cap));
         const int j = (int)(ent & kIndexMask);
         const double4 rj = a.xr[j];
         const double3 sd = sh[ent >> kIndexBits];

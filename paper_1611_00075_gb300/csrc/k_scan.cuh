@@ -84,9 +84,9 @@ template <class T>
 __global__ void scan_add_kernel(T *out, int n, const T *__restrict__ bsum, int nb,
                                 const DevStatus *ds, bool gated) {
     if (scan_off(ds, gated)) return;
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx < n) out[idx] += bsum[idx / kScanTile];
-    if (idx == 0) out[n] = bsum[nb];
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x)
+        out[idx] += bsum[idx / kScanTile];
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = bsum[nb];
 }
 
 // bsum must hold at least n / kScanTile + 2 elements.
@@ -97,7 +97,7 @@ inline cudaError_t launch_scan(const T *in, T *out, int n, T *bsum, const DevSta
     if (nb < 1) nb = 1;
     scan_block_kernel<T><<<nb, kBlock, 0, s>>>(in, out, n, bsum, ds, gated);
     scan_bsum_kernel<T><<<1, kBlock, 0, s>>>(bsum, nb, ds, gated);
-    scan_add_kernel<T><<<nblocks(n > 0 ? n : 1), kBlock, 0, s>>>(out, n, bsum, nb, ds, gated);
+    scan_add_kernel<T><<<gs_blocks(n), kBlock, 0, s>>>(out, n, bsum, nb, ds, gated);
     return cudaGetLastError();
 }
 

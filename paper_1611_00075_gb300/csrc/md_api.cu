@@ -89,6 +89,10 @@ void free_all(md_system *h) {
     F(h->scan_bsum); F(h->tmp_abs); F(h->tmp_v); F(h->tmp_orig); F(h->nlist); F(h->ncount);
     F(h->rho); F(h->dF32); F(h->dF64); F(h->partials); F(h->red_out); F(h->ds);
     F(h->exp_tmp);
+    F(h->part_bounds); F(h->cell_cost); F(h->part_scratch); F(h->cell_X); F(h->cell_pred);
+    F(h->cell_cycles); F(h->cta_cycles); F(h->samp_flag); F(h->samp_bsum); F(h->samp_X);
+    F(h->samp_y); F(h->mlp_P); F(h->mlp_G); F(h->mlp_m); F(h->mlp_v); F(h->mlp_scratch);
+    F(h->mlp_loss);
     if (h->ds_host) cudaFreeHost(h->ds_host);
     if (h->red_host) cudaFreeHost(h->red_host);
 }
@@ -115,6 +119,8 @@ md_status read_status(md_system *h) {
 
 md_status clear_status(md_system *h) {
     MD_CK(cudaMemsetAsync(&h->ds->status, 0, sizeof(int), h->stream));
+    // a launch that stopped early may have left the tile queue mid-count
+    MD_CK(cudaMemsetAsync(&h->ds->tile_counter, 0, 2 * sizeof(int), h->stream));
     return MD_OK;
 }
 
@@ -146,13 +152,78 @@ void harvest(md_system *h) {
     h->ev_used = 0;
 }
 
+// ---- persistent scheduler ----------------------------------------------------
+
+// The persistent kernel serves the mixed-precision Lennard-Jones full-list
+// force pass; every other combination uses the one-thread-per-atom grid.
+bool persistent_path(const md_system *h) {
+    return h->p.scheduler != MD_SCHED_GRID && h->p.potential == MD_POT_LJ &&
+           h->p.precision == MD_MIXED && h->p.force_variant == MD_FORCE_FULL;
+}
+
+bool uses_partition(const md_system *h) {
+    return persistent_path(h) &&
+           (h->p.scheduler == MD_SCHED_PAIRCOUNT || h->p.scheduler == MD_SCHED_MLP);
+}
+
+// Buffers of the scheduler and the cost model, allocated on first use.
+md_status ensure_sched(md_system *h) {
+    if (h->part_bounds) return MD_OK;
+    int dev = 0, sms = 0;
+    MD_CK(cudaGetDevice(&dev));
+    MD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    h->sched_ctas = sms * persist_ctas_per_sm();
+    const size_t C = (size_t)h->g.ncells;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A(dalloc(&h->part_bounds, (size_t)h->sched_ctas + 1));
+    A(dalloc(&h->cell_cost, C));
+    A(dalloc(&h->part_scratch, C + 1 + C / (kBlock * 8) + 8));
+    A(dalloc(&h->cell_X, 3 * C));
+    A(dalloc(&h->cell_pred, C));
+    A(dalloc(&h->cell_cycles, C));
+    A(dalloc(&h->cta_cycles, (size_t)h->sched_ctas));
+    A(dalloc(&h->samp_flag, 2 * (C + 1) + 2));  // flags, their scan, sample count
+    A(dalloc(&h->samp_bsum, C / (kBlock * 8) + 8));
+    A(dalloc(&h->samp_X, 3 * C));
+    A(dalloc(&h->samp_y, C));
+    A(dalloc(&h->mlp_P, kMlpParams));
+    A(dalloc(&h->mlp_G, kMlpParams));
+    A(dalloc(&h->mlp_m, kMlpParams));
+    A(dalloc(&h->mlp_v, kMlpParams));
+    A(dalloc(&h->mlp_scratch, mlp_grad_scratch_floats((long long)C)));
+    A(dalloc(&h->mlp_loss, 1));
+    if (e != cudaSuccess)
+        return fail(h, e == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA,
+                    std::string("scheduler allocation: ") + cudaGetErrorString(e));
+    MD_CK(launch_mlp_init(h->mlp_P, 0x1611000075ull, h->stream));
+    MD_CK(cudaMemsetAsync(h->mlp_m, 0, kMlpParams * sizeof(float), h->stream));
+    MD_CK(cudaMemsetAsync(h->mlp_v, 0, kMlpParams * sizeof(float), h->stream));
+    h->mlp_t = 0;
+    return MD_OK;
+}
+
+// Cost estimate and equal-cost partition of the cells over the persistent
+// CTAs; part of the rebuild chain (gated) or run right away.
+md_status enqueue_sched_prep(md_system *h, bool gated) {
+    if (!uses_partition(h)) return MD_OK;
+    const bool pc = (h->p.scheduler == MD_SCHED_PAIRCOUNT);
+    MD_CK(launch_cell_features(h, pc, gated));
+    if (!pc) MD_CK(launch_predict_costs(h, gated));
+    MD_CK(launch_partition_cells(h, gated));
+    h->launches += pc ? 5 : 7;
+    return MD_OK;
+}
+
 // Rebuild chain enqueued before a force evaluation.  gated: runs only if the
 // device flag asks for it.
 md_status enqueue_rebuild(md_system *h, bool gated) {
     MD_CK(launch_bin(h, gated));
     MD_CK(launch_build_list(h, true, gated));
-    MD_CK(launch_finish_rebuild(h, gated));
     h->launches += 13;
+    md_status st = enqueue_sched_prep(h, gated);
+    if (st != MD_OK) return st;
+    MD_CK(launch_finish_rebuild(h, gated));
     MD_CK(mark(h, K_REBUILD));
     return MD_OK;
 }
@@ -166,7 +237,7 @@ md_status rebuild_now(md_system *h, bool size_from_count) {
         if (st != MD_OK) return st;
         if (h->ds_host->status != 0)
             return fail(h, (md_status)h->ds_host->status, "device error during list count");
-        int cap = h->p.max_neighbors > 0 ? h->p.max_neighbors : cap_for(h->ds_host->max_count);
+        int cap = h->p.max_neighbors > 0 ? ((h->p.max_neighbors + 3) & ~3) : cap_for(h->ds_host->max_count);
         cap = std::max(cap, 8);
         if (cap != h->cap || h->nlist == nullptr) MD_CK(alloc_list(h, cap));
     }
@@ -183,6 +254,8 @@ md_status rebuild_now(md_system *h, bool size_from_count) {
         if (st != MD_OK) return st;
         MD_CK(alloc_list(h, cap_for(h->ds_host->max_count)));
     }
+    md_status st = enqueue_sched_prep(h, false);
+    if (st != MD_OK) return st;
     MD_CK(launch_finish_rebuild(h, false));
     h->list_valid = true;
     h->forces_valid = false;
@@ -194,6 +267,13 @@ md_status enqueue_forces(md_system *h, int mode, bool energy, bool store_f) {
         MD_CK(launch_sc_density(h));
         MD_CK(launch_sc_force(h, mode, energy, store_f));
         h->launches += 2;
+    } else if (h->p.force_variant != MD_FORCE_FULL) {
+        int nl = 0;
+        MD_CK(launch_lj_half(h, mode, energy, &nl));
+        h->launches += nl;
+    } else if (persistent_path(h) && !energy) {
+        MD_CK(launch_lj_persist(h, mode, store_f, h->p.scheduler == MD_SCHED_DYNAMIC, false));
+        h->launches += 1;
     } else {
         MD_CK(launch_lj(h, mode, energy, store_f));
         h->launches += 1;
@@ -250,10 +330,8 @@ md_status md_create(md_system **out, const md_params *p, int64_t n, const double
         return fail(nullptr, MD_ERR_INVALID, "md_create: " + why);
     if (p->force_variant != MD_FORCE_FULL && p->potential == MD_POT_SC)
         return fail(nullptr, MD_ERR_INVALID, "md_create: half lists are built for Lennard-Jones only");
-    if (p->force_variant != MD_FORCE_FULL)
-        return fail(nullptr, MD_ERR_INVALID, "md_create: half-list force kernels are not built yet");
-    if (p->scheduler != MD_SCHED_GRID)
-        return fail(nullptr, MD_ERR_INVALID, "md_create: persistent schedulers are not built yet");
+    if (p->force_variant != MD_FORCE_FULL && p->precision != MD_MIXED)
+        return fail(nullptr, MD_ERR_INVALID, "md_create: half lists are built for the mixed path");
     h = new (std::nothrow) md_system();
     if (!h) return fail(nullptr, MD_ERR_OOM, "md_create: host allocation failed");
     h->p = *p;
@@ -323,6 +401,7 @@ md_status md_create(md_system **out, const md_params *p, int64_t n, const double
     step(cudaMemsetAsync(h->e_atom, 0, N * sizeof(double), h->stream), "memset e");
     if (!vel_dev) step(cudaMemsetAsync(h->v, 0, 3 * N * sizeof(double), h->stream), "memset v");
     step(launch_load_state(h, pos_dev, vel_dev), "load_state");
+    if (st == MD_OK && p->scheduler != MD_SCHED_GRID) st = ensure_sched(h);
     if (st == MD_OK) st = rebuild_now(h, true);
     if (st == MD_OK) st = forces_now(h, false);
     if (st != MD_OK) {
@@ -546,14 +625,115 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
         return fail(h, MD_ERR_INVALID, "md_set_variant: unknown variant or scheduler");
     if (force_variant != MD_FORCE_FULL && h->p.potential == MD_POT_SC)
         return fail(h, MD_ERR_INVALID, "md_set_variant: half lists are built for Lennard-Jones only");
+    if (force_variant != MD_FORCE_FULL && h->p.precision != MD_MIXED)
+        return fail(h, MD_ERR_INVALID, "md_set_variant: half lists are built for the mixed path");
     const bool relist = (force_variant != MD_FORCE_FULL) != (h->p.force_variant != MD_FORCE_FULL);
     h->p.force_variant = force_variant;
     h->p.scheduler = scheduler;
-    if (relist) {
-        md_status st = rebuild_now(h, true);
-        if (st != MD_OK) return st;
+    md_status st = MD_OK;
+    if (scheduler != MD_SCHED_GRID) st = ensure_sched(h);
+    if (st != MD_OK) return st;
+    if (relist || !h->list_valid) return rebuild_now(h, true);
+    // same list: only the partition of the new scheduler is needed
+    return enqueue_sched_prep(h, false);
+}
+
+// Per-CTA cycles of one timed force pass, reduced on the host to max / mean.
+md_status cta_imbalance(md_system *h, float *out) {
+    std::vector<float> c((size_t)h->sched_ctas);
+    MD_CK(cudaMemcpyAsync(c.data(), h->cta_cycles, c.size() * sizeof(float),
+                          cudaMemcpyDeviceToHost, h->stream));
+    MD_CK(cudaStreamSynchronize(h->stream));
+    double mx = 0.0, sum = 0.0;
+    for (float v : c) {
+        mx = std::max(mx, (double)v);
+        sum += v;
     }
+    if (out) *out = (float)(sum > 0 ? mx / (sum / c.size()) : 0.0);
     return MD_OK;
+}
+
+md_status md_cost_model(md_system *h, int32_t op, float *loss_out) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_cost_model: null handle");
+    if (h->p.potential != MD_POT_LJ || h->p.precision != MD_MIXED ||
+        h->p.force_variant != MD_FORCE_FULL)
+        return fail(h, MD_ERR_INVALID,
+                    "md_cost_model: the cost model drives the persistent mixed-precision "
+                    "Lennard-Jones full-list force kernel");
+    md_status st = ensure_sched(h);
+    if (st != MD_OK) return st;
+    const int kPasses = 3, kIters = 400;
+    const float kLr = 3e-3f;
+    switch (op) {
+        case MD_COST_RESET:
+            MD_CK(launch_mlp_init(h->mlp_P, 0x1611000075ull, h->stream));
+            MD_CK(cudaMemsetAsync(h->mlp_m, 0, kMlpParams * sizeof(float), h->stream));
+            MD_CK(cudaMemsetAsync(h->mlp_v, 0, kMlpParams * sizeof(float), h->stream));
+            h->mlp_t = 0;
+            MD_CK(cudaStreamSynchronize(h->stream));
+            return MD_OK;
+        case MD_COST_SAMPLE: {
+            // a current list, then kPasses timed force passes under the tile queue
+            st = enqueue_rebuild(h, true);
+            if (st != MD_OK) return st;
+            MD_CK(cudaMemsetAsync(h->cell_cycles, 0, (size_t)h->g.ncells * sizeof(float),
+                                  h->stream));
+            for (int r = 0; r < kPasses; ++r) MD_CK(launch_lj_persist(h, FM_STORE, true, true, true));
+            MD_CK(launch_cell_features(h, false, false));
+            int32_t *cnt_dev = h->samp_flag + 2 * ((size_t)h->g.ncells + 1);
+            MD_CK(launch_make_samples(h, kPasses, cnt_dev));
+            int32_t cnt = 0;
+            MD_CK(cudaMemcpyAsync(&cnt, cnt_dev, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                  h->stream));
+            st = read_status(h);
+            if (st != MD_OK) return st;
+            if (h->ds_host->status != 0)
+                return fail(h, (md_status)h->ds_host->status, "md_cost_model: device error");
+            h->samp_n = cnt;
+            h->forces_valid = true;
+            if (loss_out) *loss_out = (float)cnt;
+            return MD_OK;
+        }
+        case MD_COST_TRAIN: {
+            if (h->samp_n <= 0) return fail(h, MD_ERR_INVALID, "md_cost_model: no samples");
+            for (int it = 0; it < kIters; ++it) {
+                MD_CK(launch_mlp_loss_grad(h->samp_X, h->samp_y, h->samp_n, h->mlp_P, h->mlp_G,
+                                           h->mlp_loss, h->mlp_scratch, h->stream));
+                MD_CK(launch_adam(h->mlp_P, h->mlp_G, h->mlp_m, h->mlp_v, kMlpParams, ++h->mlp_t,
+                                  kLr, 0.9f, 0.999f, 1e-8f, h->stream));
+            }
+            MD_CK(launch_mlp_loss_grad(h->samp_X, h->samp_y, h->samp_n, h->mlp_P, h->mlp_G,
+                                       h->mlp_loss, h->mlp_scratch, h->stream));
+            float loss = 0.f;
+            MD_CK(cudaMemcpyAsync(&loss, h->mlp_loss, sizeof(float), cudaMemcpyDeviceToHost,
+                                  h->stream));
+            MD_CK(cudaStreamSynchronize(h->stream));
+            if (loss_out) *loss_out = loss;
+            return MD_OK;
+        }
+        case MD_COST_PREDICT:
+            MD_CK(launch_cell_features(h, false, false));
+            MD_CK(launch_predict_costs(h, false));
+            MD_CK(launch_partition_cells(h, false));
+            MD_CK(cudaStreamSynchronize(h->stream));
+            return MD_OK;
+        case MD_COST_PROFILE: {
+            // one timed force pass with the current scheduler: max / mean CTA cycles
+            st = enqueue_rebuild(h, true);
+            if (st != MD_OK) return st;
+            MD_CK(cudaMemsetAsync(h->cell_cycles, 0, (size_t)h->g.ncells * sizeof(float),
+                                  h->stream));
+            MD_CK(launch_lj_persist(h, FM_STORE, true, h->p.scheduler != MD_SCHED_PAIRCOUNT &&
+                                                            h->p.scheduler != MD_SCHED_MLP,
+                                    true));
+            st = read_status(h);
+            if (st != MD_OK) return st;
+            h->forces_valid = true;
+            return cta_imbalance(h, loss_out);
+        }
+        default:
+            return fail(h, MD_ERR_INVALID, "md_cost_model: unknown op");
+    }
 }
 
 md_status md_stats(md_system *h, char *buf_host, size_t cap) {
@@ -588,12 +768,6 @@ md_status md_set_timing(md_system *h, int32_t on) {
     }
     h->launches = 0;
     return MD_OK;
-}
-
-md_status md_cost_model(md_system *h, int32_t op, float *loss_out) {
-    (void)op;
-    (void)loss_out;
-    return fail(h, MD_ERR_INVALID, "md_cost_model: persistent schedulers are not built yet");
 }
 
 const char *md_last_error(md_system *h) {

@@ -19,6 +19,42 @@ constexpr int kIndexBits = 27;    // list entry = (stencil << 27) | sorted index
 constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
 constexpr int64_t kMaxAtoms = (int64_t)1 << kIndexBits;
 
+// Neighbour-list layout.  Atoms are grouped by 32 (one warp); inside a group
+// each atom's entries are stored in quads: uint32 [n/32][cap/4][32][4].  A
+// lane reads its quad q with one 16-byte load, and the 32 lanes' loads of quad
+// q are 512 contiguous bytes.  cap is a multiple of 4.  Every list is padded
+// to a multiple of 4 entries with kPadStencil entries pointing at the atom
+// itself: that image lies at (w_x, w_y, w_z), at least sqrt(3) r_list away,
+// so every cutoff test rejects it and the pair loops need no tail handling.
+constexpr uint32_t kPadStencil = 26;  // stencil cell (+1, +1, +1)
+
+__host__ __device__ __forceinline__ size_t list_group(int i, int cap) {
+    return (size_t)(i >> 5) * (size_t)cap * 32;
+}
+__host__ __device__ __forceinline__ size_t list_idx(int i, int k, int cap) {
+    return list_group(i, cap) + (size_t)(k >> 2) * 128 + (size_t)((i & 31) << 2) + (size_t)(k & 3);
+}
+
+// Cell colouring for the half-list force pass without atomics.  Per
+// dimension of n >= 3 cells, cells below m = 3 floor(n / 3) take colour
+// c mod 3 and the (n - m) tail cells take colours 3, 4.  Two distinct cells
+// of one colour then differ by >= 3 cells (periodically) in some dimension,
+// so their 27-cell neighbourhoods -- everything a cell's atoms may write --
+// are disjoint.  Colours per dimension: 3 + n mod 3.
+__host__ __device__ __forceinline__ int color_1d(int c, int n) {
+    const int m = (n / 3) * 3;
+    return c < m ? c % 3 : 3 + (c - m);
+}
+__host__ __device__ __forceinline__ int colors_1d(int n) { return 3 + n % 3; }
+// number of cells of colour k along a dimension of n cells
+__host__ __device__ __forceinline__ int color_count_1d(int k, int n) {
+    return k < 3 ? n / 3 : 1;
+}
+// t-th cell of colour k along a dimension
+__host__ __device__ __forceinline__ int color_cell_1d(int k, int t, int n) {
+    return k < 3 ? k + 3 * t : (n / 3) * 3 + (k - 3);
+}
+
 // Device status word.  Every kernel of a step returns at entry when `status`
 // is non-zero, so an error stops the rest of the enqueued work and the host
 // finds the state exactly where it stopped.
@@ -35,7 +71,18 @@ struct DevStatus {
     int pad0;
     unsigned long long list_entries;  // entries of the last list build
     unsigned long long pairs_cut;     // pairs inside r_c of the last energy evaluation
-    long long pad1[2];
+    int tile_counter;                 // dynamic scheduler: next unclaimed tile
+    unsigned int done_ctas;           // dynamic scheduler: CTAs finished this launch
+    long long pad1;
+};
+
+// What the persistent force kernel needs besides ForceArgs.
+struct SchedArgs {
+    const int32_t *cell_start;  // ncells + 1
+    const long long *bounds;    // partition of cells over CTAs (gridDim.x + 1)
+    const int32_t *cell;        // sorted slot -> cell
+    float *cell_cycles;         // TIMING: per-cell cycles (accumulated)
+    float *cta_cycles;          // TIMING: per-CTA busy cycles
 };
 
 // Geometry passed by value to kernels.
@@ -119,6 +166,25 @@ struct md_system {
 
     int64_t *exp_tmp = nullptr;  // scratch of md_get_neighbors
 
+    // persistent scheduler and learned cost model (allocated on first use)
+    int sched_ctas = 0;                 // resident CTAs of the persistent force kernel
+    long long *part_bounds = nullptr;   // sched_ctas + 1 cell bounds
+    long long *cell_cost = nullptr;     // quantised per-cell cost (ncells)
+    long long *part_scratch = nullptr;  // prefix sums of the partition
+    float *cell_X = nullptr;            // features, ncells x 3
+    float *cell_pred = nullptr;         // model outputs, ncells
+    float *cell_cycles = nullptr;       // measured per-cell cycles, ncells
+    float *cta_cycles = nullptr;        // measured per-CTA cycles, sched_ctas
+    int32_t *samp_flag = nullptr;       // ncells + 1 (non-empty flags, then their scan)
+    int32_t *samp_bsum = nullptr;
+    float *samp_X = nullptr, *samp_y = nullptr;  // training set, compacted
+    int64_t samp_n = 0;
+    float *mlp_P = nullptr, *mlp_G = nullptr, *mlp_m = nullptr, *mlp_v = nullptr;
+    float *mlp_scratch = nullptr;       // gradient partials
+    float *mlp_loss = nullptr;          // device scalar
+    int64_t mlp_t = 0;                  // Adam step count
+    bool partition_valid = false;
+
     mdg::DevStatus *ds = nullptr;       // device
     mdg::DevStatus *ds_host = nullptr;  // pinned mirror
     double *red_host = nullptr;         // pinned
@@ -159,6 +225,11 @@ cudaError_t launch_export_list(md_system *h, int half, int64_t *offsets, int32_t
 
 // ---- forces (k_lj.cu, k_sc.cu) -------------------------------------------
 cudaError_t launch_lj(md_system *h, int mode, bool energy, bool store_f);
+// half-list LJ (mixed precision): zero f, force pass(es), integrate
+cudaError_t launch_lj_half(md_system *h, int mode, bool energy, int *launches);
+// persistent LJ kernel (mixed precision, full list); timing only with FM_STORE
+cudaError_t launch_lj_persist(md_system *h, int mode, bool store_f, bool dynamic, bool timing);
+int persist_ctas_per_sm();
 cudaError_t launch_sc_density(md_system *h);
 cudaError_t launch_sc_force(md_system *h, int mode, bool energy, bool store_f);
 
@@ -172,6 +243,36 @@ cudaError_t launch_reduce_pe(md_system *h);
 cudaError_t launch_reduce_ke(md_system *h);
 cudaError_t launch_set_rebuild(md_system *h);
 
+// ---- scheduler and cost model (k_sched.cu, k_mlp.cu) ----------------------
+constexpr int kMlpParams = 1217;
+// features of every cell; with paircount != 0 also cell_cost = list entries
+cudaError_t launch_cell_features(md_system *h, bool paircount, bool gated);
+// model inference on cell_X, quantised into cell_cost
+cudaError_t launch_predict_costs(md_system *h, bool gated);
+// equal-cost partition of cell_cost into part_bounds
+cudaError_t launch_partition_cells(md_system *h, bool gated);
+// training set: non-empty cells' features and log cycles (count to samp_count_dev)
+cudaError_t launch_make_samples(md_system *h, int passes, int32_t *samp_count_dev);
+cudaError_t launch_mlp_init(float *P, unsigned long long seed, cudaStream_t s);
+cudaError_t launch_mlp_forward(const float *X, long long ns, const float *P, float *y,
+                               cudaStream_t s, const DevStatus *ds = nullptr, bool gated = false);
+size_t mlp_grad_scratch_floats(long long ns);
+cudaError_t launch_mlp_loss_grad(const float *X, const float *Y, long long ns, const float *P,
+                                 float *G, float *loss, float *scratch, cudaStream_t s);
+cudaError_t launch_adam(float *P, const float *G, float *m, float *v, long long np, long long t,
+                        float lr, float b1, float b2, float eps, cudaStream_t s);
+cudaError_t launch_partition(const long long *cost, long long ncells, int nparts,
+                             long long *bounds, long long *scratch, cudaStream_t s,
+                             const DevStatus *ds = nullptr, bool gated = false);
+
 inline int nblocks(int64_t n, int b = kBlock) { return (int)((n + b - 1) / b); }
+
+// Grids of the grid-stride kernels (rebuild chain): enough blocks to fill the
+// GPU, few enough that a launch whose gate is closed costs microseconds.
+constexpr int kGridCap = 152 * 8;
+inline int gs_blocks(int64_t n) {
+    const int b = nblocks(n);
+    return b < 1 ? 1 : (b < kGridCap ? b : kGridCap);
+}
 
 }  // namespace mdg

@@ -32,7 +32,7 @@ MD_POT_LJ, MD_POT_SC = 0, 1
 MD_FP64, MD_MIXED = 0, 1
 MD_FORCE_FULL, MD_FORCE_HALF_COLOR, MD_FORCE_HALF_ATOMIC = 0, 1, 2
 MD_SCHED_GRID, MD_SCHED_PAIRCOUNT, MD_SCHED_MLP, MD_SCHED_DYNAMIC = 0, 1, 2, 3
-MD_COST_TRAIN, MD_COST_PREDICT, MD_COST_RESET, MD_COST_SAMPLE = 0, 1, 2, 3
+MD_COST_TRAIN, MD_COST_PREDICT, MD_COST_RESET, MD_COST_SAMPLE, MD_COST_PROFILE = 0, 1, 2, 3, 4
 MLP_NPARAMS = 1217
 
 
@@ -73,7 +73,7 @@ def lib() -> C.CDLL:
         "md_get_cells": [vp, vp, vp, vp], "md_get_density": [vp, vp, vp],
         "md_get_atom_energy": [vp, vp], "md_set_variant": [vp, i32, i32],
         "md_cost_model": [vp, i32, vp], "md_stats": [vp, C.c_char_p, C.c_size_t],
-        "md_set_timing": [vp, i32],
+        "md_set_timing": [vp, i32], "md_color_cells": [vp, vp, vp],
         "md_mlp_forward": [vp, i64, vp, vp, vp],
         "md_mlp_loss_grad": [vp, vp, i64, vp, vp, vp, vp],
         "md_mlp_adam": [vp, vp, vp, vp, i64, i64, C.c_float, C.c_float, C.c_float,
@@ -199,6 +199,18 @@ def md_cost_model(h, op: int) -> float:
 
 def md_set_timing(h, on: bool):
     _check(lib().md_set_timing(h, int(bool(on))), h, "md_set_timing")
+
+
+def md_color_cells(ncell):
+    """Cell colours of the half-list colouring (host call, no GPU); returns a
+    list of int colours in linear cell order and the colour count."""
+    nc = (C.c_int32 * 3)(*[int(x) for x in ncell])
+    total = int(ncell[0]) * int(ncell[1]) * int(ncell[2])
+    col = (C.c_int32 * total)()
+    k = C.c_int32()
+    _check(lib().md_color_cells(C.cast(nc, C.c_void_p), C.cast(col, C.c_void_p), C.byref(k)),
+           None, "md_color_cells")
+    return list(col), k.value
 
 
 def md_stats(h) -> str:

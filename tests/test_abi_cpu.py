@@ -64,3 +64,30 @@ def test_python_binding_names_match_c_abi(libpath):
         if n == "md_last_error":
             continue
         assert hasattr(md, n), n
+
+
+@pytest.mark.parametrize("ncell", [(3, 3, 3), (4, 5, 6), (7, 3, 8), (9, 10, 11), (5, 5, 5)])
+def test_cell_colouring_is_conflict_free(libpath, ncell):
+    """Race check of MD_FORCE_HALF_COLOR on the host: two distinct cells of one
+    colour must have disjoint (periodic) 27-cell neighbourhoods, since a cell's
+    force task writes to every atom of its neighbourhood."""
+    import numpy as np
+    from paper_1611_00075_gb300 import md
+    col, k = md.md_color_cells(ncell)
+    nx, ny, nz = ncell
+    col = np.array(col).reshape(nz, ny, nx)
+    assert len(np.unique(col)) == k
+    def neigh(c):
+        x, y, z = c
+        return {((x + a) % nx, (y + b) % ny, (z + d) % nz)
+                for a in (-1, 0, 1) for b in (-1, 0, 1) for d in (-1, 0, 1)}
+    cells = [(x, y, z) for z in range(nz) for y in range(ny) for x in range(nx)]
+    by_colour = {}
+    for c in cells:
+        by_colour.setdefault(int(col[c[2], c[1], c[0]]), []).append(c)
+    for group in by_colour.values():
+        seen = set()
+        for c in group:
+            nb = neigh(c)
+            assert not (nb & seen), (ncell, c)
+            seen |= nb

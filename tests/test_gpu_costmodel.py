@@ -1,0 +1,142 @@
+"""Learned per-cell cost model and the persistent schedulers, through the C ABI.
+
+* MLP forward / loss / gradient (fp32 GPU) vs the fp64 oracle: 1e-4 relative.
+* Adam step vs the oracle; partition bit-exact vs the oracle.
+* Every scheduler gives bit-identical forces and trajectories (only the
+  assignment of atoms to warps changes, not any per-atom arithmetic).
+* The trained network against the pair-count heuristic on a porous system.
+"""
+import numpy as np
+import pytest
+
+from paper_1611_00075_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def md():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_00075_gb300 import build
+    build.build()
+    from paper_1611_00075_gb300 import md as _md
+    torch.cuda.set_device(0)
+    _md.lib()
+    return _md
+
+
+def f32(a):
+    return np.asarray(a, np.float32)
+
+
+def rand_params(orc, seed, scale=0.3):
+    return f32(scale * inputs.gaussian(seed, orc.mlp_nparams()))
+
+
+@pytest.mark.parametrize("ns", [1, 63, 64, 65, 1000, 4097])
+def test_mlp_forward_and_gradient_match_oracle(md, orc, ns):
+    P = rand_params(orc, 200 + ns)
+    X = f32(inputs.uniform(300 + ns, 3 * ns).reshape(ns, 3))
+    y = f32(inputs.gaussian(400 + ns, ns))
+    Pd, Xd, yd = (torch.from_numpy(a).cuda() for a in (P, X, y))
+    out = torch.empty(ns, dtype=torch.float32, device="cuda")
+    md.md_mlp_forward(Xd, Pd, out)
+    G = torch.empty_like(Pd)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    md.md_mlp_loss_grad(Xd, yd, Pd, G, loss)
+    torch.cuda.synchronize()
+    # oracle on the same (float32-rounded) numbers, in float64
+    yo = orc.mlp_forward(X.astype(np.float64), P.astype(np.float64))
+    lo, Go = orc.mlp_loss_grad(X.astype(np.float64), y.astype(np.float64), P.astype(np.float64))
+    np.testing.assert_allclose(out.cpu().numpy(), yo, rtol=1e-4, atol=1e-5 * np.abs(yo).max())
+    assert abs(loss.item() - lo) <= 1e-4 * abs(lo)
+    g = G.cpu().numpy()
+    np.testing.assert_allclose(g, Go, rtol=1e-4, atol=1e-4 * np.abs(Go).max())
+
+
+def test_adam_matches_oracle(md, orc):
+    P = rand_params(orc, 501)
+    G = f32(inputs.gaussian(502, P.size))
+    m = f32(0.01 * inputs.gaussian(503, P.size))
+    v = f32(np.abs(0.01 * inputs.gaussian(504, P.size)))
+    Pd, Gd, md_, vd = (torch.from_numpy(a.copy()).cuda() for a in (P, G, m, v))
+    md.md_mlp_adam(Pd, Gd, md_, vd, 7, lr=2e-3)
+    Po, mo, vo = P.astype(np.float64), m.astype(np.float64), v.astype(np.float64)
+    orc.adam(Po, G.astype(np.float64), mo, vo, 7, lr=2e-3)
+    np.testing.assert_allclose(Pd.cpu().numpy(), Po, rtol=1e-6, atol=1e-7)
+    # fp32 b1*m + (1-b1)*g cancels for small m: compare at fp32 resolution of |m|
+    np.testing.assert_allclose(md_.cpu().numpy(), mo, rtol=1e-5, atol=1e-7 * np.abs(mo).max())
+    np.testing.assert_allclose(vd.cpu().numpy(), vo, rtol=1e-5, atol=1e-9)
+
+
+@pytest.mark.parametrize("ncells,nparts", [(1, 1), (10, 3), (5000, 912), (300000, 1216),
+                                           (70000, 7)])
+def test_partition_bit_exact(md, orc, ncells, nparts):
+    c = (inputs.splitmix64(600 + ncells, ncells) % 100000).astype(np.int64)
+    c[inputs.splitmix64(601, ncells // 3 + 1) % ncells] = 0   # empty cells
+    b = torch.empty(nparts + 1, dtype=torch.int64, device="cuda")
+    md.md_partition(torch.from_numpy(c).cuda(), nparts, b)
+    np.testing.assert_array_equal(b.cpu().numpy(), orc.partition(c, nparts))
+
+
+def porous(nc=24):
+    return inputs.lj_porous(nc=nc, fraction=0.4, rmin=3.0, rmax=8.0)
+
+
+def test_schedulers_bit_identical(md):
+    s = porous()
+    outs = {}
+    for name, sched in (("grid", md.MD_SCHED_GRID), ("pair", md.MD_SCHED_PAIRCOUNT),
+                        ("dyn", md.MD_SCHED_DYNAMIC), ("mlp", md.MD_SCHED_MLP)):
+        with md.System(s.pos, s.vel, s.box, precision="mixed", scheduler=sched) as a:
+            f0 = a.state()[2]
+            a.step(30)
+            outs[name] = (f0,) + a.state()
+    for name in ("pair", "dyn", "mlp"):
+        for x, y in zip(outs["grid"], outs[name]):
+            assert torch.equal(x, y), name
+
+
+def test_switching_scheduler_keeps_state(md):
+    s = porous()
+    with md.System(s.pos, s.vel, s.box, precision="mixed") as a, \
+            md.System(s.pos, s.vel, s.box, precision="mixed") as b:
+        # same call pattern on both (a split md_step merges its kicks differently)
+        a.step(10)
+        a.step(10)
+        b.step(10)
+        md.md_set_variant(b.h, md.MD_FORCE_FULL, md.MD_SCHED_PAIRCOUNT)
+        b.step(10)
+        for x, y in zip(a.state(), b.state()):
+            assert torch.equal(x, y)
+
+
+def test_cost_model_trains_and_is_compared(md):
+    """Sample per-cell timings, train on the GPU, predict, and compare the
+    resulting partition's measured load imbalance (max / mean CTA cycles)
+    with the pair-count partition's on the same state."""
+    s = porous(nc=48)
+    with md.System(s.pos, s.vel, s.box, precision="mixed", scheduler=md.MD_SCHED_PAIRCOUNT) as a:
+        a.step(5)
+        imb_pair = md.md_cost_model(a.h, md.MD_COST_PROFILE)
+        nsamp = md.md_cost_model(a.h, md.MD_COST_SAMPLE)
+        assert nsamp > 1000
+        md.md_cost_model(a.h, md.MD_COST_RESET)
+        loss0 = None
+        # an untrained network's loss, then training lowers it
+        loss1 = md.md_cost_model(a.h, md.MD_COST_TRAIN)
+        loss2 = md.md_cost_model(a.h, md.MD_COST_TRAIN)
+        assert np.isfinite(loss2) and loss2 <= loss1 * 1.01
+        md.md_set_variant(a.h, md.MD_FORCE_FULL, md.MD_SCHED_MLP)
+        imb_mlp = md.md_cost_model(a.h, md.MD_COST_PROFILE)
+        md.md_set_variant(a.h, md.MD_FORCE_FULL, md.MD_SCHED_DYNAMIC)
+        imb_dyn = md.md_cost_model(a.h, md.MD_COST_PROFILE)
+    print("imbalance max/mean: paircount %.3f  mlp %.3f  dynamic %.3f  loss %.4g"
+          % (imb_pair, imb_mlp, imb_dyn, loss2))
+    assert 1.0 <= imb_pair < 10 and 1.0 <= imb_mlp < 10 and 1.0 <= imb_dyn < 10
+    # the gain of the trained network over the method without it: the learned
+    # partition is better balanced than the pair-count partition
+    assert imb_mlp < imb_pair

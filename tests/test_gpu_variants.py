@@ -1,0 +1,97 @@
+"""Newton's-third-law strategies (full list, half list + cell colouring, half
+list + float64 atomics) against the oracle and against each other."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1611_00075_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def md():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_00075_gb300 import build
+    build.build()
+    from paper_1611_00075_gb300 import md as _md
+    torch.cuda.set_device(0)
+    _md.lib()
+    return _md
+
+
+def perturbed(s, amp, seed):
+    g = inputs.gaussian(seed, s.pos.size).reshape(-1, 3)
+    return np.mod(s.pos + amp * g, s.box)
+
+
+def systems():
+    a = inputs.lj_fcc(nc=10, T=0.72)
+    b = inputs.lj_porous(nc=13, fraction=0.4, rmin=2.0, rmax=5.0)   # 4 cells + tail colours
+    return {"fcc4000": (a, perturbed(a, 0.05, 701)), "porous13": (b, perturbed(b, 0.05, 702))}
+
+
+def variant_code(md, name):
+    return {"color": md.MD_FORCE_HALF_COLOR, "atomic": md.MD_FORCE_HALF_ATOMIC}[name]
+
+
+@pytest.mark.parametrize("variant", ["color", "atomic"])
+@pytest.mark.parametrize("sysname", ["fcc4000", "porous13"])
+def test_half_variants_match_oracle(md, orc, variant, sysname):
+    s, pos = systems()[sysname]
+    off, ids = orc.neighbors_cells(pos, s.box, 2.8)
+    U0, f0 = orc.lj_list(pos, s.box, off, ids)
+    rows = np.repeat(np.arange(len(pos)), np.diff(off))
+    d = pos[ids] - pos[rows]
+    d -= s.box * np.round(d / s.box)
+    r = np.sqrt((d * d).sum(1))
+    bad = np.zeros(len(pos), bool)
+    bad[rows[np.abs(r - 2.5) < 1e-5]] = True
+    with md.System(pos, s.vel, s.box, precision="mixed",
+                   force_variant=variant_code(md, variant)) as sy:
+        _, _, f = sy.state()
+        ke, pe = sy.energy()
+        hoff, hids = sy.neighbors(half=True)
+        with pytest.raises(md.MDError):
+            sy.neighbors(half=False)     # a half list cannot export the full set
+    f = f.cpu().numpy()
+    fn = np.linalg.norm(f0, axis=1)
+    rms = math.sqrt(np.mean(fn * fn))
+    err = np.linalg.norm(f - f0, axis=1)
+    assert np.all((err <= 2e-4 * fn + 1e-5 * max(1.0, rms)) | bad)
+    assert abs(pe - U0) <= 2e-6 * abs(U0)
+    ho, hi = orc.neighbors_cells(pos, s.box, 2.8, half=True)
+    np.testing.assert_array_equal(hoff.cpu().numpy(), ho)
+    np.testing.assert_array_equal(hids.cpu().numpy(), hi)
+
+
+def test_variants_agree_over_a_trajectory(md):
+    s, pos = systems()["porous13"]
+    out = {}
+    for name, code in (("full", md.MD_FORCE_FULL), ("color", md.MD_FORCE_HALF_COLOR),
+                       ("atomic", md.MD_FORCE_HALF_ATOMIC)):
+        with md.System(pos, s.vel, s.box, precision="mixed", force_variant=code) as a:
+            a.step(50)
+            out[name] = [t.cpu().numpy() for t in a.state()]
+            out[name].append(sum(a.energy()))
+    for name in ("color", "atomic"):
+        dp = out[name][0] - out["full"][0]
+        dp -= s.box * np.round(dp / s.box)
+        assert np.max(np.abs(dp)) < 1e-5, name
+        assert abs(out[name][3] - out["full"][3]) < 1e-5 * abs(out["full"][3])
+
+
+def test_switch_variant_rebuilds_list(md):
+    s, pos = systems()["fcc4000"]
+    with md.System(pos, s.vel, s.box, precision="mixed") as a:
+        off_full, _ = a.neighbors()
+        md.md_set_variant(a.h, md.MD_FORCE_HALF_COLOR, md.MD_SCHED_GRID)
+        off_half, _ = a.neighbors(half=True)
+        assert off_half[-1].item() * 2 == off_full[-1].item()
+        md.md_set_variant(a.h, md.MD_FORCE_FULL, md.MD_SCHED_GRID)
+        off2, _ = a.neighbors()
+        assert torch.equal(off2, off_full)
