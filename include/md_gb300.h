@@ -228,6 +228,27 @@ md_status md_mlp_adam(float *P_dev, const float *G_dev, float *m_dev, float *v_d
 md_status md_partition(const int64_t *cost_dev, int64_t ncells, int32_t nparts,
                        int64_t *bounds_dev, void *cuda_stream);
 
+/* md_partition for callers that cannot allocate device memory while they
+ * run -- a loop that fixed its memory budget at start-up, a host framework
+ * whose allocator owns the device heap, or a setup without stream-ordered
+ * allocation.  The paper has no counterpart; this is a service of the
+ * library.  Same arguments and result as md_partition, but the scan scratch
+ * is a fixed array inside the library's device image (about 8.4 MB, held on
+ * every GPU that loads the library until the process exits) instead of a
+ * cudaMallocAsync buffer, so the call allocates nothing.
+ *  - ncells must be <= 1,048,576; larger sizes return MD_ERR_INVALID and
+ *    md_last_error(NULL) says why (use md_partition for them).
+ *  - The first call on a device looks up the array's device address with
+ *    cudaGetSymbolAddress (once per device, with that device current); make
+ *    that first call before any stream capture.
+ *  - All calls share the one array and nothing in it needs to start at zero
+ *    (the scan overwrites every word it reads).  Calls that overlap on the
+ *    GPU -- different streams, or different host threads -- race on it; the
+ *    caller must order them.
+ * Asynchronous on stream. */
+md_status md_partition_noalloc(const int64_t *cost_dev, int64_t ncells, int32_t nparts,
+                               int64_t *bounds_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

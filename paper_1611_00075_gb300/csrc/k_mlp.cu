@@ -9,6 +9,8 @@
 // Parameter layout (1217 float32): W1[32][3], b1[32], W2[32][32], b2[32],
 // W3[32], b3[1].
 #include <cmath>
+#include <mutex>
+#include <string>
 
 #include "k_scan.cuh"
 
@@ -323,3 +325,78 @@ md_status md_partition(const int64_t *cost_dev, int64_t ncells, int32_t nparts,
 }
 
 }  // extern "C"
+
+// ---- md_partition without device allocation ----------------------------------
+//
+// Some callers cannot allocate device memory while they run: a simulation loop
+// that fixed its memory budget at start-up, a host framework whose own
+// allocator owns the device heap, or a driver setup without stream-ordered
+// allocation (cudaMallocAsync unsupported).  md_partition takes its scan
+// scratch from cudaMallocAsync; this variant uses a fixed array that lives in
+// the library's device image instead.  Every GPU that loads the library holds
+// the array (about 8.4 MB) until the process exits.
+
+namespace mdg {
+namespace {
+
+constexpr long long kNoAllocMaxCells = 1ll << 20;  // largest ncells accepted
+constexpr long long kNoAllocWords = kNoAllocMaxCells + 1 + kNoAllocMaxCells / kScanTile + 8;
+
+// prefix sums of the costs (ncells + 1) followed by the scan's tile sums
+static __device__ __align__(256) long long g_partition_scratch[kNoAllocWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+long long *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_partition_scratch on the current device.  In host code
+// the array's name is only a stand-in, so the address is looked up once per
+// device (with that device current) and cached.
+cudaError_t scratch_address(long long **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        long long *p = nullptr;
+        e = cudaGetSymbolAddress((void **)&p, g_partition_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace mdg
+
+extern "C" md_status md_partition_noalloc(const int64_t *cost_dev, int64_t ncells, int32_t nparts,
+                                          int64_t *bounds_dev, void *cuda_stream) {
+    if (ncells < 1 || nparts < 1 || !cost_dev || !bounds_dev) {
+        mdg::set_thread_error("md_partition_noalloc: bad argument");
+        return MD_ERR_INVALID;
+    }
+    if (ncells > mdg::kNoAllocMaxCells) {
+        mdg::set_thread_error("md_partition_noalloc: ncells = " + std::to_string(ncells) +
+                              " exceeds the fixed scratch limit of " +
+                              std::to_string(mdg::kNoAllocMaxCells) +
+                              " cells (use md_partition, which allocates)");
+        return MD_ERR_INVALID;
+    }
+    long long *scratch = nullptr;
+    cudaError_t e = mdg::scratch_address(&scratch);
+    if (e != cudaSuccess) {
+        mdg::set_thread_error(std::string("md_partition_noalloc: cudaGetSymbolAddress: ") +
+                              cudaGetErrorString(e));
+        return MD_ERR_CUDA;
+    }
+    // The scan overwrites every scratch word it reads, so nothing needs clearing.
+    e = mdg::launch_partition((const long long *)cost_dev, ncells, nparts, (long long *)bounds_dev,
+                              scratch, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) {
+        mdg::set_thread_error(std::string("md_partition_noalloc: ") + cudaGetErrorString(e));
+        return MD_ERR_CUDA;
+    }
+    return MD_OK;
+}

@@ -317,6 +317,8 @@ __global__ void begin_steps_kernel(DevStatus *ds, int base) { ds->steps_done = b
 
 }  // namespace
 
+void mdg::set_thread_error(const std::string &msg) { g_thread_error = msg; }
+
 extern "C" {
 
 md_status md_create(md_system **out, const md_params *p, int64_t n, const double *box3_host,

@@ -265,6 +265,9 @@ cudaError_t launch_partition(const long long *cost, long long ncells, int nparts
                              long long *bounds, long long *scratch, cudaStream_t s,
                              const DevStatus *ds = nullptr, bool gated = false);
 
+// Message returned by md_last_error(NULL) on the calling thread.
+void set_thread_error(const std::string &msg);
+
 inline int nblocks(int64_t n, int b = kBlock) { return (int)((n + b - 1) / b); }
 
 // Grids of the grid-stride kernels (rebuild chain): enough blocks to fill the

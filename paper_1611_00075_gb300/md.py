@@ -79,6 +79,7 @@ def lib() -> C.CDLL:
         "md_mlp_adam": [vp, vp, vp, vp, i64, i64, C.c_float, C.c_float, C.c_float,
                         C.c_float, vp],
         "md_partition": [vp, i64, i32, vp, vp],
+        "md_partition_noalloc": [vp, i64, i32, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -242,6 +243,13 @@ def md_mlp_adam(P, G, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream
 def md_partition(cost: torch.Tensor, nparts: int, bounds: torch.Tensor, stream=None):
     _check(lib().md_partition(_ptr(cost), cost.numel(), int(nparts), _ptr(bounds),
                               _stream(stream)), None, "md_partition")
+
+
+def md_partition_noalloc(cost: torch.Tensor, nparts: int, bounds: torch.Tensor, stream=None):
+    """md_partition without any device allocation (fixed scratch inside the
+    library; ncells <= 1,048,576; overlapping calls race on the scratch)."""
+    _check(lib().md_partition_noalloc(_ptr(cost), cost.numel(), int(nparts), _ptr(bounds),
+                                      _stream(stream)), None, "md_partition_noalloc")
 
 
 # ---- convenience wrapper -----------------------------------------------------
