@@ -191,6 +191,18 @@ md_status md_cost_model(md_system *h, int32_t op, float *loss_out);
  * Synchronizes. */
 md_status md_set_timing(md_system *h, int32_t on);
 
+/* Per-cell view of the cost model (after MD_COST_SAMPLE), each array of
+ * ncells in linear cell order, any pointer may be NULL (device arrays):
+ *   cycles_dev     float32 measured force-pass cycles of the cell, summed
+ *                  over the sampling passes
+ *   predicted_dev  int64 cost the trained network predicts (what the
+ *                  MD_SCHED_MLP partition uses)
+ *   paircount_dev  int64 list entries of the cell's atoms (what the
+ *                  MD_SCHED_PAIRCOUNT partition uses)
+ * Synchronizes. */
+md_status md_get_cell_costs(md_system *h, float *cycles_dev, int64_t *predicted_dev,
+                            int64_t *paircount_dev);
+
 /* Writes a one-line JSON summary (atoms, cells, list capacity, rebuild
  * count, steps, last kernel times) into buf_host (NUL-terminated, at most
  * cap bytes).  Synchronizes. */

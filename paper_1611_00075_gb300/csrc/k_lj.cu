@@ -51,33 +51,36 @@ __device__ __forceinline__ void lj_mixed_atom(const ForceArgs &a, const float4 *
     const float rc2 = a.fc.rc2f, sig2 = a.fc.sig2f, e48 = a.fc.eps48f;
     double Fx = 0.0, Fy = 0.0, Fz = 0.0, E = 0.0;
     unsigned npair = 0;
+    float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+    auto pair = [&](uint32_t ent) {
+        const float4 qj = __ldg(a.xq + (ent & kIndexMask));
+        const float4 sf = sh[ent >> kIndexBits];
+        const float ex = (qj.x - qi.x) + sf.x;
+        const float ey = (qj.y - qi.y) + sf.y;
+        const float ez = (qj.z - qi.z) + sf.z;
+        const float r2 = ex * ex + ey * ey + ez * ez;
+        if (r2 < rc2) {
+            const float r2i = __fdividef(1.0f, r2);
+            float s6 = sig2 * r2i;
+            s6 = s6 * s6 * s6;
+            const float fs = e48 * r2i * s6 * (s6 - 0.5f);
+            fx -= fs * ex;
+            fy -= fs * ey;
+            fz -= fs * ez;
+            if (ENERGY) {
+                e += a.fc.eps4f * s6 * (s6 - 1.0f) - a.fc.shiftf;
+                ++npair;
+            }
+        }
+    };
+    // list quads stream through once (evict-first), one quad loaded ahead;
+    // the float64 sums run once per chunk, outside the inner loop
+    uint4 nxt = nq > 0 ? __ldcs(lq) : make_uint4(0u, 0u, 0u, 0u);
     for (int q0 = 0; q0 < nq; q0 += kChunkQ) {
         const int q1 = min(q0 + kChunkQ, nq);
-        float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
-        auto pair = [&](uint32_t ent) {
-            const float4 qj = __ldg(a.xq + (ent & kIndexMask));
-            const float4 sf = sh[ent >> kIndexBits];
-            const float ex = (qj.x - qi.x) + sf.x;
-            const float ey = (qj.y - qi.y) + sf.y;
-            const float ez = (qj.z - qi.z) + sf.z;
-            const float r2 = ex * ex + ey * ey + ez * ez;
-            if (r2 < rc2) {
-                const float r2i = __fdividef(1.0f, r2);
-                float s6 = sig2 * r2i;
-                s6 = s6 * s6 * s6;
-                const float fs = e48 * r2i * s6 * (s6 - 0.5f);
-                fx -= fs * ex;
-                fy -= fs * ey;
-                fz -= fs * ez;
-                if (ENERGY) {
-                    e += a.fc.eps4f * s6 * (s6 - 1.0f) - a.fc.shiftf;
-                    ++npair;
-                }
-            }
-        };
-#pragma unroll 2
         for (int q = q0; q < q1; ++q) {
-            const uint4 e4 = __ldg(lq + (size_t)q * 32);
+            const uint4 e4 = nxt;
+            if (q + 1 < nq) nxt = __ldcs(lq + (size_t)(q + 1) * 32);
             pair(e4.x);
             pair(e4.y);
             pair(e4.z);
@@ -86,7 +89,11 @@ __device__ __forceinline__ void lj_mixed_atom(const ForceArgs &a, const float4 *
         Fx += (double)fx;
         Fy += (double)fy;
         Fz += (double)fz;
-        if (ENERGY) E += (double)e;
+        fx = fy = fz = 0.f;
+        if (ENERGY) {
+            E += (double)e;
+            e = 0.f;
+        }
     }
     const size_t n = (size_t)a.n;
     if (MODE == FM_STORE || store_f) {
@@ -103,7 +110,7 @@ __device__ __forceinline__ void lj_mixed_atom(const ForceArgs &a, const float4 *
 
 // One thread per sorted atom; the hardware block scheduler spreads the work.
 template <int MODE, bool ENERGY>
-__global__ void __launch_bounds__(kBlock) lj_mixed_kernel(ForceArgs a, int store_f) {
+__global__ void __launch_bounds__(kBlock, 5) lj_mixed_kernel(ForceArgs a, int store_f) {
     __shared__ float4 sh[kStencil];
     load_shifts_f32(a, sh);
     __syncthreads();
@@ -116,9 +123,12 @@ __global__ void __launch_bounds__(kBlock) lj_mixed_kernel(ForceArgs a, int store
 // Persistent variant: gridDim.x CTAs stay resident; each warp processes tiles
 // of 32 consecutive sorted atoms (tile t = atoms 32t .. 32t+31, aligned with
 // the list layout).
-//   STATIC:  CTA b owns atoms [cell_start[bounds[b]], cell_start[bounds[b+1]])
-//            -- a contiguous range of whole cells from an equal-cost
-//            partition -- and its warps take that range's tiles round-robin.
+//   STATIC:  the cells are cut into rounds * G contiguous ranges of equal
+//            (predicted) cost; CTA b owns ranges b, b + G, b + 2G, ... and its
+//            warps take each range's tiles round-robin.  Each CTA gets the
+//            same predicted total, while at any moment all CTAs work in the
+//            same window of the sorted atoms, which keeps neighbour gathers
+//            in L2.
 //   DYNAMIC: warps claim tiles from a global counter until none are left; the
 //            last CTA to finish resets the counter for the next launch.
 // TIMING adds clock64 per tile: the tile's cycles are shared equally by its
@@ -141,9 +151,14 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
     int A = 0, B = a.n;
     int t = 0, tend = ntiles, tstep = nwarp;
     int claim_end = 0;
+    int round = 0;
     if (!DYNAMIC) {
-        A = sa.cell_start[sa.bounds[blockIdx.x]];
-        B = sa.cell_start[sa.bounds[blockIdx.x + 1]];
+        // cyclic static partition: this CTA owns ranges b, b + G, b + 2G, ...
+        // so that at any time all CTAs work in one window of the sorted atoms
+        // (neighbour gathers then hit in L2)
+        const long long q = blockIdx.x;
+        A = sa.cell_start[sa.bounds[q]];
+        B = sa.cell_start[sa.bounds[q + 1]];
         t = (A >> 5) + warp;
         tend = (B + 31) >> 5;
     }
@@ -154,6 +169,14 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
                 if (lane == 0) claimed = atomicAdd(&a.ds->tile_counter, kClaim);
                 t = __shfl_sync(0xffffffffu, claimed, 0);
                 claim_end = t + kClaim;
+            }
+        } else {
+            while (t >= tend && ++round < sa.rounds) {
+                const long long q = (long long)round * gridDim.x + blockIdx.x;
+                A = sa.cell_start[sa.bounds[q]];
+                B = sa.cell_start[sa.bounds[q + 1]];
+                t = (A >> 5) + warp;
+                tend = (B + 31) >> 5;
             }
         }
         if (t >= tend) break;
@@ -175,7 +198,7 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
     }
     if (TIMING || DYNAMIC) __syncthreads();
     if (threadIdx.x == 0) {
-        if (TIMING) sa.cta_cycles[blockIdx.x] = (float)(clock64() - cta_t0);
+        if (TIMING) sa.cta_cycles[blockIdx.x] += (float)(clock64() - cta_t0);
         if (DYNAMIC) {
             __threadfence();
             const unsigned prev = atomicAdd(&a.ds->done_ctas, 1u);
@@ -313,6 +336,7 @@ cudaError_t launch_lj_persist(md_system *h, int mode, bool store_f, bool dynamic
     sa.cell = h->cell;
     sa.cell_cycles = h->cell_cycles;
     sa.cta_cycles = h->cta_cycles;
+    sa.rounds = kSchedRounds;
     const int G = h->sched_ctas;
     const int sf = store_f ? 1 : 0;
     cudaStream_t s = h->stream;

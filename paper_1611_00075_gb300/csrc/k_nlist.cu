@@ -49,8 +49,8 @@ build_list_kernel(int n, Grid g, float lo, float hi, double rl2, const float4 *_
         const float4 qi = xq[i];
         const double4 ai = xabs[i];
         const int myo = __float_as_int(qi.w);
-        uint4 *quads = reinterpret_cast<uint4 *>(nlist + list_group(i, cap)) + (i & 31);
-        uint4 pend = make_uint4(0u, 0u, 0u, 0u);
+        // entry k of atom i: row[(k / 4) * 128 + k % 4]
+        uint32_t *row = nlist + list_group(i, cap) + ((i & 31) << 2);
         for (int dz = -1; dz <= 1; ++dz) {
             int zz = cz + dz;
             double shz = 0.0;
@@ -69,31 +69,26 @@ build_list_kernel(int n, Grid g, float lo, float hi, double rl2, const float4 *_
                     const int cn = (zz * g.ny + yy) * g.nx + xx;
                     const int s = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
                     const float4 sf = sh[s];
+                    // home position moved against the cell shift: e = q_j - (q_i - shift)
+                    const float hx = qi.x - sf.x, hy = qi.y - sf.y, hz = qi.z - sf.z;
                     const int b = start[cn], e = start[cn + 1];
-                    for (int j0 = b; j0 < e; j0 += 4) {
-                        // four candidate loads in flight before the tests
-                        float4 qj[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            qj[u] = (j0 + u < e) ? xq[j0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int j = j0 + u;
-                            if (j >= e || j == i) continue;
-                            if (HALF && __float_as_int(qj[u].w) <= myo) continue;
-                            bool acc;
+                    const int skip = (s == 13) ? i : -1;  // the atom itself, home cell only
+#pragma unroll 4
+                    for (int j = b; j < e; ++j) {
+                        {
+                            const float4 qj = xq[j];
                             float r2f = 0.f;
+                            bool cand = true;
                             if (PREFILTER) {
-                                const float ex = (qj[u].x - qi.x) + sf.x;
-                                const float ey = (qj[u].y - qi.y) + sf.y;
-                                const float ez = (qj[u].z - qi.z) + sf.z;
+                                const float ex = qj.x - hx, ey = qj.y - hy, ez = qj.z - hz;
                                 r2f = ex * ex + ey * ey + ez * ez;
+                                cand = r2f < hi;
                             }
-                            if (PREFILTER && r2f < lo) {
-                                acc = true;
-                            } else if (PREFILTER && r2f >= hi) {
-                                acc = false;
-                            } else {
+                            cand = cand && (j != skip);
+                            if (HALF) cand = cand && (__float_as_int(qj.w) > myo);
+                            if (!cand) continue;
+                            bool acc = true;
+                            if (!PREFILTER || r2f >= lo) {
                                 // the float64 definition, operation for operation
                                 const double4 aj = xabs[j];
                                 double ddx = __dadd_rn(__dadd_rn(aj.x, -ai.x), shx);
@@ -104,32 +99,20 @@ build_list_kernel(int n, Grid g, float lo, float hi, double rl2, const float4 *_
                                 r2 = __dadd_rn(r2, __dmul_rn(ddz, ddz));
                                 acc = r2 < rl2;
                             }
-                            if (acc) {
-                                if (WRITE && cnt < cap) {
-                                    const uint32_t ent = ((uint32_t)s << kIndexBits) | (uint32_t)j;
-                                    switch (cnt & 3) {
-                                        case 0: pend.x = ent; break;
-                                        case 1: pend.y = ent; break;
-                                        case 2: pend.z = ent; break;
-                                        default:
-                                            pend.w = ent;
-                                            quads[(size_t)(cnt >> 2) * 32] = pend;
-                                    }
-                                }
-                                ++cnt;
-                            }
+                            if (!acc) continue;
+                            if (WRITE && cnt < cap)
+                                row[(size_t)(cnt >> 2) * 128 + (cnt & 3)] =
+                                    ((uint32_t)s << kIndexBits) | (uint32_t)j;
+                            ++cnt;
                         }
                     }
                 }
             }
         }
-        if (WRITE && cnt <= cap && (cnt & 3)) {
+        if (WRITE && cnt <= cap) {
             // pad the last quad with self-entries that no cutoff accepts
             const uint32_t pad = (kPadStencil << kIndexBits) | (uint32_t)i;
-            if ((cnt & 3) <= 1) pend.y = pad;
-            if ((cnt & 3) <= 2) pend.z = pad;
-            pend.w = pad;
-            quads[(size_t)(cnt >> 2) * 32] = pend;
+            for (int k = cnt; k & 3; ++k) row[(size_t)(k >> 2) * 128 + (k & 3)] = pad;
         }
         ncount[i] = cnt;
         atomicMax(&ds->max_count, cnt);

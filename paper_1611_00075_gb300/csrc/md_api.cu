@@ -176,7 +176,7 @@ md_status ensure_sched(md_system *h) {
     const size_t C = (size_t)h->g.ncells;
     cudaError_t e = cudaSuccess;
     auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-    A(dalloc(&h->part_bounds, (size_t)h->sched_ctas + 1));
+    A(dalloc(&h->part_bounds, (size_t)h->sched_ctas * kSchedRounds + 1));
     A(dalloc(&h->cell_cost, C));
     A(dalloc(&h->part_scratch, C + 1 + C / (kBlock * 8) + 8));
     A(dalloc(&h->cell_X, 3 * C));
@@ -640,6 +640,30 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
     return enqueue_sched_prep(h, false);
 }
 
+md_status md_get_cell_costs(md_system *h, float *cycles_dev, int64_t *predicted_dev,
+                            int64_t *paircount_dev) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_get_cell_costs: null handle");
+    if (!h->part_bounds || h->samp_n <= 0)
+        return fail(h, MD_ERR_INVALID, "md_get_cell_costs: run md_cost_model(MD_COST_SAMPLE) first");
+    const size_t C = (size_t)h->g.ncells;
+    if (cycles_dev)
+        MD_CK(cudaMemcpyAsync(cycles_dev, h->cell_cycles, C * sizeof(float),
+                              cudaMemcpyDeviceToDevice, h->stream));
+    if (paircount_dev) {
+        MD_CK(launch_cell_features(h, true, false));
+        MD_CK(cudaMemcpyAsync(paircount_dev, h->cell_cost, C * sizeof(int64_t),
+                              cudaMemcpyDeviceToDevice, h->stream));
+    }
+    if (predicted_dev) {
+        MD_CK(launch_cell_features(h, false, false));
+        MD_CK(launch_predict_costs(h, false));
+        MD_CK(cudaMemcpyAsync(predicted_dev, h->cell_cost, C * sizeof(int64_t),
+                              cudaMemcpyDeviceToDevice, h->stream));
+    }
+    MD_CK(cudaStreamSynchronize(h->stream));
+    return MD_OK;
+}
+
 // Per-CTA cycles of one timed force pass, reduced on the host to max / mean.
 md_status cta_imbalance(md_system *h, float *out) {
     std::vector<float> c((size_t)h->sched_ctas);
@@ -679,6 +703,8 @@ md_status md_cost_model(md_system *h, int32_t op, float *loss_out) {
             st = enqueue_rebuild(h, true);
             if (st != MD_OK) return st;
             MD_CK(cudaMemsetAsync(h->cell_cycles, 0, (size_t)h->g.ncells * sizeof(float),
+                                  h->stream));
+            MD_CK(cudaMemsetAsync(h->cta_cycles, 0, (size_t)h->sched_ctas * sizeof(float),
                                   h->stream));
             for (int r = 0; r < kPasses; ++r) MD_CK(launch_lj_persist(h, FM_STORE, true, true, true));
             MD_CK(launch_cell_features(h, false, false));
@@ -725,9 +751,13 @@ md_status md_cost_model(md_system *h, int32_t op, float *loss_out) {
             if (st != MD_OK) return st;
             MD_CK(cudaMemsetAsync(h->cell_cycles, 0, (size_t)h->g.ncells * sizeof(float),
                                   h->stream));
-            MD_CK(launch_lj_persist(h, FM_STORE, true, h->p.scheduler != MD_SCHED_PAIRCOUNT &&
-                                                            h->p.scheduler != MD_SCHED_MLP,
-                                    true));
+            MD_CK(cudaMemsetAsync(h->cta_cycles, 0, (size_t)h->sched_ctas * sizeof(float),
+                                  h->stream));
+            for (int r = 0; r < kPasses; ++r)
+                MD_CK(launch_lj_persist(h, FM_STORE, true,
+                                        h->p.scheduler != MD_SCHED_PAIRCOUNT &&
+                                            h->p.scheduler != MD_SCHED_MLP,
+                                        true));
             st = read_status(h);
             if (st != MD_OK) return st;
             h->forces_valid = true;

@@ -79,17 +79,20 @@ struct DevStatus {
 // What the persistent force kernel needs besides ForceArgs.
 struct SchedArgs {
     const int32_t *cell_start;  // ncells + 1
-    const long long *bounds;    // partition of cells over CTAs (gridDim.x + 1)
+    const long long *bounds;    // partition of cells into rounds * gridDim.x ranges (+1)
+    int rounds;                 // ranges per CTA (cyclic assignment)
     const int32_t *cell;        // sorted slot -> cell
     float *cell_cycles;         // TIMING: per-cell cycles (accumulated)
     float *cta_cycles;          // TIMING: per-CTA busy cycles
 };
 
-// Geometry passed by value to kernels.
+// Geometry of one periodic box and its cells.  A system may hold several
+// independent boxes (replicas); their cells are numbered consecutively and
+// cell0 is the first global cell id of this box.
 struct Grid {
     int nx, ny, nz, pad0;
     int ncells;
-    int pad1;
+    int cell0;
     double L[3];
     double w[3];        // cell widths L / n
     double inv_w[3];    // n / L
@@ -121,7 +124,19 @@ struct md_system {
     md_params p;
     int64_t n = 0;
     cudaStream_t stream = nullptr;
-    mdg::Grid g{};
+    mdg::Grid g{};  // the box (the first box of a batch); g.ncells counts all cells
+
+    // replicas (md_create_batch): R boxes, atoms of replica r are original ids
+    // [atom_off[r], atom_off[r+1]) and cells [grids[r].cell0, + grids[r].ncells)
+    int R = 1;
+    std::vector<mdg::Grid> grids_h;
+    std::vector<int64_t> atom_off_h;
+    mdg::Grid *grids = nullptr;       // device copy of grids_h
+    int64_t *atom_off = nullptr;      // device copy of atom_off_h
+    uint16_t *rep = nullptr;          // sorted slot -> replica (batches only)
+    uint16_t *tmp_rep = nullptr;
+    float4 *shifts32 = nullptr;       // R x 27 float32 cell shifts (batches only)
+    double *rep_ke = nullptr, *rep_pe = nullptr;  // per-replica sums (device)
     mdg::ForceConsts fc{};
     double r_list = 0.0;
     float list_lo = 0.f, list_hi = 0.f;  // fp32 prefilter band around r_list^2
@@ -245,6 +260,8 @@ cudaError_t launch_set_rebuild(md_system *h);
 
 // ---- scheduler and cost model (k_sched.cu, k_mlp.cu) ----------------------
 constexpr int kMlpParams = 1217;
+// The static schedulers cut the cells into kSchedRounds ranges per CTA.
+constexpr int kSchedRounds = 8;
 // features of every cell; with paircount != 0 also cell_cost = list entries
 cudaError_t launch_cell_features(md_system *h, bool paircount, bool gated);
 // model inference on cell_X, quantised into cell_cost

@@ -74,6 +74,7 @@ def lib() -> C.CDLL:
         "md_get_atom_energy": [vp, vp], "md_set_variant": [vp, i32, i32],
         "md_cost_model": [vp, i32, vp], "md_stats": [vp, C.c_char_p, C.c_size_t],
         "md_set_timing": [vp, i32], "md_color_cells": [vp, vp, vp],
+        "md_get_cell_costs": [vp, vp, vp, vp],
         "md_mlp_forward": [vp, i64, vp, vp, vp],
         "md_mlp_loss_grad": [vp, vp, i64, vp, vp, vp, vp],
         "md_mlp_adam": [vp, vp, vp, vp, i64, i64, C.c_float, C.c_float, C.c_float,
@@ -196,6 +197,11 @@ def md_cost_model(h, op: int) -> float:
     loss = C.c_float(float("nan"))
     _check(lib().md_cost_model(h, int(op), C.byref(loss)), h, "md_cost_model")
     return loss.value
+
+
+def md_get_cell_costs(h, cycles=None, predicted=None, paircount=None):
+    _check(lib().md_get_cell_costs(h, _ptr(cycles), _ptr(predicted), _ptr(paircount)), h,
+           "md_get_cell_costs")
 
 
 def md_set_timing(h, on: bool):
