@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="porous", choices=["porous", "fcc", "sc"])
+    ap.add_argument("--workload", default="porous", choices=["porous", "fcc", "sc", "ensemble"])
     ap.add_argument("--compare-steps", type=int, default=100,
                     help="steps timed for each other scheduler (0 = skip the comparison)")
     ap.add_argument("--scheduler", default="mlp",
@@ -62,6 +62,14 @@ def dist_env():
 
 
 def make_workload(name: str, nc: int = 0):
+    if name == "ensemble":
+        reps = inputs.lj_ensemble(count=nc or 64)
+        n = sum(r.n for r in reps)
+        desc = ("batched ensemble: %d Lennard-Jones fcc replicas, sizes log-uniform 1,000-200,000 "
+                "(%d atoms in all), rho* U(0.7,0.9), T* U(0.5,1.5), rc=2.5, skin=0.3, dt=0.005, "
+                "one launch per phase over all replicas, steps replayed from CUDA graphs"
+                % (len(reps), n))
+        return reps, desc
     if name == "porous" and nc:
         s = inputs.lj_porous(nc=nc)
         return s, "porous Lennard-Jones solid, %d^3 fcc cells (profiling size), %d atoms" % (nc, s.n)
@@ -166,6 +174,15 @@ def run_gpu(args, rank, world, local):
     md.lib()
     stream = torch.cuda.Stream(device=dev)
     s, desc = make_workload(args.workload, args.nc)
+    ensemble = args.workload == "ensemble"
+    if ensemble:
+        reps = s
+        s = inputs.System(name="ensemble", pos=np.concatenate([r.pos for r in reps]),
+                          vel=np.concatenate([r.vel for r in reps]), box=reps[0].box,
+                          params=reps[0].params)
+        if args.scheduler not in ("grid", "dynamic"):
+            args.scheduler = "dynamic"
+        args.fp64_steps = 0  # batches run the mixed path; per-replica fp64 is not the comparison
     kw = md_kwargs(s)
     sched = {"grid": md.MD_SCHED_GRID, "paircount": md.MD_SCHED_PAIRCOUNT,
              "mlp": md.MD_SCHED_MLP, "dynamic": md.MD_SCHED_DYNAMIC}[args.scheduler]
@@ -186,8 +203,9 @@ def run_gpu(args, rank, world, local):
     def n_of(sysobj):
         return sysobj.n * world
 
-    def timed(sysobj, nsteps):
-        md.md_set_timing(sysobj.h, True)
+    def timed(sysobj, nsteps, events=True):
+        # md_set_timing also zeroes the handle's launch counter
+        md.md_set_timing(sysobj.h, events)
         torch.cuda.synchronize()
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -204,11 +222,31 @@ def run_gpu(args, rank, world, local):
 
     sampler = ClockSampler(local)
     with torch.cuda.stream(stream):
-        mixed = md.System(s.pos, s.vel, s.box, precision="mixed", stream=stream, **kw)
+        if ensemble:
+            mixed = md.Batch([(r.pos, r.vel, r.box) for r in reps], precision="mixed",
+                             stream=stream, **kw)
+        else:
+            mixed = md.System(s.pos, s.vel, s.box, precision="mixed", stream=stream, **kw)
         md.md_step(mixed.h, args.warmup)
         sched_info = {}
+        if ensemble:
+            md.md_set_variant(mixed.h, md.MD_FORCE_FULL, sched)
+            if args.compare_steps > 0:
+                sched_info["per_replica_launches"] = per_replica(md, reps, kw, stream,
+                                                                 args.compare_steps, args.warmup)
+                # the batch over the same number of steps, plain device time (graphs on)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                md.md_step(mixed.h, args.compare_steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                sched_info["batched_graphs"] = {
+                    "atom_steps_per_s": mixed.n * args.compare_steps / (e0.elapsed_time(e1) * 1e-3),
+                    "steps": args.compare_steps}
         # the other schedulers on the same state, for comparison (short runs)
-        if args.compare_steps > 0 and kw["potential"] == "lj":
+        elif args.compare_steps > 0 and kw["potential"] == "lj":
             for name, code in (("grid", md.MD_SCHED_GRID), ("paircount", md.MD_SCHED_PAIRCOUNT),
                                ("dynamic", md.MD_SCHED_DYNAMIC)):
                 md.md_set_variant(mixed.h, md.MD_FORCE_FULL, code)
@@ -217,7 +255,9 @@ def run_gpu(args, rank, world, local):
                                     "force_ms_per_launch": stx["ms"]["force"] / max(1, stx["count"]["force"])}
                 if code != md.MD_SCHED_GRID:
                     sched_info[name]["cta_imbalance"] = md.md_cost_model(mixed.h, md.MD_COST_PROFILE)
-        if args.scheduler == "mlp" and kw["potential"] == "lj":
+        if ensemble:
+            pass
+        elif args.scheduler == "mlp" and kw["potential"] == "lj":
             # the learned part: per-cell clock64 timings of this run -> GPU training
             md.md_set_variant(mixed.h, md.MD_FORCE_FULL, md.MD_SCHED_DYNAMIC)
             t0 = time.perf_counter()
@@ -232,9 +272,18 @@ def run_gpu(args, rank, world, local):
             md.md_set_variant(mixed.h, md.MD_FORCE_FULL, sched)
         builds0 = json.loads(md.md_stats(mixed.h))["builds"]
         sampler.start()
-        ms, st = timed(mixed, args.steps)
+        # batches of small replicas are launch-bound: their timed region replays
+        # graphs, which per-launch events would disable
+        ms, st = timed(mixed, args.steps, events=not ensemble)
         builds_timed = st["builds"] - builds0
         clock_rows = sampler.stop()
+        launches_timed = st["launches"]
+        if ensemble:
+            # kernel durations from a separate run with per-launch events
+            kb_steps = min(args.steps, 200)
+            _, st = timed(mixed, kb_steps)
+            sched_info["kernel_breakdown_steps"] = kb_steps
+            st["launches"] = launches_timed
         ms = max_over_ranks(ms)
         ke, pe = md.md_energy(mixed.h)
         st_e = json.loads(md.md_stats(mixed.h))
@@ -314,16 +363,46 @@ def run_gpu(args, rank, world, local):
             "traffic": None,
             "kernel": ("lj_mixed_persist<FM_FUSED_FULL> (%s)" % args.scheduler if args.scheduler != "grid"
                        else "lj_mixed_kernel<FM_FUSED_FULL>") if kw["potential"] == "lj" else "sc_force_mixed",
+            "multi_box": ensemble,
             "peak_source": peak_src,
             "algorithmic_bytes_per_launch": bytes_, "algorithmic_flops_per_launch": flops,
             "launch_ms": t_force * 1e3,
             "fp32": {"achieved_tflops": ach_flops, "peak_tflops": fp32_peak,
                      "frac": ach_flops / fp32_peak,
                      "peak_note": "SMs x 128 fp32 lanes x 2 x max SM clock"}}
+    pos, force, box, n_chk = pos.cpu().numpy(), force.cpu().numpy(), s.box, n
+    if ensemble:
+        # the force check runs on the largest replica (its own box)
+        k = int(np.argmax([r.n for r in reps]))
+        a0 = sum(r.n for r in reps[:k])
+        pos, force, box, n_chk = pos[a0:a0 + reps[k].n], force[a0:a0 + reps[k].n], reps[k].box, reps[k].n
     return dict(n=n, value=value, ms=ms, st=st, st_e=st_e, fp64=fp64, e2e=e2e, roof=roof,
-                clk=clk, desc=desc, pos=pos.cpu().numpy(), force=force.cpu().numpy(),
-                box=s.box, params=s.params, ke=ke, pe=pe, builds_timed=builds_timed,
+                clk=clk, desc=desc, pos=pos, force=force, n_check=n_chk,
+                box=box, params=s.params, ke=ke, pe=pe, builds_timed=builds_timed,
                 sched_info=sched_info)
+
+
+def per_replica(md, reps, kw, stream, steps, warmup):
+    """The same replicas as separate systems, each advanced by its own
+    md_step calls (its own launches and graphs), one after the other."""
+    import torch
+    systems = [md.System(r.pos, r.vel, r.box, precision="mixed", stream=stream, **kw)
+               for r in reps]
+    for a in systems:
+        md.md_step(a.h, warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for a in systems:
+        md.md_step(a.h, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    n = sum(a.n for a in systems)
+    for a in systems:
+        a.close()
+    return {"atom_steps_per_s": n * steps / (e0.elapsed_time(e1) * 1e-3), "steps": steps,
+            "note": "each replica its own system: md_step per replica in turn, graphs on"}
 
 
 # ------------------------------------------------------------------ CPU legs
@@ -335,6 +414,10 @@ def oracle_sample_system(args):
         return inputs.lj_porous(nc=72), "porous LJ 72^3 fcc cells (same rho*, voids U(3,15), >=40%)"
     if args.workload == "fcc":
         return inputs.lj_fcc(nc=32, T=1.2), "LJ fcc 32^3 cells"
+    if args.workload == "ensemble":
+        reps = inputs.lj_ensemble(count=args.nc or 64)
+        k = max((r for r in range(len(reps)) if reps[r].n <= 150000), key=lambda r: reps[r].n)
+        return reps[k], "ensemble replica %d (the largest with <= 150,000 atoms)" % k
     return inputs.sc_fcc(nc=48), "Sutton-Chen fcc 48^3 cells"
 
 
@@ -367,7 +450,7 @@ def cpu_baseline_leg(args, gpu=None, steps=None):
            "sample": "%s, %d atoms, %d velocity-Verlet steps after the first list build "
                      "(fp64 C oracle, OpenMP over atoms)" % (what, s.n, k)}
     if gpu is not None:
-        rng_idx = (inputs.splitmix64(inputs.SEED_BASE + 99, 4096) % gpu["n"]).astype(np.int64)
+        rng_idx = (inputs.splitmix64(inputs.SEED_BASE + 99, 4096) % gpu["n_check"]).astype(np.int64)
         idx = np.unique(rng_idx)
         fref, _ = orc.forces_sample(oracle_params(orc, gpu["params"]), gpu["pos"], gpu["box"], idx)
         f = gpu["force"][idx]

@@ -100,6 +100,25 @@ typedef struct {
 md_status md_create(md_system **out, const md_params *p, int64_t n, const double *box3_host,
                     const double *pos_dev, const double *vel_dev, void *cuda_stream);
 
+/* A batch of n_replicas independent systems advanced together: replica r
+ * has n_each_host[r] atoms in the box box3_each_host[3r .. 3r+2]; pos_dev /
+ * vel_dev hold all replicas' atoms one replica after the other (n = sum of
+ * n_each).  Every step of the path runs as one launch over all replicas (the
+ * cells of all boxes are numbered consecutively), so small replicas do not
+ * pay one launch each.  Batches run mixed-precision Lennard-Jones with full
+ * lists under MD_SCHED_GRID or MD_SCHED_DYNAMIC; the list is rebuilt for all
+ * replicas when any replica needs it.  All other calls work on the whole
+ * batch (original order = the concatenation); md_get_cells reports global
+ * cell ids (replica r's cells follow those of replicas 0..r-1, each box in
+ * its own x-fastest order) and ncell_host = {total cells, 1, 1}. */
+md_status md_create_batch(md_system **out, const md_params *p, int32_t n_replicas,
+                          const int64_t *n_each_host, const double *box3_each_host,
+                          const double *pos_dev, const double *vel_dev, void *cuda_stream);
+
+/* Kinetic and potential energy of every replica (host arrays of n_replicas;
+ * 1 for md_create systems); a fresh force evaluation.  Synchronizes. */
+md_status md_energy_batch(md_system *h, double *ke_host, double *pe_host);
+
 /* Cell binning only (Sec. 2.1): assigns each atom to cell
  * c = min(floor(x * n_d / L_d), n_d - 1) per dimension, n_d = floor(L_d /
  * r_list), linear id (cz * ny + cy) * nx + cx, and reorders the private copy

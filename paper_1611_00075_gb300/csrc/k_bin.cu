@@ -8,6 +8,10 @@
 // equals a stable sort by (cell, original id).  The gather then rewrites the
 // state in the new order as float64 positions relative to the cell centre
 // plus their float32 copy (the layout the force kernels read).
+//
+// A system of several boxes (replicas) numbers its cells consecutively, box
+// after box, so each box's atoms stay one contiguous range of the sorted
+// order; every kernel reads the geometry of the atom's own box.
 #include "k_scan.cuh"
 
 namespace mdg {
@@ -36,6 +40,7 @@ __device__ __forceinline__ int cell_coord(double x, double inv_w, int n) {
     return (int)q;
 }
 
+// centre of the box-local cell `c` of geometry g
 __device__ __forceinline__ double3 cell_centre(int c, const Grid &g) {
     int cx = c % g.nx;
     int cy = (c / g.nx) % g.ny;
@@ -45,20 +50,23 @@ __device__ __forceinline__ double3 cell_centre(int c, const Grid &g) {
 }
 
 // Absolute positions from the relative state (skipped when they are exact).
-__global__ void prepare_abs_kernel(int n, Grid g, const double4 *__restrict__ xr,
+__global__ void prepare_abs_kernel(int n, const Grid *__restrict__ grids,
+                                   const uint16_t *__restrict__ rep,
+                                   const double4 *__restrict__ xr,
                                    const int32_t *__restrict__ cell, double4 *__restrict__ xabs,
                                    const DevStatus *ds, bool gated) {
     if (chain_off(ds, gated) || ds->abs_fresh) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double4 r = xr[i];
-    int c = cell[i];
-    double x = r.x, y = r.y, z = r.z;
-    if (c >= 0) {
-        double3 C = cell_centre(c, g);
-        x = C.x + x; y = C.y + y; z = C.z + z;
-    }
-    xabs[i] = make_double4(wrap_coord(x, g.L[0]), wrap_coord(y, g.L[1]), wrap_coord(z, g.L[2]),
-                           0.0);
+        const Grid &g = grids[rep ? rep[i] : 0];
+        double4 r = xr[i];
+        int c = cell[i];
+        double x = r.x, y = r.y, z = r.z;
+        if (c >= 0) {
+            double3 C = cell_centre(c - g.cell0, g);
+            x = C.x + x; y = C.y + y; z = C.z + z;
+        }
+        xabs[i] = make_double4(wrap_coord(x, g.L[0]), wrap_coord(y, g.L[1]),
+                               wrap_coord(z, g.L[2]), 0.0);
     }
 }
 
@@ -69,20 +77,23 @@ __global__ void zero_counts_kernel(int ncells, int32_t *count, DevStatus *ds, bo
         count[c] = 0;
 }
 
-__global__ void bin_count_kernel(int n, Grid g, const double4 *__restrict__ xabs,
+__global__ void bin_count_kernel(int n, const Grid *__restrict__ grids,
+                                 const uint16_t *__restrict__ rep,
+                                 const double4 *__restrict__ xabs,
                                  int32_t *__restrict__ count, int32_t *__restrict__ new_cell,
                                  int32_t *__restrict__ slot, DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double4 x = xabs[i];
-    int cx = cell_coord(x.x, g.inv_w[0], g.nx);
-    int cy = cell_coord(x.y, g.inv_w[1], g.ny);
-    int cz = cell_coord(x.z, g.inv_w[2], g.nz);
-    int c = (cz * g.ny + cy) * g.nx + cx;
-    new_cell[i] = c;
-    int s = atomicAdd(&count[c], 1);
-    slot[i] = s;
-    atomicMax(&ds->max_cell, s + 1);
+        const Grid &g = grids[rep ? rep[i] : 0];
+        double4 x = xabs[i];
+        int cx = cell_coord(x.x, g.inv_w[0], g.nx);
+        int cy = cell_coord(x.y, g.inv_w[1], g.ny);
+        int cz = cell_coord(x.z, g.inv_w[2], g.nz);
+        int c = g.cell0 + (cz * g.ny + cy) * g.nx + cx;
+        new_cell[i] = c;
+        int s = atomicAdd(&count[c], 1);
+        slot[i] = s;
+        atomicMax(&ds->max_cell, s + 1);
     }
 }
 
@@ -105,62 +116,69 @@ __global__ void cell_sort_kernel(int ncells, const int32_t *__restrict__ start,
                                  const DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
-    int b = start[c], e = start[c + 1];
-    for (int a = b + 1; a < e; ++a) {
-        int k = key[a], s = src[a];
-        int q = a - 1;
-        while (q >= b && key[q] > k) {
-            key[q + 1] = key[q];
-            src[q + 1] = src[q];
-            --q;
+        int b = start[c], e = start[c + 1];
+        for (int a = b + 1; a < e; ++a) {
+            int k = key[a], s = src[a];
+            int q = a - 1;
+            while (q >= b && key[q] > k) {
+                key[q + 1] = key[q];
+                src[q + 1] = src[q];
+                --q;
+            }
+            key[q + 1] = k;
+            src[q + 1] = s;
         }
-        key[q + 1] = k;
-        src[q + 1] = s;
-    }
     }
 }
 
 __global__ void copy_src_kernel(int n, const double4 *__restrict__ xabs,
                                 const double *__restrict__ v, const int32_t *__restrict__ orig,
-                                double4 *__restrict__ tabs, double *__restrict__ tv,
-                                int32_t *__restrict__ torig, const DevStatus *ds, bool gated) {
+                                const uint16_t *__restrict__ rep, double4 *__restrict__ tabs,
+                                double *__restrict__ tv, int32_t *__restrict__ torig,
+                                uint16_t *__restrict__ trep, const DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    tabs[i] = xabs[i];
-    tv[i] = v[i];
-    tv[n + i] = v[n + i];
-    tv[2 * (size_t)n + i] = v[2 * (size_t)n + i];
-    torig[i] = orig[i];
+        tabs[i] = xabs[i];
+        tv[i] = v[i];
+        tv[n + i] = v[n + i];
+        tv[2 * (size_t)n + i] = v[2 * (size_t)n + i];
+        torig[i] = orig[i];
+        if (rep) trep[i] = rep[i];
     }
 }
 
-__global__ void gather_kernel(int n, Grid g, const int32_t *__restrict__ src,
+__global__ void gather_kernel(int n, const Grid *__restrict__ grids,
+                              const int32_t *__restrict__ src,
                               const int32_t *__restrict__ new_cell,
                               const double4 *__restrict__ tabs, const double *__restrict__ tv,
-                              const int32_t *__restrict__ torig, double4 *__restrict__ xr,
+                              const int32_t *__restrict__ torig,
+                              const uint16_t *__restrict__ trep, double4 *__restrict__ xr,
                               float4 *__restrict__ xq, float4 *__restrict__ xq_build,
                               double4 *__restrict__ xabs, double *__restrict__ v,
                               int32_t *__restrict__ orig, int32_t *__restrict__ cell,
-                              DevStatus *ds, bool gated) {
+                              uint16_t *__restrict__ rep, DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) ds->abs_fresh = 1;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    int s = src[k];
-    int c = new_cell[s];
-    double3 C = cell_centre(c, g);
-    double4 a = tabs[s];
-    double rx = a.x - C.x, ry = a.y - C.y, rz = a.z - C.z;
-    int o = torig[s];
-    xr[k] = make_double4(rx, ry, rz, 0.0);
-    float4 q = make_float4((float)rx, (float)ry, (float)rz, __int_as_float(o));
-    xq[k] = q;
-    xq_build[k] = q;
-    xabs[k] = a;
-    v[k] = tv[s];
-    v[n + k] = tv[n + s];
-    v[2 * (size_t)n + k] = tv[2 * (size_t)n + s];
-    orig[k] = o;
-    cell[k] = c;
+        int s = src[k];
+        int c = new_cell[s];
+        const uint16_t r = trep ? trep[s] : 0;
+        const Grid &g = grids[r];
+        double3 C = cell_centre(c - g.cell0, g);
+        double4 a = tabs[s];
+        double rx = a.x - C.x, ry = a.y - C.y, rz = a.z - C.z;
+        int o = torig[s];
+        xr[k] = make_double4(rx, ry, rz, 0.0);
+        float4 q = make_float4((float)rx, (float)ry, (float)rz, __int_as_float(o));
+        xq[k] = q;
+        xq_build[k] = q;
+        xabs[k] = a;
+        v[k] = tv[s];
+        v[n + k] = tv[n + s];
+        v[2 * (size_t)n + k] = tv[2 * (size_t)n + s];
+        orig[k] = o;
+        cell[k] = c;
+        if (rep) rep[k] = r;
     }
 }
 
@@ -184,25 +202,28 @@ cudaError_t launch_bin(md_system *h, bool gated) {
     int n = (int)h->n;
     cudaStream_t s = h->stream;
     int cur = h->cur;
-    prepare_abs_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->g, h->xr64[cur], h->cell, h->xabs,
-                                                     h->ds, gated);
+    prepare_abs_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->grids, h->rep, h->xr64[cur], h->cell,
+                                                       h->xabs, h->ds, gated);
     zero_counts_kernel<<<gs_blocks(h->g.ncells), kBlock, 0, s>>>(h->g.ncells, h->cell_count,
-                                                               h->ds, gated);
-    bin_count_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->g, h->xabs, h->cell_count, h->new_cell,
-                                                   h->slot, h->ds, gated);
+                                                                 h->ds, gated);
+    bin_count_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->grids, h->rep, h->xabs,
+                                                     h->cell_count, h->new_cell, h->slot, h->ds,
+                                                     gated);
     cudaError_t e = launch_scan_i32(h->cell_count, h->cell_start, h->g.ncells, h->scan_bsum,
                                     h->ds, gated, s);
     if (e != cudaSuccess) return e;
-    scatter_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->new_cell, h->slot, h->cell_start, h->orig,
-                                                 h->src, h->key, h->ds, gated);
+    scatter_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->new_cell, h->slot, h->cell_start,
+                                                   h->orig, h->src, h->key, h->ds, gated);
     cell_sort_kernel<<<gs_blocks(h->g.ncells), kBlock, 0, s>>>(h->g.ncells, h->cell_start, h->key,
-                                                             h->src, h->ds, gated);
-    copy_src_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->xabs, h->v, h->orig, h->tmp_abs,
-                                                  h->tmp_v, h->tmp_orig, h->ds, gated);
-    gather_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->g, h->src, h->new_cell, h->tmp_abs,
-                                                h->tmp_v, h->tmp_orig, h->xr64[cur], h->xq[cur],
-                                                h->xq_build, h->xabs, h->v, h->orig, h->cell,
-                                                h->ds, gated);
+                                                               h->src, h->ds, gated);
+    copy_src_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->xabs, h->v, h->orig, h->rep,
+                                                    h->tmp_abs, h->tmp_v, h->tmp_orig,
+                                                    h->tmp_rep, h->ds, gated);
+    gather_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->grids, h->src, h->new_cell, h->tmp_abs,
+                                                  h->tmp_v, h->tmp_orig,
+                                                  h->rep ? h->tmp_rep : nullptr, h->xr64[cur],
+                                                  h->xq[cur], h->xq_build, h->xabs, h->v, h->orig,
+                                                  h->cell, h->rep, h->ds, gated);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,8 @@ struct ForceArgs {
     double *__restrict__ rho;     // many-body: rho_i (Eq. 2)
     float *__restrict__ dF32;     // many-body: F'(rho_i) in float32
     double *__restrict__ dF64;    // many-body: F'(rho_i) in float64
+    const uint16_t *__restrict__ rep;     // batches: replica of each sorted atom
+    const float4 *__restrict__ shifts32;  // batches: R x 27 float32 cell shifts
     DevStatus *ds;
     Grid g;
     ForceConsts fc;
@@ -78,7 +80,8 @@ __device__ __forceinline__ void step_bookkeeping(const ForceArgs &a) {
             a.ds->since_build = sb;
             if (a.rebuild_every > 0 && sb >= a.rebuild_every) a.ds->rebuild = 1;
         }
-        if (MODE != FM_STORE) a.ds->steps_done = a.step;
+        // a device-side count, so that a step replayed from a CUDA graph counts too
+        if (MODE != FM_STORE) a.ds->steps_done += 1;
     }
 }
 

@@ -64,7 +64,8 @@ __global__ void load_state_kernel(int n, const double *__restrict__ pos,
                                   const double *__restrict__ vel, double4 *__restrict__ xr,
                                   float4 *__restrict__ xq, double4 *__restrict__ xabs,
                                   double *__restrict__ v, int32_t *__restrict__ orig,
-                                  int32_t *__restrict__ cell, DevStatus *ds) {
+                                  int32_t *__restrict__ cell, const int64_t *__restrict__ atom_off,
+                                  int R, uint16_t *__restrict__ rep, DevStatus *ds) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         ds->abs_fresh = 1;
@@ -80,6 +81,16 @@ __global__ void load_state_kernel(int n, const double *__restrict__ pos,
         xq[i] = make_float4((float)a.x, (float)a.y, (float)a.z, __int_as_float(i));
         orig[i] = i;
         cell[i] = -1;
+        if (rep) {
+            // replica of input row i: the last r with atom_off[r] <= i
+            int lo = 0, hi = R - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (atom_off[mid] <= i) lo = mid;
+                else hi = mid - 1;
+            }
+            rep[i] = (uint16_t)lo;
+        }
     }
     if (vel) {
         v[i] = vel[3 * (size_t)i];
@@ -99,7 +110,8 @@ __global__ void load_vel_kernel(int n, const double *__restrict__ vel,
     v[2 * N + i] = vel[3 * o + 2];
 }
 
-__global__ void get_state_kernel(int n, Grid g, const double4 *__restrict__ xr,
+__global__ void get_state_kernel(int n, const Grid *__restrict__ grids,
+                                 const uint16_t *__restrict__ rep, const double4 *__restrict__ xr,
                                  const double4 *__restrict__ xabs, const int32_t *__restrict__ cell,
                                  const int32_t *__restrict__ orig, const double *__restrict__ v,
                                  const double *__restrict__ f, double *pos, double *vel,
@@ -108,6 +120,7 @@ __global__ void get_state_kernel(int n, Grid g, const double4 *__restrict__ xr,
     if (i >= n) return;
     const size_t N = (size_t)n, o = (size_t)orig[i];
     if (pos) {
+        const Grid &g = grids[rep ? rep[i] : 0];
         double x, y, z;
         if (ds->abs_fresh) {
             double4 a = xabs[i];
@@ -117,6 +130,7 @@ __global__ void get_state_kernel(int n, Grid g, const double4 *__restrict__ xr,
             x = r.x; y = r.y; z = r.z;
             int c = cell[i];
             if (c >= 0) {
+                c -= g.cell0;
                 int cx = c % g.nx, cy = (c / g.nx) % g.ny, cz = c / (g.nx * g.ny);
                 x = ((double)cx + 0.5) * g.w[0] + x;
                 y = ((double)cy + 0.5) * g.w[1] + y;
@@ -199,6 +213,30 @@ __global__ void final_sum_kernel(int nb, const double *__restrict__ partials, do
 
 __global__ void set_rebuild_kernel(DevStatus *ds) { ds->rebuild = 1; }
 
+// One block per replica: its atoms are one contiguous sorted range (its
+// cells); fixed-order sums of potential and kinetic energy.
+__global__ void replica_energy_kernel(const Grid *__restrict__ grids,
+                                      const int32_t *__restrict__ start,
+                                      const double *__restrict__ e, const double *__restrict__ v,
+                                      int n, double half_m, double *__restrict__ pe,
+                                      double *__restrict__ ke) {
+    const Grid &g = grids[blockIdx.x];
+    const int a = start[g.cell0], b = start[g.cell0 + g.ncells];
+    const size_t N = (size_t)n;
+    double sp = 0.0, sk = 0.0;
+    for (int i = a + threadIdx.x; i < b; i += blockDim.x) {
+        sp += e[i];
+        const double x = v[i], y = v[N + i], z = v[2 * N + i];
+        sk += half_m * (x * x + y * y + z * z);
+    }
+    const double tp = block_sum(sp);
+    const double tk = block_sum(sk);
+    if (threadIdx.x == 0) {
+        pe[blockIdx.x] = tp;
+        ke[blockIdx.x] = tk;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_kick_drift(md_system *h) {
@@ -213,7 +251,8 @@ cudaError_t launch_load_state(md_system *h, const double *pos, const double *vel
     int n = (int)h->n;
     if (pos) {
         load_state_kernel<<<nblocks(n), kBlock, 0, h->stream>>>(
-            n, pos, vel, h->xr64[h->cur], h->xq[h->cur], h->xabs, h->v, h->orig, h->cell, h->ds);
+            n, pos, vel, h->xr64[h->cur], h->xq[h->cur], h->xabs, h->v, h->orig, h->cell,
+            h->atom_off, h->R, h->rep, h->ds);
     } else if (vel) {
         load_vel_kernel<<<nblocks(n), kBlock, 0, h->stream>>>(n, vel, h->orig, h->v);
     }
@@ -222,9 +261,16 @@ cudaError_t launch_load_state(md_system *h, const double *pos, const double *vel
 
 cudaError_t launch_get_state(md_system *h, double *pos, double *vel, double *force) {
     int n = (int)h->n;
-    get_state_kernel<<<nblocks(n), kBlock, 0, h->stream>>>(n, h->g, h->xr64[h->cur], h->xabs,
-                                                           h->cell, h->orig, h->v, h->f, pos,
-                                                           vel, force, h->ds);
+    get_state_kernel<<<nblocks(n), kBlock, 0, h->stream>>>(n, h->grids, h->rep, h->xr64[h->cur],
+                                                           h->xabs, h->cell, h->orig, h->v, h->f,
+                                                           pos, vel, force, h->ds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_replica_energy(md_system *h) {
+    replica_energy_kernel<<<h->R, kBlock, 0, h->stream>>>(h->grids, h->cell_start, h->e_atom, h->v,
+                                                          (int)h->n, 0.5 * h->p.mass, h->rep_pe,
+                                                          h->rep_ke);
     return cudaGetLastError();
 }
 

@@ -41,10 +41,13 @@ __device__ __forceinline__ void load_shifts_f32(const ForceArgs &a, float4 *sh) 
 }
 
 // The whole per-atom job of the mixed path for sorted atom i: pair loop over
-// its list, stores, and the velocity-Verlet epilogue.
-template <int MODE, bool ENERGY>
+// its list, stores, and the velocity-Verlet epilogue.  MULTI (systems of
+// several boxes) reads the cell shifts of the atom's own box from a global
+// R x 27 table instead of the block's shared table.
+template <int MODE, bool ENERGY, bool MULTI = false>
 __device__ __forceinline__ void lj_mixed_atom(const ForceArgs &a, const float4 *sh, int i,
                                               int store_f) {
+    const float4 *shr = MULTI ? a.shifts32 + 27 * (int)a.rep[i] : sh;
     const float4 qi = a.xq[i];
     const int nq = (min(a.ncount[i], a.cap) + 3) >> 2;
     const uint4 *lq = reinterpret_cast<const uint4 *>(a.nlist + list_group(i, a.cap)) + (i & 31);
@@ -54,7 +57,7 @@ __device__ __forceinline__ void lj_mixed_atom(const ForceArgs &a, const float4 *
     float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
     auto pair = [&](uint32_t ent) {
         const float4 qj = __ldg(a.xq + (ent & kIndexMask));
-        const float4 sf = sh[ent >> kIndexBits];
+        const float4 sf = MULTI ? __ldg(shr + (ent >> kIndexBits)) : sh[ent >> kIndexBits];
         const float ex = (qj.x - qi.x) + sf.x;
         const float ey = (qj.y - qi.y) + sf.y;
         const float ez = (qj.z - qi.z) + sf.z;
@@ -109,15 +112,15 @@ __device__ __forceinline__ void lj_mixed_atom(const ForceArgs &a, const float4 *
 }
 
 // One thread per sorted atom; the hardware block scheduler spreads the work.
-template <int MODE, bool ENERGY>
+template <int MODE, bool ENERGY, bool MULTI = false>
 __global__ void __launch_bounds__(kBlock, 5) lj_mixed_kernel(ForceArgs a, int store_f) {
     __shared__ float4 sh[kStencil];
-    load_shifts_f32(a, sh);
+    if (!MULTI) load_shifts_f32(a, sh);
     __syncthreads();
     if (a.ds->status != 0) return;
     step_bookkeeping<MODE>(a);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.n) lj_mixed_atom<MODE, ENERGY>(a, sh, i, store_f);
+    if (i < a.n) lj_mixed_atom<MODE, ENERGY, MULTI>(a, sh, i, store_f);
 }
 
 // Persistent variant: gridDim.x CTAs stay resident; each warp processes tiles
@@ -136,11 +139,11 @@ __global__ void __launch_bounds__(kBlock, 5) lj_mixed_kernel(ForceArgs a, int st
 // cycles go to cta_cycles -- the training data of the cost model.
 constexpr int kClaim = 8;  // tiles claimed per atomic by the dynamic queue
 
-template <int MODE, bool ENERGY, bool DYNAMIC, bool TIMING>
+template <int MODE, bool ENERGY, bool DYNAMIC, bool TIMING, bool MULTI = false>
 __global__ void __launch_bounds__(kBlock, 5)
 lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
     __shared__ float4 sh[kStencil];
-    load_shifts_f32(a, sh);
+    if (!MULTI) load_shifts_f32(a, sh);
     __syncthreads();
     if (a.ds->status != 0) return;
     step_bookkeeping<MODE>(a);
@@ -187,7 +190,7 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
             __syncwarp();
             t0 = clock64();
         }
-        if (active) lj_mixed_atom<MODE, ENERGY>(a, sh, i, store_f);
+        if (active) lj_mixed_atom<MODE, ENERGY, MULTI>(a, sh, i, store_f);
         if (TIMING) {
             __syncwarp();
             const long long dt = clock64() - t0;
@@ -287,6 +290,8 @@ ForceArgs make_force_args(md_system *h) {
     a.rho = h->rho;
     a.dF32 = h->dF32;
     a.dF64 = h->dF64;
+    a.rep = h->rep;
+    a.shifts32 = h->shifts32;
     a.ds = h->ds;
     a.g = h->g;
     a.fc = h->fc;
@@ -299,7 +304,21 @@ cudaError_t launch_lj(md_system *h, int mode, bool energy, bool store_f) {
     const int sf = store_f ? 1 : 0;
     cudaStream_t s = h->stream;
 #define MDG_LJ(K, M, E) K<M, E><<<nb, kBlock, 0, s>>>(a, sf)
-    if (h->p.precision == MD_MIXED) {
+    if (h->R > 1) {
+        // several boxes: mixed precision only (checked at creation)
+        switch (mode) {
+            case FM_STORE:
+                if (energy) lj_mixed_kernel<FM_STORE, true, true><<<nb, kBlock, 0, s>>>(a, sf);
+                else lj_mixed_kernel<FM_STORE, false, true><<<nb, kBlock, 0, s>>>(a, sf);
+                break;
+            case FM_FUSED_FULL:
+                lj_mixed_kernel<FM_FUSED_FULL, false, true><<<nb, kBlock, 0, s>>>(a, sf);
+                break;
+            default:
+                lj_mixed_kernel<FM_FUSED_HALF, false, true><<<nb, kBlock, 0, s>>>(a, sf);
+                break;
+        }
+    } else if (h->p.precision == MD_MIXED) {
         switch (mode) {
             case FM_STORE: if (energy) MDG_LJ(lj_mixed_kernel, FM_STORE, true); else MDG_LJ(lj_mixed_kernel, FM_STORE, false); break;
             case FM_FUSED_FULL: if (energy) MDG_LJ(lj_mixed_kernel, FM_FUSED_FULL, true); else MDG_LJ(lj_mixed_kernel, FM_FUSED_FULL, false); break;
@@ -340,6 +359,21 @@ cudaError_t launch_lj_persist(md_system *h, int mode, bool store_f, bool dynamic
     const int G = h->sched_ctas;
     const int sf = store_f ? 1 : 0;
     cudaStream_t s = h->stream;
+    if (h->R > 1) {
+        // several boxes: the tile queue (the static partitions are single-box)
+        switch (mode) {
+            case FM_STORE:
+                lj_mixed_persist<FM_STORE, false, true, false, true><<<G, kBlock, 0, s>>>(a, sf, sa);
+                break;
+            case FM_FUSED_FULL:
+                lj_mixed_persist<FM_FUSED_FULL, false, true, false, true><<<G, kBlock, 0, s>>>(a, sf, sa);
+                break;
+            default:
+                lj_mixed_persist<FM_FUSED_HALF, false, true, false, true><<<G, kBlock, 0, s>>>(a, sf, sa);
+                break;
+        }
+        return cudaGetLastError();
+    }
     if (timing) {
         if (dynamic) lj_mixed_persist<FM_STORE, false, true, true><<<G, kBlock, 0, s>>>(a, 1, sa);
         else lj_mixed_persist<FM_STORE, false, false, true><<<G, kBlock, 0, s>>>(a, 1, sa);

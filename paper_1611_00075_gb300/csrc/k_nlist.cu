@@ -27,24 +27,20 @@ __device__ __forceinline__ bool chain_off(const DevStatus *ds, bool gated) {
 
 template <bool PREFILTER, bool WRITE, bool HALF>
 __global__ void __launch_bounds__(kBlock)
-build_list_kernel(int n, Grid g, float lo, float hi, double rl2, const float4 *__restrict__ xq,
+build_list_kernel(int n, const Grid *__restrict__ grids, const uint16_t *__restrict__ rep,
+                  float lo, float hi, double rl2, const float4 *__restrict__ xq,
                   const double4 *__restrict__ xabs, const int32_t *__restrict__ cell,
                   const int32_t *__restrict__ start, uint32_t *__restrict__ nlist,
                   int32_t *__restrict__ ncount, int cap, DevStatus *ds, bool gated) {
-    __shared__ float4 sh[kStencil];
-    if (threadIdx.x < kStencil) {
-        int s = threadIdx.x;
-        int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
-        sh[s] = make_float4((float)(dx * g.w[0]), (float)(dy * g.w[1]), (float)(dz * g.w[2]),
-                            0.f);
-    }
-    __syncthreads();
     if (chain_off(ds, gated)) return;
     unsigned long long tot = 0;
     int overflow = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int cnt = 0;
-        const int c = cell[i];
+        const Grid &g = grids[rep ? rep[i] : 0];
+        // float32 cell widths: stencil shift (dx, dy, dz) * w, exact for dx in {-1, 0, 1}
+        const float wx = (float)g.w[0], wy = (float)g.w[1], wz = (float)g.w[2];
+        const int c = cell[i] - g.cell0;
         const int cx = c % g.nx, cy = (c / g.nx) % g.ny, cz = c / (g.nx * g.ny);
         const float4 qi = xq[i];
         const double4 ai = xabs[i];
@@ -66,11 +62,11 @@ build_list_kernel(int n, Grid g, float lo, float hi, double rl2, const float4 *_
                     double shx = 0.0;
                     if (xx < 0) { xx += g.nx; shx = -g.L[0]; }
                     else if (xx >= g.nx) { xx -= g.nx; shx = g.L[0]; }
-                    const int cn = (zz * g.ny + yy) * g.nx + xx;
+                    const int cn = g.cell0 + (zz * g.ny + yy) * g.nx + xx;
                     const int s = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
-                    const float4 sf = sh[s];
                     // home position moved against the cell shift: e = q_j - (q_i - shift)
-                    const float hx = qi.x - sf.x, hy = qi.y - sf.y, hz = qi.z - sf.z;
+                    const float hx = qi.x - (float)dx * wx, hy = qi.y - (float)dy * wy,
+                                hz = qi.z - (float)dz * wz;
                     const int b = start[cn], e = start[cn + 1];
                     const int skip = (s == 13) ? i : -1;  // the atom itself, home cell only
 #pragma unroll 4
@@ -199,7 +195,8 @@ cudaError_t launch_build_list(md_system *h, bool write, bool gated) {
     reset_max_count_kernel<<<1, 1, 0, s>>>(h->ds, gated);
 #define MDG_LIST(PF, WR, HF)                                                                    \
     build_list_kernel<PF, WR, HF><<<gs_blocks(n), kBlock, 0, s>>>(                                \
-        n, h->g, h->list_lo, h->list_hi, h->rl2, h->xq[cur], h->xabs, h->cell, h->cell_start, \
+        n, h->grids, h->rep, h->list_lo, h->list_hi, h->rl2, h->xq[cur], h->xabs, h->cell,   \
+        h->cell_start,                                                                         \
         h->nlist, h->ncount, h->cap, h->ds, gated)
     if (prefilter) {
         if (write) { if (half) MDG_LIST(true, true, true); else MDG_LIST(true, true, false); }

@@ -93,11 +93,16 @@ void free_all(md_system *h) {
     F(h->cell_cycles); F(h->cta_cycles); F(h->samp_flag); F(h->samp_bsum); F(h->samp_X);
     F(h->samp_y); F(h->mlp_P); F(h->mlp_G); F(h->mlp_m); F(h->mlp_v); F(h->mlp_scratch);
     F(h->mlp_loss);
+    F(h->grids); F(h->atom_off); F(h->rep); F(h->tmp_rep); F(h->shifts32); F(h->rep_pe);
+    F(h->rep_ke);
     if (h->ds_host) cudaFreeHost(h->ds_host);
     if (h->red_host) cudaFreeHost(h->red_host);
 }
 
+void drop_graphs(md_system *h);
+
 cudaError_t alloc_list(md_system *h, int cap) {
+    drop_graphs(h);  // captured steps hold the old list pointer and capacity
     if (h->nlist) cudaFree(h->nlist);
     h->nlist = nullptr;
     h->cap = cap;
@@ -169,6 +174,7 @@ bool uses_partition(const md_system *h) {
 // Buffers of the scheduler and the cost model, allocated on first use.
 md_status ensure_sched(md_system *h) {
     if (h->part_bounds) return MD_OK;
+    drop_graphs(h);
     int dev = 0, sms = 0;
     MD_CK(cudaGetDevice(&dev));
     MD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -315,44 +321,131 @@ md_status forces_now(md_system *h, bool energy) {
 
 __global__ void begin_steps_kernel(DevStatus *ds, int base) { ds->steps_done = base; }
 
+// ---- CUDA graphs of one full step ---------------------------------------------
+//
+// The launches of a step that is neither the first nor the last of an md_step
+// call -- the gated rebuild chain and the fused force + kick + drift -- are
+// the same every step except for the double-buffer parity, so they are
+// captured once per parity and replayed.  Kernels that decide on the device
+// (rebuild gate, status word, step counter) keep working under replay.  Any
+// change of buffers or launch choice drops the graphs; capture needs a
+// non-default stream and is skipped while per-launch timing is on.
+
+void drop_graphs(md_system *h) {
+    for (int b = 0; b < 2; ++b)
+        if (h->gexec[b]) {
+            cudaGraphExecDestroy(h->gexec[b]);
+            h->gexec[b] = nullptr;
+        }
+}
+
+md_status capture_full_step(md_system *h, int parity) {
+    const long long l0 = h->launches;
+    cudaGraph_t graph = nullptr;
+    MD_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    md_status st = enqueue_rebuild(h, true);
+    if (st == MD_OK) st = enqueue_forces(h, FM_FUSED_FULL, false, false);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (st == MD_OK && e == cudaSuccess)
+        e = cudaGraphInstantiate(&h->gexec[parity], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    h->graph_launches[parity] = h->launches - l0;
+    h->launches = l0;
+    if (st != MD_OK || e != cudaSuccess) {
+        cudaGetLastError();
+        h->gexec[parity] = nullptr;
+        h->graphs_ok = false;  // fall back to plain launches for this handle
+    }
+    return MD_OK;
+}
+
+// One step between the first and the last of an md_step call (parity h->cur).
+md_status enqueue_full_step(md_system *h) {
+    const int par = h->cur;
+    if (h->graphs_ok && !h->timing && h->stream != nullptr) {
+        if (!h->gexec[par]) {
+            md_status st = capture_full_step(h, par);
+            if (st != MD_OK) return st;
+        }
+        if (h->gexec[par]) {
+            MD_CK(cudaGraphLaunch(h->gexec[par], h->stream));
+            h->launches += h->graph_launches[par];
+            return MD_OK;
+        }
+    }
+    md_status st = enqueue_rebuild(h, true);
+    if (st != MD_OK) return st;
+    return enqueue_forces(h, FM_FUSED_FULL, false, false);
+}
+
 }  // namespace
 
 void mdg::set_thread_error(const std::string &msg) { g_thread_error = msg; }
 
 extern "C" {
 
-md_status md_create(md_system **out, const md_params *p, int64_t n, const double *box3_host,
-                    const double *pos_dev, const double *vel_dev, void *cuda_stream) {
+// Shared by md_create (one box) and md_create_batch (R boxes, atoms and
+// positions concatenated box after box).
+static md_status create_impl(md_system **out, const md_params *p, int R, const int64_t *n_each,
+                             const double *boxes, const double *pos_dev, const double *vel_dev,
+                             void *cuda_stream, const char *who) {
     md_system *h = nullptr;
-    if (!out || !p || !box3_host || !pos_dev)
-        return fail(nullptr, MD_ERR_INVALID, "md_create: null argument");
+    const std::string W(who);
+    if (!out || !p || !boxes || !pos_dev || !n_each || R < 1)
+        return fail(nullptr, MD_ERR_INVALID, W + ": null argument");
     *out = nullptr;
+    if (R > 65535) return fail(nullptr, MD_ERR_INVALID, W + ": at most 65535 replicas");
+    int64_t n = 0;
     std::string why;
-    if (check_params(p, n, box3_host, &why) != MD_OK)
-        return fail(nullptr, MD_ERR_INVALID, "md_create: " + why);
+    for (int r = 0; r < R; ++r) {
+        if (check_params(p, n_each[r], boxes + 3 * r, &why) != MD_OK)
+            return fail(nullptr, MD_ERR_INVALID,
+                        W + (R > 1 ? ": replica " + std::to_string(r) + ": " : ": ") + why);
+        n += n_each[r];
+    }
+    if (n >= kMaxAtoms) return fail(nullptr, MD_ERR_INVALID, W + ": too many atoms in total");
     if (p->force_variant != MD_FORCE_FULL && p->potential == MD_POT_SC)
-        return fail(nullptr, MD_ERR_INVALID, "md_create: half lists are built for Lennard-Jones only");
+        return fail(nullptr, MD_ERR_INVALID, W + ": half lists are built for Lennard-Jones only");
     if (p->force_variant != MD_FORCE_FULL && p->precision != MD_MIXED)
-        return fail(nullptr, MD_ERR_INVALID, "md_create: half lists are built for the mixed path");
+        return fail(nullptr, MD_ERR_INVALID, W + ": half lists are built for the mixed path");
+    if (R > 1 && (p->potential != MD_POT_LJ || p->precision != MD_MIXED ||
+                  p->force_variant != MD_FORCE_FULL ||
+                  (p->scheduler != MD_SCHED_GRID && p->scheduler != MD_SCHED_DYNAMIC)))
+        return fail(nullptr, MD_ERR_INVALID,
+                    W + ": batches run mixed-precision Lennard-Jones with full lists under "
+                        "MD_SCHED_GRID or MD_SCHED_DYNAMIC");
     h = new (std::nothrow) md_system();
-    if (!h) return fail(nullptr, MD_ERR_OOM, "md_create: host allocation failed");
+    if (!h) return fail(nullptr, MD_ERR_OOM, W + ": host allocation failed");
     h->p = *p;
     h->n = n;
+    h->R = R;
     h->stream = (cudaStream_t)cuda_stream;
     h->r_list = p->rc + p->skin;
     h->rl2 = h->r_list * h->r_list;
     h->list_lo = (float)(h->rl2 * (1.0 - 1.0 / 16384.0));
     h->list_hi = (float)(h->rl2 * (1.0 + 1.0 / 16384.0));
-    Grid &g = h->g;
-    int nc[3];
-    for (int d = 0; d < 3; ++d) {
-        nc[d] = (int)std::floor(box3_host[d] / h->r_list);
-        g.L[d] = box3_host[d];
-        g.w[d] = box3_host[d] / nc[d];
-        g.inv_w[d] = (double)nc[d] / box3_host[d];
+    int cells_total = 0;
+    h->atom_off_h.assign(1, 0);
+    for (int r = 0; r < R; ++r) {
+        Grid g{};
+        int nc[3];
+        for (int d = 0; d < 3; ++d) {
+            nc[d] = (int)std::floor(boxes[3 * r + d] / h->r_list);
+            g.L[d] = boxes[3 * r + d];
+            g.w[d] = boxes[3 * r + d] / nc[d];
+            g.inv_w[d] = (double)nc[d] / boxes[3 * r + d];
+        }
+        g.nx = nc[0]; g.ny = nc[1]; g.nz = nc[2];
+        g.ncells = nc[0] * nc[1] * nc[2];
+        g.cell0 = cells_total;
+        cells_total += g.ncells;
+        h->grids_h.push_back(g);
+        h->atom_off_h.push_back(h->atom_off_h.back() + n_each[r]);
     }
-    g.nx = nc[0]; g.ny = nc[1]; g.nz = nc[2];
-    g.ncells = nc[0] * nc[1] * nc[2];
+    // h->g: the first box, with the cell count of the whole system
+    h->g = h->grids_h[0];
+    h->g.ncells = cells_total;
+    h->g.cell0 = 0;
     ForceConsts &fc = h->fc;
     const double s2 = p->sigma * p->sigma, rc2 = p->rc * p->rc;
     const double sr6 = std::pow(s2 / rc2, 3);
@@ -366,7 +459,7 @@ md_status md_create(md_system **out, const md_params *p, int64_t n, const double
     fc.dt = p->dt; fc.inv_m = 1.0 / p->mass;
     fc.half_skin2f = (float)(0.25 * p->skin * p->skin);
 
-    const size_t N = (size_t)n, C = (size_t)g.ncells;
+    const size_t N = (size_t)n, C = (size_t)cells_total;
     const size_t scan_len = std::max(N, C + 1) / (kBlock * 8) + 4;
     cudaError_t e = cudaSuccess;
     auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
@@ -377,6 +470,12 @@ md_status md_create(md_system **out, const md_params *p, int64_t n, const double
     A(dalloc(&h->new_cell, N)); A(dalloc(&h->slot, N)); A(dalloc(&h->src, N));
     A(dalloc(&h->key, N)); A(dalloc(&h->scan_bsum, scan_len)); A(dalloc(&h->tmp_abs, N));
     A(dalloc(&h->tmp_v, 3 * N)); A(dalloc(&h->tmp_orig, N)); A(dalloc(&h->ncount, N));
+    A(dalloc(&h->grids, (size_t)R)); A(dalloc(&h->atom_off, (size_t)R + 1));
+    A(dalloc(&h->rep_pe, (size_t)R)); A(dalloc(&h->rep_ke, (size_t)R));
+    if (R > 1) {
+        A(dalloc(&h->rep, N)); A(dalloc(&h->tmp_rep, N));
+        A(dalloc(&h->shifts32, (size_t)R * kStencil));
+    }
     if (p->potential == MD_POT_SC) {
         A(dalloc(&h->rho, N)); A(dalloc(&h->dF32, N)); A(dalloc(&h->dF64, N));
     }
@@ -387,7 +486,7 @@ md_status md_create(md_system **out, const md_params *p, int64_t n, const double
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->red_host, 4 * sizeof(double));
     if (e != cudaSuccess) {
         md_status st = (e == cudaErrorMemoryAllocation) ? MD_ERR_OOM : MD_ERR_CUDA;
-        std::string m = std::string("md_create: allocation failed: ") + cudaGetErrorString(e);
+        std::string m = W + ": allocation failed: " + cudaGetErrorString(e);
         cudaGetLastError();
         free_all(h);
         delete h;
@@ -398,21 +497,68 @@ md_status md_create(md_system **out, const md_params *p, int64_t n, const double
         if (st == MD_OK && r != cudaSuccess)
             st = fail(h, MD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(r));
     };
+    std::vector<float4> sh;
+    if (R > 1) {
+        for (int r = 0; r < R; ++r)
+            for (int s = 0; s < kStencil; ++s) {
+                const Grid &g = h->grids_h[r];
+                const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+                sh.push_back(make_float4((float)(dx * g.w[0]), (float)(dy * g.w[1]),
+                                         (float)(dz * g.w[2]), 0.f));
+            }
+        step(cudaMemcpyAsync(h->shifts32, sh.data(), sh.size() * sizeof(float4),
+                             cudaMemcpyHostToDevice, h->stream), "copy shifts");
+    }
+    step(cudaMemcpyAsync(h->grids, h->grids_h.data(), R * sizeof(Grid), cudaMemcpyHostToDevice,
+                         h->stream), "copy grids");
+    step(cudaMemcpyAsync(h->atom_off, h->atom_off_h.data(), (R + 1) * sizeof(int64_t),
+                         cudaMemcpyHostToDevice, h->stream), "copy offsets");
     step(cudaMemsetAsync(h->ds, 0, sizeof(DevStatus), h->stream), "memset status");
     step(cudaMemsetAsync(h->f, 0, 3 * N * sizeof(double), h->stream), "memset f");
     step(cudaMemsetAsync(h->e_atom, 0, N * sizeof(double), h->stream), "memset e");
     if (!vel_dev) step(cudaMemsetAsync(h->v, 0, 3 * N * sizeof(double), h->stream), "memset v");
     step(launch_load_state(h, pos_dev, vel_dev), "load_state");
+    // host arrays above stay alive until the copies finish
+    if (st == MD_OK) step(cudaStreamSynchronize(h->stream), "synchronize");
     if (st == MD_OK && p->scheduler != MD_SCHED_GRID) st = ensure_sched(h);
     if (st == MD_OK) st = rebuild_now(h, true);
     if (st == MD_OK) st = forces_now(h, false);
     if (st != MD_OK) {
-        g_thread_error = "md_create: " + h->last_error;
+        g_thread_error = W + ": " + h->last_error;
         free_all(h);
         delete h;
         return st;
     }
     *out = h;
+    return MD_OK;
+}
+
+md_status md_create(md_system **out, const md_params *p, int64_t n, const double *box3_host,
+                    const double *pos_dev, const double *vel_dev, void *cuda_stream) {
+    return create_impl(out, p, 1, &n, box3_host, pos_dev, vel_dev, cuda_stream, "md_create");
+}
+
+md_status md_create_batch(md_system **out, const md_params *p, int32_t n_replicas,
+                          const int64_t *n_each_host, const double *box3_each_host,
+                          const double *pos_dev, const double *vel_dev, void *cuda_stream) {
+    return create_impl(out, p, n_replicas, n_each_host, box3_each_host, pos_dev, vel_dev,
+                       cuda_stream, "md_create_batch");
+}
+
+md_status md_energy_batch(md_system *h, double *ke_host, double *pe_host) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_energy_batch: null handle");
+    MD_CK(cudaMemsetAsync(&h->ds->pairs_cut, 0, sizeof(unsigned long long), h->stream));
+    md_status st = forces_now(h, true);
+    if (st != MD_OK) return st;
+    MD_CK(launch_replica_energy(h));
+    h->launches += 1;
+    if (ke_host)
+        MD_CK(cudaMemcpyAsync(ke_host, h->rep_ke, h->R * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
+    if (pe_host)
+        MD_CK(cudaMemcpyAsync(pe_host, h->rep_pe, h->R * sizeof(double), cudaMemcpyDeviceToHost,
+                              h->stream));
+    MD_CK(cudaStreamSynchronize(h->stream));
     return MD_OK;
 }
 
@@ -460,10 +606,14 @@ md_status md_step(md_system *h, int64_t nsteps) {
         for (int64_t s = sr; s <= nsteps; ++s) {
             h->steps_total = base + s;
             h->cur = c0 ^ (int)((s - 1) & 1);
+            if (s < nsteps) {
+                st = enqueue_full_step(h);
+                if (st != MD_OK) return st;
+                continue;
+            }
             st = enqueue_rebuild(h, true);
             if (st != MD_OK) return st;
-            const int mode = (s < nsteps) ? FM_FUSED_FULL : FM_FUSED_HALF;
-            st = enqueue_forces(h, mode, false, s == nsteps);
+            st = enqueue_forces(h, FM_FUSED_HALF, false, true);
             if (st != MD_OK) return st;
         }
         h->cur = c0 ^ (int)((nsteps - 1) & 1);
@@ -494,6 +644,8 @@ md_status md_step(md_system *h, int64_t nsteps) {
             return fail(h, MD_ERR_LIST_OVERFLOW, "md_step: neighbour count exceeds max_neighbors");
         MD_CK(alloc_list(h, cap_for(h->ds_host->max_count)));
         MD_CK(launch_build_list(h, true, false));
+        st = enqueue_sched_prep(h, false);
+        if (st != MD_OK) return st;
         MD_CK(launch_finish_rebuild(h, false));
         sr = S;
         // re-enqueue steps S..nsteps; the loop's first rebuild is gated off
@@ -592,9 +744,10 @@ md_status md_get_cells(md_system *h, int32_t *cell_of_atom_dev, int64_t *cell_st
     MD_CK(launch_export_cells(h, cell_of_atom_dev, cell_start_dev));
     MD_CK(cudaStreamSynchronize(h->stream));
     if (ncell_host) {
-        ncell_host[0] = h->g.nx;
-        ncell_host[1] = h->g.ny;
-        ncell_host[2] = h->g.nz;
+        // a batch reports its cells as one line, so that the product sizes cell_start
+        ncell_host[0] = h->R > 1 ? h->g.ncells : h->g.nx;
+        ncell_host[1] = h->R > 1 ? 1 : h->g.ny;
+        ncell_host[2] = h->R > 1 ? 1 : h->g.nz;
     }
     return MD_OK;
 }
@@ -629,7 +782,12 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
         return fail(h, MD_ERR_INVALID, "md_set_variant: half lists are built for Lennard-Jones only");
     if (force_variant != MD_FORCE_FULL && h->p.precision != MD_MIXED)
         return fail(h, MD_ERR_INVALID, "md_set_variant: half lists are built for the mixed path");
+    if (h->R > 1 && (force_variant != MD_FORCE_FULL ||
+                     (scheduler != MD_SCHED_GRID && scheduler != MD_SCHED_DYNAMIC)))
+        return fail(h, MD_ERR_INVALID,
+                    "md_set_variant: batches run full lists under MD_SCHED_GRID or MD_SCHED_DYNAMIC");
     const bool relist = (force_variant != MD_FORCE_FULL) != (h->p.force_variant != MD_FORCE_FULL);
+    drop_graphs(h);  // the captured steps launch the old variant's kernels
     h->p.force_variant = force_variant;
     h->p.scheduler = scheduler;
     md_status st = MD_OK;
@@ -682,10 +840,10 @@ md_status cta_imbalance(md_system *h, float *out) {
 md_status md_cost_model(md_system *h, int32_t op, float *loss_out) {
     if (!h) return fail(nullptr, MD_ERR_INVALID, "md_cost_model: null handle");
     if (h->p.potential != MD_POT_LJ || h->p.precision != MD_MIXED ||
-        h->p.force_variant != MD_FORCE_FULL)
+        h->p.force_variant != MD_FORCE_FULL || h->R > 1)
         return fail(h, MD_ERR_INVALID,
                     "md_cost_model: the cost model drives the persistent mixed-precision "
-                    "Lennard-Jones full-list force kernel");
+                    "Lennard-Jones full-list force kernel of a single box");
     md_status st = ensure_sched(h);
     if (st != MD_OK) return st;
     const int kPasses = 3, kIters = 400;
@@ -811,6 +969,7 @@ void md_destroy(md_system *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    drop_graphs(h);
     free_all(h);
     delete h;
 }

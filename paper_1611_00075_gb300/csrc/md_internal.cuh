@@ -204,6 +204,11 @@ struct md_system {
     mdg::DevStatus *ds_host = nullptr;  // pinned mirror
     double *red_host = nullptr;         // pinned
 
+    // captured full steps (one per double-buffer parity)
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    long long graph_launches[2] = {0, 0};
+    bool graphs_ok = true;
+
     // per-launch timing (md_set_timing)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -254,6 +259,7 @@ cudaError_t launch_load_state(md_system *h, const double *pos, const double *vel
 cudaError_t launch_get_state(md_system *h, double *pos, double *vel, double *force);
 cudaError_t launch_scatter_orig(md_system *h, const double *src_sorted, double *dst_orig);
 cudaError_t launch_scatter_orig_f32(md_system *h, const float *src_sorted, double *dst_orig);
+cudaError_t launch_replica_energy(md_system *h);  // per-replica PE and KE
 cudaError_t launch_reduce_pe(md_system *h);
 cudaError_t launch_reduce_ke(md_system *h);
 cudaError_t launch_set_rebuild(md_system *h);

@@ -75,6 +75,8 @@ def lib() -> C.CDLL:
         "md_cost_model": [vp, i32, vp], "md_stats": [vp, C.c_char_p, C.c_size_t],
         "md_set_timing": [vp, i32], "md_color_cells": [vp, vp, vp],
         "md_get_cell_costs": [vp, vp, vp, vp],
+        "md_create_batch": [C.POINTER(vp), C.POINTER(md_params), i32, vp, vp, vp, vp, vp],
+        "md_energy_batch": [vp, vp, vp],
         "md_mlp_forward": [vp, i64, vp, vp, vp],
         "md_mlp_loss_grad": [vp, vp, i64, vp, vp, vp, vp],
         "md_mlp_adam": [vp, vp, vp, vp, i64, i64, C.c_float, C.c_float, C.c_float,
@@ -135,6 +137,26 @@ def md_create(params: md_params, pos: torch.Tensor, vel: torch.Tensor | None, bo
                          _ptr(pos), _ptr(vel), _stream(stream))
     _check(st, None, "md_create")
     return h.value
+
+
+def md_create_batch(params: md_params, n_each, pos: torch.Tensor, vel, boxes,
+                    stream=None) -> int:
+    R = len(n_each)
+    ne = (C.c_int64 * R)(*[int(x) for x in n_each])
+    bx = (C.c_double * (3 * R))(*[float(b) for box in boxes for b in box])
+    h = C.c_void_p()
+    st = lib().md_create_batch(C.byref(h), C.byref(params), R, C.cast(ne, C.c_void_p),
+                               C.cast(bx, C.c_void_p), _ptr(pos), _ptr(vel), _stream(stream))
+    _check(st, None, "md_create_batch")
+    return h.value
+
+
+def md_energy_batch(h, R: int):
+    ke = (C.c_double * R)()
+    pe = (C.c_double * R)()
+    _check(lib().md_energy_batch(h, C.cast(ke, C.c_void_p), C.cast(pe, C.c_void_p)), h,
+           "md_energy_batch")
+    return list(ke), list(pe)
 
 
 def md_bin_cells(h):
@@ -333,3 +355,32 @@ class System:
     def stats(self):
         import json
         return json.loads(md_stats(self.h))
+
+
+class Batch(System):
+    """Several independent replicas advanced as one system (md_create_batch).
+    replicas: list of (pos, vel, box); atoms are concatenated in that order."""
+
+    def __init__(self, replicas, params=None, stream=None, **kw):
+        self.h = None
+        if params is None:
+            params = make_params(**kw)
+        elif isinstance(params, dict):
+            params = make_params(**params)
+        self.params = params
+        self.stream = stream
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.sizes = [int(len(r[0])) for r in replicas]
+        self.offsets = [0]
+        for n in self.sizes:
+            self.offsets.append(self.offsets[-1] + n)
+        p = torch.cat([torch.as_tensor(r[0], dtype=torch.float64) for r in replicas]).to(dev)
+        v = torch.cat([torch.as_tensor(r[1], dtype=torch.float64) for r in replicas]).to(dev)
+        self.n = p.shape[0]
+        self.boxes = [[float(b) for b in r[2]] for r in replicas]
+        self.box = self.boxes[0]
+        self.h = md_create_batch(params, self.sizes, p.contiguous(), v.contiguous(), self.boxes,
+                                 stream)
+
+    def energies(self):
+        return md_energy_batch(self.h, len(self.sizes))

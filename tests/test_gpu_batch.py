@@ -1,0 +1,141 @@
+"""Batches of uneven replicas in one system (md_create_batch) and CUDA-graph
+replay of the time step, against the oracle and against separate systems."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1611_00075_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def md():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_00075_gb300 import build
+    build.build()
+    from paper_1611_00075_gb300 import md as _md
+    torch.cuda.set_device(0)
+    _md.lib()
+    return _md
+
+
+def ensemble(count=5):
+    """Uneven replicas (864 .. ~5300 atoms, rho 0.7-0.9, T 0.5-1.5), each
+    perturbed off its lattice so that forces are non-zero."""
+    reps = inputs.lj_ensemble(count=count, nmin=800, nmax=6000, seed=inputs.SEED_BASE + 55)
+    out = []
+    for r, s in enumerate(reps):
+        g = inputs.gaussian(inputs.SEED_BASE + 560 + r, s.pos.size).reshape(-1, 3)
+        out.append((np.mod(s.pos + 0.05 * g, s.box), s.vel, s.box))
+    return out
+
+
+def near_cutoff(pos, box, off, ids, rc, delta):
+    rows = np.repeat(np.arange(len(pos)), np.diff(off))
+    d = pos[ids] - pos[rows]
+    d -= box * np.round(d / box)
+    r = np.sqrt(np.sum(d * d, axis=1))
+    bad = np.zeros(len(pos), bool)
+    bad[rows[np.abs(r - rc) < delta]] = True
+    return bad
+
+
+def test_batch_cells_lists_forces_match_oracle(md, orc):
+    reps = ensemble()
+    with md.Batch(reps, precision="mixed") as b:
+        nc, cell_of, start = b.cells()
+        off, ids = b.neighbors()
+        _, _, f = b.state()
+        ke, pe = b.energies()
+    cell_of, start, off, ids, f = (t.cpu().numpy() for t in (cell_of, start, off, ids, f))
+    cell0 = 0
+    for r, (pos, vel, box) in enumerate(reps):
+        a0, a1 = b.offsets[r], b.offsets[r + 1]
+        onc, ocell, ostart, _ = orc.bin_cells(pos, box, 2.8)
+        nr = int(np.prod(onc))
+        np.testing.assert_array_equal(cell_of[a0:a1], ocell + cell0)
+        np.testing.assert_array_equal(start[cell0:cell0 + nr + 1], ostart + a0)
+        cell0 += nr
+        ooff, oids = orc.neighbors_cells(pos, box, 2.8)
+        np.testing.assert_array_equal(off[a0:a1 + 1] - off[a0], ooff)
+        np.testing.assert_array_equal(ids[off[a0]:off[a1]], oids + a0)
+        U0, f0 = orc.lj_list(pos, box, ooff, oids)
+        bad = near_cutoff(pos, np.asarray(box), ooff, oids, 2.5, 1e-5)
+        fn = np.linalg.norm(f0, axis=1)
+        rms = math.sqrt(np.mean(fn * fn))
+        err = np.linalg.norm(f[a0:a1] - f0, axis=1)
+        ok = (err <= 2e-4 * fn + 1e-5 * max(1.0, rms)) | bad
+        assert ok.all(), (r, int((~ok).sum()))
+        assert abs(pe[r] - U0) <= 2e-6 * abs(U0) + (0 if bad.sum() == 0 else 1e-3), r
+        assert abs(ke[r] - 0.5 * np.sum(vel ** 2)) <= 1e-12 * ke[r]
+    assert cell0 == nc[0] and nc[1] == nc[2] == 1
+    assert len(start) == cell0 + 1
+
+
+def test_batch_dynamics_equal_separate_systems(md):
+    reps = ensemble()
+    sep = []
+    for pos, vel, box in reps:
+        with md.System(pos, vel, box, precision="mixed") as a:
+            a.step(60)
+            sep.append((a.state()[0].cpu().numpy(), sum(a.energy())))
+    with md.Batch(reps, precision="mixed") as b:
+        b.step(60)
+        pos = b.state()[0].cpu().numpy()
+        ke, pe = b.energies()
+    for r, (_, _, box) in enumerate(reps):
+        d = pos[b.offsets[r]:b.offsets[r + 1]] - sep[r][0]
+        d -= np.asarray(box) * np.round(d / np.asarray(box))
+        # the batch rebuilds every replica's list when any replica needs it;
+        # that only changes the order of float32 chunk sums
+        assert np.max(np.abs(d)) < 1e-6, r
+        assert abs(ke[r] + pe[r] - sep[r][1]) < 1e-6 * abs(sep[r][1]), r
+
+
+def test_batch_energy_tracks_oracle(md, orc):
+    reps = ensemble(3)
+    with md.Batch(reps, precision="mixed", scheduler=md.MD_SCHED_DYNAMIC) as b:
+        b.step(40)
+        ke, pe = b.energies()
+    p = orc.make_params(potential=orc.POT_LJ, dt=0.005)
+    for r, (pos, vel, box) in enumerate(reps):
+        E = orc.md_run(p, pos, vel, box, 40)["energies"][-1, 2]
+        assert abs(ke[r] + pe[r] - E) < 1e-4 * abs(E), (r, ke[r] + pe[r], E)
+
+
+def test_batch_rejects_unsupported_modes(md):
+    reps = ensemble(2)
+    with pytest.raises(md.MDError):
+        md.Batch(reps, precision="fp64")
+    with pytest.raises(md.MDError):
+        md.Batch(reps, scheduler=md.MD_SCHED_MLP)
+    with md.Batch(reps) as b:
+        with pytest.raises(md.MDError):
+            md.md_set_variant(b.h, md.MD_FORCE_HALF_COLOR, md.MD_SCHED_GRID)
+        with pytest.raises(md.MDError):
+            md.md_cost_model(b.h, md.MD_COST_SAMPLE)
+
+
+def test_graph_replay_equals_plain_launches(md):
+    """md_step on a non-default stream replays a captured step; with per-launch
+    timing on it launches kernels one by one.  Both must agree bit for bit."""
+    s = inputs.lj_fcc(nc=8, T=1.0)
+    st = torch.cuda.Stream()
+    out = []
+    for timing in (False, True):
+        with torch.cuda.stream(st):
+            a = md.System(s.pos, s.vel, s.box, precision="mixed", stream=st)
+            md.md_set_timing(a.h, timing)
+            a.step(40)
+            a.step(25)
+            out.append(a.state())
+            stats = a.stats()
+            a.close()
+        assert stats["builds"] >= 2
+    for x, y in zip(*out):
+        assert torch.equal(x, y)
