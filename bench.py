@@ -279,6 +279,19 @@ def run_gpu(args, rank, world, local):
                                     "force_ms_per_launch": stx["ms"]["force"] / max(1, stx["count"]["force"])}
                 if code != md.MD_SCHED_GRID:
                     sched_info[name]["cta_imbalance"] = md.md_cost_model(mixed.h, md.MD_COST_PROFILE)
+            # the Newton's-third-law variants (half lists) against the full list
+            variants = {}
+            for name, code in (("half_color", md.MD_FORCE_HALF_COLOR),
+                               ("half_atomic", md.MD_FORCE_HALF_ATOMIC)):
+                md.md_set_variant(mixed.h, code, md.MD_SCHED_GRID)
+                msx, stx = timed(mixed, args.compare_steps)
+                variants[name] = {"atom_steps_per_s": n_of(mixed) * args.compare_steps / (msx * 1e-3),
+                                  "force_ms_per_launch": stx["ms"]["force"] / max(1, stx["count"]["force"]),
+                                  "rebuild_ms_per_step": stx["ms"]["rebuild"] / args.compare_steps}
+            md.md_set_variant(mixed.h, md.MD_FORCE_FULL, md.MD_SCHED_GRID)
+            variants["full"] = {"atom_steps_per_s": sched_info["grid"]["atom_steps_per_s"],
+                                "force_ms_per_launch": sched_info["grid"]["force_ms_per_launch"]}
+            sched_info["force_variants"] = variants
         if ensemble:
             pass
         elif args.scheduler == "mlp" and kw["potential"] == "lj":

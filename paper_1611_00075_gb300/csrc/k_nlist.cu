@@ -25,6 +25,26 @@ __device__ __forceinline__ bool chain_off(const DevStatus *ds, bool gated) {
     return ds->status != 0 || (gated && ds->rebuild == 0);
 }
 
+// r^2 < r_list^2 by the float64 definition, operation for operation.
+__device__ __forceinline__ bool exact_within(const double4 &ai, const double4 &aj, double shx,
+                                             double shy, double shz, double rl2) {
+    const double ddx = __dadd_rn(__dadd_rn(aj.x, -ai.x), shx);
+    const double ddy = __dadd_rn(__dadd_rn(aj.y, -ai.y), shy);
+    const double ddz = __dadd_rn(__dadd_rn(aj.z, -ai.z), shz);
+    double r2 = __dmul_rn(ddx, ddx);
+    r2 = __dadd_rn(r2, __dmul_rn(ddy, ddy));
+    r2 = __dadd_rn(r2, __dmul_rn(ddz, ddz));
+    return r2 < rl2;
+}
+
+// The same test for the rare candidates of the float32 band, kept out of line
+// so that the compiler cannot turn it into predicated code that every
+// candidate of the hot loop would issue.
+__device__ __noinline__ bool exact_within_band(const double4 *__restrict__ xabs, int i, int j,
+                                               double shx, double shy, double shz, double rl2) {
+    return exact_within(xabs[i], xabs[j], shx, shy, shz, rl2);
+}
+
 template <bool PREFILTER, bool WRITE, bool HALF>
 __global__ void __launch_bounds__(kBlock)
 build_list_kernel(int n, const Grid *__restrict__ grids, const uint16_t *__restrict__ rep,
@@ -84,17 +104,8 @@ build_list_kernel(int n, const Grid *__restrict__ grids, const uint16_t *__restr
                             if (HALF) cand = cand && (__float_as_int(qj.w) > myo);
                             if (!cand) continue;
                             bool acc = true;
-                            if (!PREFILTER || r2f >= lo) {
-                                // the float64 definition, operation for operation
-                                const double4 aj = xabs[j];
-                                double ddx = __dadd_rn(__dadd_rn(aj.x, -ai.x), shx);
-                                double ddy = __dadd_rn(__dadd_rn(aj.y, -ai.y), shy);
-                                double ddz = __dadd_rn(__dadd_rn(aj.z, -ai.z), shz);
-                                double r2 = __dmul_rn(ddx, ddx);
-                                r2 = __dadd_rn(r2, __dmul_rn(ddy, ddy));
-                                r2 = __dadd_rn(r2, __dmul_rn(ddz, ddz));
-                                acc = r2 < rl2;
-                            }
+                            if (!PREFILTER) acc = exact_within(ai, xabs[j], shx, shy, shz, rl2);
+                            else if (r2f >= lo) acc = exact_within_band(xabs, i, j, shx, shy, shz, rl2);
                             if (!acc) continue;
                             if (WRITE && cnt < cap)
                                 row[(size_t)(cnt >> 2) * 128 + (cnt & 3)] =
