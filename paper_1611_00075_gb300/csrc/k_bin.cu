@@ -83,6 +83,7 @@ __global__ void bin_count_kernel(int n, const Grid *__restrict__ grids,
                                  int32_t *__restrict__ count, int32_t *__restrict__ new_cell,
                                  int32_t *__restrict__ slot, DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
+    int maxs = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const Grid &g = grids[rep ? rep[i] : 0];
         double4 x = xabs[i];
@@ -93,8 +94,11 @@ __global__ void bin_count_kernel(int n, const Grid *__restrict__ grids,
         new_cell[i] = c;
         int s = atomicAdd(&count[c], 1);
         slot[i] = s;
-        atomicMax(&ds->max_cell, s + 1);
+        maxs = max(maxs, s + 1);
     }
+    // all lanes arrive here (grid-stride loop): one atomic per warp
+    maxs = __reduce_max_sync(0xffffffffu, (unsigned)maxs);
+    if ((threadIdx.x & 31) == 0 && maxs) atomicMax(&ds->max_cell, maxs);
 }
 
 __global__ void scatter_kernel(int n, const int32_t *__restrict__ new_cell,

@@ -32,6 +32,24 @@ struct ForceArgs {
     ForceConsts fc;
 };
 
+// Float32 cell shifts (dx, dy, dz) * w of the 27 stencil cells, in shared
+// memory, one array per component: the lanes of a warp read up to 27
+// distinct words of one array, which sit in 27 distinct banks, so each read
+// is a single wavefront (a float4 table costs several).
+struct ShiftTab {
+    float x[32], y[32], z[32];
+};
+
+__device__ __forceinline__ void load_shifts_f32(const Grid &g, ShiftTab *sh) {
+    if (threadIdx.x < kStencil) {
+        int s = threadIdx.x;
+        int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+        sh->x[s] = (float)(dx * g.w[0]);
+        sh->y[s] = (float)(dy * g.w[1]);
+        sh->z[s] = (float)(dz * g.w[2]);
+    }
+}
+
 // Fills a ForceArgs from the handle for the current double-buffer index.
 ForceArgs make_force_args(md_system *h);
 

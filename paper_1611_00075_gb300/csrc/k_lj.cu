@@ -30,24 +30,14 @@
 
 namespace mdg {
 
-// Float32 cell shifts (dx, dy, dz) * w of the 27 stencil cells, in shared memory.
-__device__ __forceinline__ void load_shifts_f32(const ForceArgs &a, float4 *sh) {
-    if (threadIdx.x < kStencil) {
-        int s = threadIdx.x;
-        int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
-        sh[s] = make_float4((float)(dx * a.g.w[0]), (float)(dy * a.g.w[1]),
-                            (float)(dz * a.g.w[2]), 0.f);
-    }
-}
-
 // The whole per-atom job of the mixed path for sorted atom i: pair loop over
 // its list, stores, and the velocity-Verlet epilogue.  MULTI (systems of
 // several boxes) reads the cell shifts of the atom's own box from a global
 // R x 27 table instead of the block's shared table.
 template <int MODE, bool ENERGY, bool MULTI = false>
-__device__ __forceinline__ void lj_mixed_atom(const ForceArgs &a, const float4 *sh, int i,
+__device__ __forceinline__ void lj_mixed_atom(const ForceArgs &a, const ShiftTab *sh, int i,
                                               int store_f) {
-    const float4 *shr = MULTI ? a.shifts32 + 27 * (int)a.rep[i] : sh;
+    const float4 *shr = MULTI ? a.shifts32 + 27 * (int)a.rep[i] : nullptr;
     const float4 qi = a.xq[i];
     const int nq = (min(a.ncount[i], a.cap) + 3) >> 2;
     const uint4 *lq = reinterpret_cast<const uint4 *>(a.nlist + list_group(i, a.cap)) + (i & 31);
@@ -57,7 +47,8 @@ __device__ __forceinline__ void lj_mixed_atom(const ForceArgs &a, const float4 *
     float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
     auto pair = [&](uint32_t ent) {
         const float4 qj = __ldg(a.xq + (ent & kIndexMask));
-        const float4 sf = MULTI ? __ldg(shr + (ent >> kIndexBits)) : sh[ent >> kIndexBits];
+        const uint32_t st = ent >> kIndexBits;
+        const float4 sf = MULTI ? __ldg(shr + st) : make_float4(sh->x[st], sh->y[st], sh->z[st], 0.f);
         const float ex = (qj.x - qi.x) + sf.x;
         const float ey = (qj.y - qi.y) + sf.y;
         const float ez = (qj.z - qi.z) + sf.z;
@@ -114,13 +105,13 @@ __device__ __forceinline__ void lj_mixed_atom(const ForceArgs &a, const float4 *
 // One thread per sorted atom; the hardware block scheduler spreads the work.
 template <int MODE, bool ENERGY, bool MULTI = false>
 __global__ void __launch_bounds__(kBlock, 5) lj_mixed_kernel(ForceArgs a, int store_f) {
-    __shared__ float4 sh[kStencil];
-    if (!MULTI) load_shifts_f32(a, sh);
+    __shared__ ShiftTab sh;
+    if (!MULTI) load_shifts_f32(a.g, &sh);
     __syncthreads();
     if (a.ds->status != 0) return;
     step_bookkeeping<MODE>(a);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.n) lj_mixed_atom<MODE, ENERGY, MULTI>(a, sh, i, store_f);
+    if (i < a.n) lj_mixed_atom<MODE, ENERGY, MULTI>(a, &sh, i, store_f);
 }
 
 // Persistent variant: gridDim.x CTAs stay resident; each warp processes tiles
@@ -128,7 +119,9 @@ __global__ void __launch_bounds__(kBlock, 5) lj_mixed_kernel(ForceArgs a, int st
 // the list layout).
 //   STATIC:  the cells are cut into rounds * G contiguous ranges of equal
 //            (predicted) cost; CTA b owns ranges b, b + G, b + 2G, ... and its
-//            warps take each range's tiles round-robin.  Each CTA gets the
+//            warps take each range's tiles round-robin.  A range starts at
+//            the first whole tile of its first cell, so no tile is split
+//            between two ranges (and no lane idles at a range boundary).  Each CTA gets the
 //            same predicted total, while at any moment all CTAs work in the
 //            same window of the sorted atoms, which keeps neighbour gathers
 //            in L2.
@@ -139,11 +132,15 @@ __global__ void __launch_bounds__(kBlock, 5) lj_mixed_kernel(ForceArgs a, int st
 // cycles go to cta_cycles -- the training data of the cost model.
 constexpr int kClaim = 8;  // tiles claimed per atomic by the dynamic queue
 
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <int MODE, bool ENERGY, bool DYNAMIC, bool TIMING, bool MULTI = false>
 __global__ void __launch_bounds__(kBlock, 5)
 lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
-    __shared__ float4 sh[kStencil];
-    if (!MULTI) load_shifts_f32(a, sh);
+    __shared__ ShiftTab sh;
+    if (!MULTI) load_shifts_f32(a.g, &sh);
     __syncthreads();
     if (a.ds->status != 0) return;
     step_bookkeeping<MODE>(a);
@@ -151,7 +148,6 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
     const int ntiles = (a.n + 31) >> 5;
     long long cta_t0 = 0;
     if (TIMING) cta_t0 = clock64();
-    int A = 0, B = a.n;
     int t = 0, tend = ntiles, tstep = nwarp;
     int claim_end = 0;
     int round = 0;
@@ -160,10 +156,8 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
         // so that at any time all CTAs work in one window of the sorted atoms
         // (neighbour gathers then hit in L2)
         const long long q = blockIdx.x;
-        A = sa.cell_start[sa.bounds[q]];
-        B = sa.cell_start[sa.bounds[q + 1]];
-        t = (A >> 5) + warp;
-        tend = (B + 31) >> 5;
+        t = ((sa.cell_start[sa.bounds[q]] + 31) >> 5) + warp;
+        tend = (sa.cell_start[sa.bounds[q + 1]] + 31) >> 5;
     }
     for (;;) {
         if (DYNAMIC) {
@@ -176,21 +170,30 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
         } else {
             while (t >= tend && ++round < sa.rounds) {
                 const long long q = (long long)round * gridDim.x + blockIdx.x;
-                A = sa.cell_start[sa.bounds[q]];
-                B = sa.cell_start[sa.bounds[q + 1]];
-                t = (A >> 5) + warp;
-                tend = (B + 31) >> 5;
+                t = ((sa.cell_start[sa.bounds[q]] + 31) >> 5) + warp;
+                tend = (sa.cell_start[sa.bounds[q + 1]] + 31) >> 5;
             }
         }
         if (t >= tend) break;
         const int i = (t << 5) + lane;
-        const bool active = (i >= A) && (i < B);
+        const bool active = i < a.n;
+        {
+            // the next tile's list head, position and count into L2 while this
+            // tile runs (a grid launch gets this overlap from its next CTAs)
+            const int tn = DYNAMIC ? t + 1 : t + tstep;
+            const int in = (tn << 5) + lane;
+            if (tn < (DYNAMIC ? claim_end : tend) && in < a.n) {
+                prefetch_l2(a.nlist + list_group(in, a.cap) + ((in & 31) << 2));
+                prefetch_l2(a.xq + in);
+                prefetch_l2(a.ncount + in);
+            }
+        }
         long long t0 = 0;
         if (TIMING) {
             __syncwarp();
             t0 = clock64();
         }
-        if (active) lj_mixed_atom<MODE, ENERGY, MULTI>(a, sh, i, store_f);
+        if (active) lj_mixed_atom<MODE, ENERGY, MULTI>(a, &sh, i, store_f);
         if (TIMING) {
             __syncwarp();
             const long long dt = clock64() - t0;

@@ -54,7 +54,7 @@ build_list_kernel(int n, const Grid *__restrict__ grids, const uint16_t *__restr
                   int32_t *__restrict__ ncount, int cap, DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
     unsigned long long tot = 0;
-    int overflow = 0;
+    int overflow = 0, maxc = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int cnt = 0;
         const Grid &g = grids[rep ? rep[i] : 0];
@@ -122,13 +122,18 @@ build_list_kernel(int n, const Grid *__restrict__ grids, const uint16_t *__restr
             for (int k = cnt; k & 3; ++k) row[(size_t)(k >> 2) * 128 + (k & 3)] = pad;
         }
         ncount[i] = cnt;
-        atomicMax(&ds->max_count, cnt);
+        maxc = max(maxc, cnt);
         tot += (unsigned long long)cnt;
         overflow |= (cnt > cap);
     }
-    // every lane of the block reaches this point (grid-stride loop, no early exit)
+    // every lane of the block reaches this point (grid-stride loop, no early
+    // exit); one atomic per warp instead of one per atom on the same address
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
-    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&ds->list_entries, tot);
+    maxc = __reduce_max_sync(0xffffffffu, (unsigned)maxc);
+    if ((threadIdx.x & 31) == 0) {
+        if (tot) atomicAdd(&ds->list_entries, tot);
+        if (maxc) atomicMax(&ds->max_count, maxc);
+    }
     if (WRITE && overflow) atomicCAS(&ds->status, 0, (int)MD_ERR_LIST_OVERFLOW);
 }
 

@@ -71,13 +71,8 @@ __device__ __forceinline__ double sc_embed_deriv_f64(double rho, double ec) {
 
 template <int ME>
 __global__ void __launch_bounds__(kBlock) sc_density_mixed(ForceArgs a) {
-    __shared__ float4 sh[kStencil];
-    if (threadIdx.x < kStencil) {
-        int s = threadIdx.x;
-        int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
-        sh[s] = make_float4((float)(dx * a.g.w[0]), (float)(dy * a.g.w[1]),
-                            (float)(dz * a.g.w[2]), 0.f);
-    }
+    __shared__ ShiftTab sh;
+    load_shifts_f32(a.g, &sh);
     __syncthreads();
     if (a.ds->status != 0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -93,10 +88,10 @@ __global__ void __launch_bounds__(kBlock) sc_density_mixed(ForceArgs a) {
         float r = 0.f;
         auto pair = [&](uint32_t ent) {
             const float4 qj = __ldg(a.xq + (ent & kIndexMask));
-            const float4 sf = sh[ent >> kIndexBits];
-            const float ex = (qj.x - qi.x) + sf.x;
-            const float ey = (qj.y - qi.y) + sf.y;
-            const float ez = (qj.z - qi.z) + sf.z;
+            const uint32_t st = ent >> kIndexBits;
+            const float ex = (qj.x - qi.x) + sh.x[st];
+            const float ey = (qj.y - qi.y) + sh.y[st];
+            const float ez = (qj.z - qi.z) + sh.z[st];
             const float r2 = ex * ex + ey * ey + ez * ez;
             if (r2 < rc2) {
                 const float s = a2 * __fdividef(1.0f, r2);
@@ -154,13 +149,8 @@ __global__ void __launch_bounds__(kBlock) sc_density_fp64(ForceArgs a) {
 
 template <int MODE, bool ENERGY, int NE, int ME>
 __global__ void __launch_bounds__(kBlock) sc_force_mixed(ForceArgs a, int store_f) {
-    __shared__ float4 sh[kStencil];
-    if (threadIdx.x < kStencil) {
-        int s = threadIdx.x;
-        int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
-        sh[s] = make_float4((float)(dx * a.g.w[0]), (float)(dy * a.g.w[1]),
-                            (float)(dz * a.g.w[2]), 0.f);
-    }
+    __shared__ ShiftTab sh;
+    load_shifts_f32(a.g, &sh);
     __syncthreads();
     if (a.ds->status != 0) return;
     step_bookkeeping<MODE>(a);
@@ -181,10 +171,10 @@ __global__ void __launch_bounds__(kBlock) sc_force_mixed(ForceArgs a, int store_
         auto pair = [&](uint32_t ent) {
             const int j = (int)(ent & kIndexMask);
             const float4 qj = __ldg(a.xq + j);
-            const float4 sf = sh[ent >> kIndexBits];
-            const float ex = (qj.x - qi.x) + sf.x;
-            const float ey = (qj.y - qi.y) + sf.y;
-            const float ez = (qj.z - qi.z) + sf.z;
+            const uint32_t st = ent >> kIndexBits;
+            const float ex = (qj.x - qi.x) + sh.x[st];
+            const float ey = (qj.y - qi.y) + sh.y[st];
+            const float ez = (qj.z - qi.z) + sh.z[st];
             const float r2 = ex * ex + ey * ey + ez * ez;
             if (r2 < rc2) {
                 const float r2i = __fdividef(1.0f, r2);

@@ -267,7 +267,7 @@ cudaError_t launch_set_rebuild(md_system *h);
 // ---- scheduler and cost model (k_sched.cu, k_mlp.cu) ----------------------
 constexpr int kMlpParams = 1217;
 // The static schedulers cut the cells into kSchedRounds ranges per CTA.
-constexpr int kSchedRounds = 8;
+constexpr int kSchedRounds = 4;
 // features of every cell; with paircount != 0 also cell_cost = list entries
 cudaError_t launch_cell_features(md_system *h, bool paircount, bool gated);
 // model inference on cell_X, quantised into cell_cost
