@@ -99,12 +99,15 @@ def make_workload(name: str, nc: int = 0):
                 "spherical voids r~U(3,15) until >=40% removed, T*=0.3, rc=2.5, skin=0.3, "
                 "dt=0.005, half-skin rebuilds")
     elif name == "fcc":
-        s = inputs.lj_fcc(nc=64, T=1.2)
-        desc = "Lennard-Jones fcc 64^3 cells = 1,048,576 atoms, rho*=0.8442, T*=1.2, rc=2.5, skin=0.3"
+        k = nc or 64
+        s = inputs.lj_fcc(nc=k, T=1.2)
+        desc = ("Lennard-Jones fcc %d^3 cells = %d atoms, rho*=0.8442, T*=1.2, rc=2.5, skin=0.3"
+                % (k, s.n))
     else:
-        s = inputs.sc_fcc(nc=128)
-        desc = ("Sutton-Chen fcc 128^3 cells = 8,388,608 atoms, a0=a=1, c=39.432, n=9, m=6, "
-                "rc=2a, skin=0.2, T*=2.088, dt=7.6e-4")
+        k = nc or 128
+        s = inputs.sc_fcc(nc=k)
+        desc = ("Sutton-Chen fcc %d^3 cells = %d atoms, a0=a=1, c=39.432, n=9, m=6, "
+                "rc=2a, skin=0.2, T*=2.088, dt=7.6e-4" % (k, s.n))
     return s, desc
 
 
