@@ -24,6 +24,7 @@ struct ForceArgs {
     const int32_t *__restrict__ ncount;
     double *__restrict__ rho;     // many-body: rho_i (Eq. 2)
     float *__restrict__ dF32;     // many-body: F'(rho_i) in float32
+    float4 *__restrict__ xqf;     // many-body, mixed: (x, y, z, F'(rho)) per atom
     double *__restrict__ dF64;    // many-body: F'(rho_i) in float64
     const uint16_t *__restrict__ rep;     // batches: replica of each sorted atom
     const float4 *__restrict__ shifts32;  // batches: R x 27 float32 cell shifts

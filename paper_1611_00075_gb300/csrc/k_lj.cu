@@ -292,6 +292,7 @@ ForceArgs make_force_args(md_system *h) {
     a.ncount = h->ncount;
     a.rho = h->rho;
     a.dF32 = h->dF32;
+    a.xqf = h->xqf;
     a.dF64 = h->dF64;
     a.rep = h->rep;
     a.shifts32 = h->shifts32;

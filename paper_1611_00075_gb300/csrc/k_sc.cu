@@ -12,7 +12,9 @@
 //
 // The second step (atom loop: F(rho_i), F'(rho_i)) only needs rho_i, so it
 // runs as the epilogue of the density pass in the thread that owns atom i;
-// sc_embed() below is that step.  The third step gathers F'_j per pair.
+// sc_embed_deriv_*() below is that step.  The third step needs F'_j per pair:
+// the mixed path's density epilogue writes (x, y, z, F'(rho)) of each atom
+// into one float4, so the force pass gathers position and F'_j in one load.
 //
 // Precision as for Lennard-Jones: MIXED computes pair terms in float32 and
 // sums rho and the forces in float64 over float32 chunks; F'(rho) feeds the
@@ -83,6 +85,8 @@ __global__ void __launch_bounds__(kBlock) sc_density_mixed(ForceArgs a) {
     const float rc2 = a.fc.rc2f, af = a.fc.sc_af, a2 = af * af;
     const int m = a.fc.sc_m;
     double R = 0.0;
+    // list quads stream through once (evict-first), one quad loaded ahead
+    uint4 nxt = nq > 0 ? __ldcs(lq) : make_uint4(0u, 0u, 0u, 0u);
     for (int q0 = 0; q0 < nq; q0 += kChunkQ) {
         const int q1 = min(q0 + kChunkQ, nq);
         float r = 0.f;
@@ -101,9 +105,9 @@ __global__ void __launch_bounds__(kBlock) sc_density_mixed(ForceArgs a) {
                 r += psi;
             }
         };
-#pragma unroll 2
         for (int q = q0; q < q1; ++q) {
-            const uint4 e4 = __ldg(lq + (size_t)q * 32);
+            const uint4 e4 = nxt;
+            if (q + 1 < nq) nxt = __ldcs(lq + (size_t)(q + 1) * 32);
             pair(e4.x);
             pair(e4.y);
             pair(e4.z);
@@ -112,7 +116,10 @@ __global__ void __launch_bounds__(kBlock) sc_density_mixed(ForceArgs a) {
         R += (double)r;
     }
     a.rho[i] = R;
-    a.dF32[i] = sc_embed_deriv_f32(R, a.fc.sc_ecf);
+    const float dF = sc_embed_deriv_f32(R, a.fc.sc_ecf);
+    a.dF32[i] = dF;
+    // the force pass gathers F'(rho_j) together with the position of j
+    a.xqf[i] = make_float4(qi.x, qi.y, qi.z, dF);
 }
 
 __global__ void __launch_bounds__(kBlock) sc_density_fp64(ForceArgs a) {
@@ -156,8 +163,8 @@ __global__ void __launch_bounds__(kBlock) sc_force_mixed(ForceArgs a, int store_
     step_bookkeeping<MODE>(a);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    const float4 qi = a.xq[i];
-    const float dFi = a.dF32[i];
+    const float4 qi = a.xqf[i];  // position, F'(rho_i)
+    const float dFi = qi.w;
     const int nq = (min(a.ncount[i], a.cap) + 3) >> 2;
     const uint4 *lq = reinterpret_cast<const uint4 *>(a.nlist + list_group(i, a.cap)) + (i & 31);
     const float rc2 = a.fc.rc2f, af = a.fc.sc_af, a2 = af * af, epsf = a.fc.sc_epsf;
@@ -165,12 +172,12 @@ __global__ void __launch_bounds__(kBlock) sc_force_mixed(ForceArgs a, int store_
     const float nf = (float)(NE > 0 ? NE : nexp), mf = (float)(ME > 0 ? ME : mexp);
     double Fx = 0.0, Fy = 0.0, Fz = 0.0, E = 0.0;
     unsigned npair = 0;
+    uint4 nxt = nq > 0 ? __ldcs(lq) : make_uint4(0u, 0u, 0u, 0u);
     for (int q0 = 0; q0 < nq; q0 += kChunkQ) {
         const int q1 = min(q0 + kChunkQ, nq);
         float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
         auto pair = [&](uint32_t ent) {
-            const int j = (int)(ent & kIndexMask);
-            const float4 qj = __ldg(a.xq + j);
+            const float4 qj = __ldg(a.xqf + (ent & kIndexMask));  // position, F'(rho_j)
             const uint32_t st = ent >> kIndexBits;
             const float ex = (qj.x - qi.x) + sh.x[st];
             const float ey = (qj.y - qi.y) + sh.y[st];
@@ -189,8 +196,7 @@ __global__ void __launch_bounds__(kBlock) sc_force_mixed(ForceArgs a, int store_
                     Phi = epsf * ((nexp & 1) ? rpow(s, nexp / 2) * ar : rpow(s, nexp / 2));
                     psi = (mexp & 1) ? rpow(s, mexp / 2) * ar : rpow(s, mexp / 2);
                 }
-                const float dFj = __ldg(a.dF32 + j);
-                const float fs = (nf * Phi + mf * (dFi + dFj) * psi) * r2i;
+                const float fs = (nf * Phi + mf * (dFi + qj.w) * psi) * r2i;
                 fx -= fs * ex;
                 fy -= fs * ey;
                 fz -= fs * ez;
@@ -200,9 +206,9 @@ __global__ void __launch_bounds__(kBlock) sc_force_mixed(ForceArgs a, int store_
                 }
             }
         };
-#pragma unroll 2
         for (int q = q0; q < q1; ++q) {
-            const uint4 e4 = __ldg(lq + (size_t)q * 32);
+            const uint4 e4 = nxt;
+            if (q + 1 < nq) nxt = __ldcs(lq + (size_t)(q + 1) * 32);
             pair(e4.x);
             pair(e4.y);
             pair(e4.z);
@@ -223,7 +229,9 @@ __global__ void __launch_bounds__(kBlock) sc_force_mixed(ForceArgs a, int store_
         a.e_atom[i] = 0.5 * E - a.fc.sc_ec * sqrt(a.rho[i]);
         count_pairs(a.ds, npair);
     }
-    if (MODE != FM_STORE) vv_epilogue<MODE>(a, i, Fx, Fy, Fz, qi.w);
+    // the float32 position's w word holds the original id
+    if (MODE != FM_STORE)
+        vv_epilogue<MODE>(a, i, Fx, Fy, Fz, reinterpret_cast<const float *>(a.xq)[4 * (size_t)i + 3]);
 }
 
 template <int MODE, bool ENERGY>

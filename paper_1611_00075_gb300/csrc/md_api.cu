@@ -87,7 +87,7 @@ void free_all(md_system *h) {
     F(h->xq_build); F(h->xabs); F(h->v); F(h->f); F(h->e_atom); F(h->orig); F(h->cell);
     F(h->cell_start); F(h->cell_count); F(h->new_cell); F(h->slot); F(h->src); F(h->key);
     F(h->scan_bsum); F(h->tmp_abs); F(h->tmp_v); F(h->tmp_orig); F(h->nlist); F(h->ncount);
-    F(h->rho); F(h->dF32); F(h->dF64); F(h->partials); F(h->red_out); F(h->ds);
+    F(h->rho); F(h->dF32); F(h->dF64); F(h->xqf); F(h->partials); F(h->red_out); F(h->ds);
     F(h->exp_tmp);
     F(h->part_bounds); F(h->cell_cost); F(h->part_scratch); F(h->cell_X); F(h->cell_pred);
     F(h->cell_cycles); F(h->cta_cycles); F(h->samp_flag); F(h->samp_bsum); F(h->samp_X);
@@ -478,6 +478,7 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
     }
     if (p->potential == MD_POT_SC) {
         A(dalloc(&h->rho, N)); A(dalloc(&h->dF32, N)); A(dalloc(&h->dF64, N));
+        if (p->precision == MD_MIXED) A(dalloc(&h->xqf, N));
     }
     h->nblocks_n = nblocks(n);
     A(dalloc(&h->partials, (size_t)h->nblocks_n + 1)); A(dalloc(&h->red_out, 4));

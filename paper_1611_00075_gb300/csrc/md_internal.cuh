@@ -172,6 +172,7 @@ struct md_system {
     // many-body
     double *rho = nullptr;
     float *dF32 = nullptr;
+    float4 *xqf = nullptr;  // Sutton-Chen mixed: position with F'(rho) in w
     double *dF64 = nullptr;
 
     // reductions
