@@ -281,42 +281,50 @@ def run_gpu(args, rank, world, local):
                 sched_info["batched_graphs"] = {
                     "atom_steps_per_s": mixed.n * args.compare_steps / (e0.elapsed_time(e1) * 1e-3),
                     "steps": args.compare_steps}
-        # the other schedulers on the same state, for comparison (short runs)
-        elif args.compare_steps > 0 and kw["potential"] == "lj":
-            for name, code in (("grid", md.MD_SCHED_GRID), ("paircount", md.MD_SCHED_PAIRCOUNT),
-                               ("dynamic", md.MD_SCHED_DYNAMIC)):
-                md.md_set_variant(mixed.h, md.MD_FORCE_FULL, code)
-                msx, stx = timed(mixed, args.compare_steps)
-                sched_info[name] = {"atom_steps_per_s": n_of(mixed) * args.compare_steps / (msx * 1e-3),
-                                    "force_ms_per_launch": stx["ms"]["force"] / max(1, stx["count"]["force"])}
-                if code != md.MD_SCHED_GRID:
-                    sched_info[name]["cta_imbalance"] = md.md_cost_model(mixed.h, md.MD_COST_PROFILE)
-            # the Newton's-third-law variants (half lists) against the full list
-            variants = {}
-            for name, code in (("half_color", md.MD_FORCE_HALF_COLOR),
-                               ("half_atomic", md.MD_FORCE_HALF_ATOMIC)):
-                md.md_set_variant(mixed.h, code, md.MD_SCHED_GRID)
-                msx, stx = timed(mixed, args.compare_steps)
-                variants[name] = {"atom_steps_per_s": n_of(mixed) * args.compare_steps / (msx * 1e-3),
-                                  "force_ms_per_launch": stx["ms"]["force"] / max(1, stx["count"]["force"]),
-                                  "rebuild_ms_per_step": stx["ms"]["rebuild"] / args.compare_steps}
-            md.md_set_variant(mixed.h, md.MD_FORCE_FULL, md.MD_SCHED_GRID)
-            variants["full"] = {"atom_steps_per_s": sched_info["grid"]["atom_steps_per_s"],
-                                "force_ms_per_launch": sched_info["grid"]["force_ms_per_launch"]}
-            sched_info["force_variants"] = variants
-        if ensemble:
-            pass
-        elif args.scheduler == "mlp" and kw["potential"] == "lj":
-            # the learned part: per-cell clock64 timings of this run -> GPU training
-            md.md_set_variant(mixed.h, md.MD_FORCE_FULL, md.MD_SCHED_DYNAMIC)
-            t0 = time.perf_counter()
-            nsamp = md.md_cost_model(mixed.h, md.MD_COST_SAMPLE)
-            loss = md.md_cost_model(mixed.h, md.MD_COST_TRAIN)
-            t1 = time.perf_counter()
-            md.md_set_variant(mixed.h, md.MD_FORCE_FULL, md.MD_SCHED_MLP)
-            sched_info["mlp_training"] = {"samples": int(nsamp), "final_mse": loss,
-                                          "sample_and_train_s": t1 - t0}
-            sched_info["mlp_cta_imbalance"] = md.md_cost_model(mixed.h, md.MD_COST_PROFILE)
+        elif kw["potential"] == "lj":
+            # the learned part first: per-cell clock64 timings of this state,
+            # then the network trained on the GPU
+            if args.scheduler == "mlp" or args.compare_steps > 0:
+                md.md_set_variant(mixed.h, md.MD_FORCE_FULL, md.MD_SCHED_DYNAMIC)
+                t0 = time.perf_counter()
+                nsamp = md.md_cost_model(mixed.h, md.MD_COST_SAMPLE)
+                loss = md.md_cost_model(mixed.h, md.MD_COST_TRAIN)
+                t1 = time.perf_counter()
+                sched_info["mlp_training"] = {"samples": int(nsamp), "final_mse": loss,
+                                              "sample_and_train_s": t1 - t0}
+            # every scheduler and force variant runs from the same saved state
+            # (a porous system warms up as its surfaces relax, so runs taken one
+            # after another would see different work)
+            s0 = mixed.state()[:2]
+
+            def from_s0(force_variant, code):
+                md.md_set_state(mixed.h, s0[0], s0[1])
+                md.md_set_variant(mixed.h, force_variant, code)
+
+            if args.compare_steps > 0:
+                for name, code in (("grid", md.MD_SCHED_GRID), ("paircount", md.MD_SCHED_PAIRCOUNT),
+                                   ("dynamic", md.MD_SCHED_DYNAMIC), ("mlp", md.MD_SCHED_MLP)):
+                    from_s0(md.MD_FORCE_FULL, code)
+                    msx, stx = timed(mixed, args.compare_steps)
+                    sched_info[name] = {
+                        "atom_steps_per_s": n_of(mixed) * args.compare_steps / (msx * 1e-3),
+                        "force_ms_per_launch": stx["ms"]["force"] / max(1, stx["count"]["force"])}
+                    if code != md.MD_SCHED_GRID:
+                        sched_info[name]["cta_imbalance"] = md.md_cost_model(mixed.h, md.MD_COST_PROFILE)
+                # the Newton's-third-law variants (half lists) against the full list
+                variants = {}
+                for name, code in (("half_color", md.MD_FORCE_HALF_COLOR),
+                                   ("half_atomic", md.MD_FORCE_HALF_ATOMIC)):
+                    from_s0(code, md.MD_SCHED_GRID)
+                    msx, stx = timed(mixed, args.compare_steps)
+                    variants[name] = {
+                        "atom_steps_per_s": n_of(mixed) * args.compare_steps / (msx * 1e-3),
+                        "force_ms_per_launch": stx["ms"]["force"] / max(1, stx["count"]["force"]),
+                        "rebuild_ms_per_step": stx["ms"]["rebuild"] / args.compare_steps}
+                variants["full"] = {"atom_steps_per_s": sched_info["grid"]["atom_steps_per_s"],
+                                    "force_ms_per_launch": sched_info["grid"]["force_ms_per_launch"]}
+                sched_info["force_variants"] = variants
+            from_s0(md.MD_FORCE_FULL, sched)
         else:
             md.md_set_variant(mixed.h, md.MD_FORCE_FULL, sched)
         builds0 = json.loads(md.md_stats(mixed.h))["builds"]

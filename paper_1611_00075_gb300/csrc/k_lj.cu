@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kBlock, 5) lj_mixed_kernel(ForceArgs a, int st
 // the list layout).
 //   STATIC:  the cells are cut into rounds * G contiguous ranges of equal
 //            (predicted) cost; CTA b owns ranges b, b + G, b + 2G, ... and its
-//            warps take each range's tiles round-robin.  A range starts at
+//            warps claim their tiles from a shared counter.  A range starts at
 //            the first whole tile of its first cell, so no tile is split
 //            between two ranges (and no lane idles at a range boundary).  Each CTA gets the
 //            same predicted total, while at any moment all CTAs work in the
@@ -139,55 +139,75 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 template <int MODE, bool ENERGY, bool DYNAMIC, bool TIMING, bool MULTI = false>
 __global__ void __launch_bounds__(kBlock, 5)
 lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
+    static_assert(kSchedRounds <= 8, "per-CTA range table holds 8 rounds");
     __shared__ ShiftTab sh;
+    __shared__ int s_first[8], s_pre[9], s_next;  // this CTA's ranges (static mode)
     if (!MULTI) load_shifts_f32(a.g, &sh);
     __syncthreads();
     if (a.ds->status != 0) return;
     step_bookkeeping<MODE>(a);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int ntiles = (a.n + 31) >> 5;
     long long cta_t0 = 0;
     if (TIMING) cta_t0 = clock64();
-    int t = 0, tend = ntiles, tstep = nwarp;
-    int claim_end = 0;
-    int round = 0;
+    int nlocal = 0;  // static mode: tiles of all this CTA's ranges
     if (!DYNAMIC) {
         // cyclic static partition: this CTA owns ranges b, b + G, b + 2G, ...
         // so that at any time all CTAs work in one window of the sorted atoms
-        // (neighbour gathers then hit in L2)
-        const long long q = blockIdx.x;
-        t = ((sa.cell_start[sa.bounds[q]] + 31) >> 5) + warp;
-        tend = (sa.cell_start[sa.bounds[q + 1]] + 31) >> 5;
-    }
-    for (;;) {
-        if (DYNAMIC) {
-            if (t >= claim_end) {
-                int claimed = 0;
-                if (lane == 0) claimed = atomicAdd(&a.ds->tile_counter, kClaim);
-                t = __shfl_sync(0xffffffffu, claimed, 0);
-                claim_end = t + kClaim;
+        // (neighbour gathers then hit in L2).  Its warps claim the ranges'
+        // tiles one at a time from a shared counter, so they finish together.
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int r = 0; r < sa.rounds; ++r) {
+                const long long q = (long long)r * gridDim.x + blockIdx.x;
+                const int tf = (sa.cell_start[sa.bounds[q]] + 31) >> 5;
+                const int te = (sa.cell_start[sa.bounds[q + 1]] + 31) >> 5;
+                s_first[r] = tf;
+                s_pre[r] = acc;
+                acc += te - tf;
             }
-        } else {
-            while (t >= tend && ++round < sa.rounds) {
-                const long long q = (long long)round * gridDim.x + blockIdx.x;
-                t = ((sa.cell_start[sa.bounds[q]] + 31) >> 5) + warp;
-                tend = (sa.cell_start[sa.bounds[q + 1]] + 31) >> 5;
-            }
+            s_pre[sa.rounds] = acc;
+            s_next = 0;
         }
-        if (t >= tend) break;
-        const int i = (t << 5) + lane;
-        const bool active = i < a.n;
-        {
-            // the next tile's list head, position and count into L2 while this
-            // tile runs (a grid launch gets this overlap from its next CTAs)
-            const int tn = DYNAMIC ? t + 1 : t + tstep;
+        __syncthreads();
+        nlocal = s_pre[sa.rounds];
+    }
+    // next tile of this warp, or -1 when none is left
+    int claim_end = 0, tdyn = 0;
+    auto claim = [&]() -> int {
+        if (DYNAMIC) {
+            if (tdyn >= claim_end) {
+                int c = 0;
+                if (lane == 0) c = atomicAdd(&a.ds->tile_counter, kClaim);
+                tdyn = __shfl_sync(0xffffffffu, c, 0);
+                claim_end = tdyn + kClaim;
+            }
+            return tdyn < ntiles ? tdyn++ : -1;
+        }
+        int k = 0;
+        if (lane == 0) k = atomicAdd(&s_next, 1);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= nlocal) return -1;
+        int r = 0;
+        while (k >= s_pre[r + 1]) ++r;
+        return s_first[r] + (k - s_pre[r]);
+    };
+    int t = claim();
+    while (t >= 0) {
+        // claim the next tile now and bring its list head, position and count
+        // into L2 while this tile runs (a grid launch gets this overlap from
+        // its next CTAs)
+        const int tn = claim();
+        if (tn >= 0) {
             const int in = (tn << 5) + lane;
-            if (tn < (DYNAMIC ? claim_end : tend) && in < a.n) {
+            if (in < a.n) {
                 prefetch_l2(a.nlist + list_group(in, a.cap) + ((in & 31) << 2));
                 prefetch_l2(a.xq + in);
                 prefetch_l2(a.ncount + in);
             }
         }
+        const int i = (t << 5) + lane;
+        const bool active = i < a.n;
         long long t0 = 0;
         if (TIMING) {
             __syncwarp();
@@ -200,7 +220,7 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
             const unsigned act = __ballot_sync(0xffffffffu, active);
             if (active) atomicAdd(&sa.cell_cycles[sa.cell[i]], (float)dt / (float)__popc(act));
         }
-        t += DYNAMIC ? 1 : tstep;
+        t = tn;
     }
     if (TIMING || DYNAMIC) __syncthreads();
     if (threadIdx.x == 0) {

@@ -146,6 +146,32 @@ def test_neighbors_bit_exact(md, orc, name, precision):
         np.testing.assert_array_equal(ids.cpu().numpy(), oids)
 
 
+@pytest.mark.parametrize("jitter", [0.0, 3e-9])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_neighbors_shell_on_list_radius(md, orc, jitter, precision):
+    """An fcc lattice whose 5th shell (24 neighbours at a0 sqrt(5/2)) lies on
+    r_list = 2.8: every atom has two dozen candidates inside the float32
+    band, where only the float64 definition decides (and whose rounding puts
+    some just inside and some just outside).  Jitter of a few 1e-9 moves
+    pairs across r_list both ways."""
+    a0 = 2.8 / math.sqrt(2.5)
+    nc = 6
+    base = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    g = np.stack(np.meshgrid(*[np.arange(nc)] * 3, indexing="ij"), -1).reshape(-1, 1, 3)
+    pos = ((g + base[None]) * a0).reshape(-1, 3)
+    box = np.full(3, nc * a0)
+    if jitter:
+        pos = np.mod(pos + jitter * inputs.gaussian(inputs.SEED_BASE + 77, pos.size).reshape(-1, 3),
+                     box)
+    with md.System(pos, np.zeros_like(pos), box, precision=precision) as sy:
+        off, ids = sy.neighbors()
+    ooff, oids = orc.neighbors_cells(pos, box, 2.8)
+    np.testing.assert_array_equal(off.cpu().numpy(), ooff)
+    np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+    counts = np.diff(ooff)
+    assert counts.min() >= 54 and counts.max() <= 78  # shells 1-4 always, shell 5 in part
+
+
 def test_neighbors_perfect_lattice_counts(md, orc):
     s = inputs.lj_fcc(nc=10, T=0.0)
     with md.System(s.pos, s.vel, s.box, precision="mixed") as sy:
