@@ -59,6 +59,10 @@ def sources_sha1() -> str:
 
 
 def parse():
+    return parse_args(None)
+
+
+def parse_args(argv):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=500)
@@ -75,7 +79,30 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nc", type=int, default=0,
                     help="fcc cells per side (0 = the workload's own size; smaller for profiling)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
+
+
+def rank_barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def rank_max(x: float, world: int, device=None) -> float:
+    """The largest value over all ranks (the slowest rank's time)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(atoms_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job atom-steps/s: every rank advances its own replica (weak
+    scaling), timed by the slowest rank."""
+    return atoms_per_rank * steps * world / (ms_max * 1e-3)
 
 
 def dist_env():
@@ -220,17 +247,10 @@ def run_gpu(args, rank, world, local):
              "mlp": md.MD_SCHED_MLP, "dynamic": md.MD_SCHED_DYNAMIC}[args.scheduler]
 
     def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        rank_barrier(world)
 
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(x, world, dev)
 
     def n_of(sysobj):
         return sysobj.n * world
@@ -346,7 +366,7 @@ def run_gpu(args, rank, world, local):
         st_e = json.loads(md.md_stats(mixed.h))
         pos, vel, force = mixed.state()
         n = mixed.n
-        value = n * args.steps * world / (ms * 1e-3)
+        value = job_throughput(n, args.steps, world, ms)
 
         # plain fp64 path, same workload
         fp64 = None
