@@ -320,6 +320,8 @@ def run_gpu(args, rank, world, local):
             def from_s0(force_variant, code):
                 md.md_set_state(mixed.h, s0[0], s0[1])
                 md.md_set_variant(mixed.h, force_variant, code)
+                md.md_forces(mixed.h)  # forces ready: timed regions hold whole steps only
+                torch.cuda.synchronize()
 
             if args.compare_steps > 0:
                 for name, code in (("grid", md.MD_SCHED_GRID), ("paircount", md.MD_SCHED_PAIRCOUNT),
