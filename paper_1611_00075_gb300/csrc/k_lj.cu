@@ -142,9 +142,13 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
     static_assert(kSchedRounds <= 8, "per-CTA range table holds 8 rounds");
     __shared__ ShiftTab sh;
     __shared__ int s_first[8], s_pre[9], s_next;  // this CTA's ranges (static mode)
+    __shared__ int s_stop;
     if (!MULTI) load_shifts_f32(a.g, &sh);
+    // one read of the status word for the whole CTA: every thread must take the
+    // same branch, since the CTA meets barriers below
+    if (threadIdx.x == 0) s_stop = a.ds->status;
     __syncthreads();
-    if (a.ds->status != 0) return;
+    if (s_stop != 0) return;
     step_bookkeeping<MODE>(a);
     const int lane = threadIdx.x & 31;
     const int ntiles = (a.n + 31) >> 5;
