@@ -1,6 +1,6 @@
 """GPU path vs the CPU oracle, element by element, through the C ABI.
 
-Bars (written here, stated in the design doc):
+Bars (the tolerances every parity test below applies):
   * cells and neighbour sets: bit-exact.
   * forces, fp64 path: |df_i| <= 1e-5 |f_i| + 1e-9 rms(f) per atom.
   * forces, mixed path: |df_i| <= 2e-4 |f_i| + 1e-5 * max(1, rms(f)) per atom
