@@ -125,12 +125,18 @@ __global__ void __launch_bounds__(kBlock, 5) lj_mixed_kernel(ForceArgs a, int st
 //            same predicted total, while at any moment all CTAs work in the
 //            same window of the sorted atoms, which keeps neighbour gathers
 //            in L2.
-//   DYNAMIC: warps claim tiles from a global counter until none are left; the
-//            last CTA to finish resets the counter for the next launch.
+//            The cells after the static ranges (the partition's last parts,
+//            about a ninth of the predicted cost) form a tail that warps
+//            claim from a global counter, two tiles at a time, once their
+//            CTA's ranges are done: whichever CTA is early absorbs the error
+//            of the prediction.
+//   DYNAMIC: warps claim tiles from a global counter until none are left.
+//   Either way the last CTA to finish resets the counter for the next launch.
 // TIMING adds clock64 per tile: the tile's cycles are shared equally by its
 // active atoms and added to their cells (cell_cycles), and each CTA's busy
 // cycles go to cta_cycles -- the training data of the cost model.
-constexpr int kClaim = 8;  // tiles claimed per atomic by the dynamic queue
+constexpr int kClaim = 8;      // tiles claimed per atomic by the dynamic queue
+constexpr int kClaimTail = 2;  // tiles claimed per atomic from the static mode's tail
 
 __device__ __forceinline__ void prefetch_l2(const void *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
@@ -154,8 +160,11 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
     const int ntiles = (a.n + 31) >> 5;
     long long cta_t0 = 0;
     if (TIMING) cta_t0 = clock64();
-    int nlocal = 0;  // static mode: tiles of all this CTA's ranges
+    int nlocal = 0;       // static mode: tiles of all this CTA's ranges
+    int tail0 = ntiles;   // static mode: first tile of the tail
     if (!DYNAMIC) {
+        const long long qt = (long long)sa.rounds * gridDim.x;
+        tail0 = (sa.cell_start[sa.bounds[qt]] + 31) >> 5;
         // cyclic static partition: this CTA owns ranges b, b + G, b + 2G, ...
         // so that at any time all CTAs work in one window of the sorted atoms
         // (neighbour gathers then hit in L2).  Its warps claim the ranges'
@@ -178,23 +187,29 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
     }
     // next tile of this warp, or -1 when none is left
     int claim_end = 0, tdyn = 0;
+    bool local_done = DYNAMIC;
     auto claim = [&]() -> int {
-        if (DYNAMIC) {
-            if (tdyn >= claim_end) {
-                int c = 0;
-                if (lane == 0) c = atomicAdd(&a.ds->tile_counter, kClaim);
-                tdyn = __shfl_sync(0xffffffffu, c, 0);
-                claim_end = tdyn + kClaim;
+        if (!local_done) {
+            int k = 0;
+            if (lane == 0) k = atomicAdd(&s_next, 1);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if (k < nlocal) {
+                int r = 0;
+                while (k >= s_pre[r + 1]) ++r;
+                return s_first[r] + (k - s_pre[r]);
             }
-            return tdyn < ntiles ? tdyn++ : -1;
+            local_done = true;
         }
-        int k = 0;
-        if (lane == 0) k = atomicAdd(&s_next, 1);
-        k = __shfl_sync(0xffffffffu, k, 0);
-        if (k >= nlocal) return -1;
-        int r = 0;
-        while (k >= s_pre[r + 1]) ++r;
-        return s_first[r] + (k - s_pre[r]);
+        // the global queue: all tiles (dynamic mode) or the tail (static mode)
+        const int base = DYNAMIC ? 0 : tail0;
+        const int step = DYNAMIC ? kClaim : kClaimTail;
+        if (tdyn >= claim_end) {
+            int c = 0;
+            if (lane == 0) c = atomicAdd(&a.ds->tile_counter, step);
+            tdyn = base + __shfl_sync(0xffffffffu, c, 0);
+            claim_end = tdyn + step;
+        }
+        return tdyn < ntiles ? tdyn++ : -1;
     };
     int t = claim();
     while (t >= 0) {
@@ -226,10 +241,10 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
         }
         t = tn;
     }
-    if (TIMING || DYNAMIC) __syncthreads();
+    __syncthreads();
     if (threadIdx.x == 0) {
         if (TIMING) sa.cta_cycles[blockIdx.x] += (float)(clock64() - cta_t0);
-        if (DYNAMIC) {
+        {
             __threadfence();
             const unsigned prev = atomicAdd(&a.ds->done_ctas, 1u);
             if (prev == gridDim.x - 1) {

@@ -79,7 +79,8 @@ struct DevStatus {
 // What the persistent force kernel needs besides ForceArgs.
 struct SchedArgs {
     const int32_t *cell_start;  // ncells + 1
-    const long long *bounds;    // partition of cells into rounds * gridDim.x ranges (+1)
+    const long long *bounds;    // partition of cells: rounds * gridDim.x static ranges,
+                                // then the tail's parts (bounds[last] = ncells)
     int rounds;                 // ranges per CTA (cyclic assignment)
     const int32_t *cell;        // sorted slot -> cell
     float *cell_cycles;         // TIMING: per-cell cycles (accumulated)
@@ -184,7 +185,7 @@ struct md_system {
 
     // persistent scheduler and learned cost model (allocated on first use)
     int sched_ctas = 0;                 // resident CTAs of the persistent force kernel
-    long long *part_bounds = nullptr;   // sched_ctas + 1 cell bounds
+    long long *part_bounds = nullptr;   // sched_parts(sched_ctas) + 1 cell bounds
     long long *cell_cost = nullptr;     // quantised per-cell cost (ncells)
     long long *part_scratch = nullptr;  // prefix sums of the partition
     float *cell_X = nullptr;            // features, ncells x 3
@@ -267,8 +268,12 @@ cudaError_t launch_set_rebuild(md_system *h);
 
 // ---- scheduler and cost model (k_sched.cu, k_mlp.cu) ----------------------
 constexpr int kMlpParams = 1217;
-// The static schedulers cut the cells into kSchedRounds ranges per CTA.
+// The static schedulers cut the cells into kSchedRounds ranges per CTA, plus
+// a tail of sched_tail_parts() further equal-cost parts (a ninth of the
+// total) that the persistent kernel hands out dynamically.
 constexpr int kSchedRounds = 4;
+inline int sched_tail_parts(int ctas) { return ctas * kSchedRounds / 8; }
+inline int sched_parts(int ctas) { return ctas * kSchedRounds + sched_tail_parts(ctas); }
 // features of every cell; with paircount != 0 also cell_cost = list entries
 cudaError_t launch_cell_features(md_system *h, bool paircount, bool gated);
 // model inference on cell_X, quantised into cell_cost
