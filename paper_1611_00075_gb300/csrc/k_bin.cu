@@ -22,34 +22,19 @@ __device__ __forceinline__ bool chain_off(const DevStatus *ds, bool gated) {
     return ds->status != 0 || (gated && ds->rebuild == 0);
 }
 
-// Periodic wrap into [0, L): x - L*floor(x/L), which for |x| < 2L is the
-// single x += L or x -= L; the second test catches x + L rounding up to L.
-__device__ __forceinline__ double wrap_coord(double x, double L) {
-    if (x < 0.0 || x >= L) x -= L * floor(x / L);
-    if (x >= L) x -= L;
-    return x;
-}
-
-// floor(x * inv_w) clamped to [0, n-1]; a NaN coordinate maps to 0 so that an
-// exploding state can never index outside the cell arrays (the drift check
-// reports it as MD_ERR_NONFINITE).
+// floor(x * inv_w) clamped to [0, n-1] (one float64 floor-convert: the
+// conversion saturates, and a NaN coordinate converts to 0, so an exploding
+// state can never index outside the cell arrays; the drift check reports it
+// as MD_ERR_NONFINITE).
 __device__ __forceinline__ int cell_coord(double x, double inv_w, int n) {
-    const double q = floor(x * inv_w);
-    if (!(q >= 0.0)) return 0;
-    if (q > (double)(n - 1)) return n - 1;
-    return (int)q;
-}
-
-// centre of the box-local cell `c` of geometry g
-__device__ __forceinline__ double3 cell_centre(int c, const Grid &g) {
-    int cx = c % g.nx;
-    int cy = (c / g.nx) % g.ny;
-    int cz = c / (g.nx * g.ny);
-    return make_double3(((double)cx + 0.5) * g.w[0], ((double)cy + 0.5) * g.w[1],
-                        ((double)cz + 0.5) * g.w[2]);
+    const int q = __double2int_rd(x * inv_w);
+    return q < 0 ? 0 : (q > n - 1 ? n - 1 : q);
 }
 
 // Absolute positions from the relative state (skipped when they are exact).
+// An atom of an interior cell whose offset is below the cell width lies
+// strictly inside the box, so only boundary cells and stray offsets need the
+// periodic wrap.
 __global__ void prepare_abs_kernel(int n, const Grid *__restrict__ grids,
                                    const uint16_t *__restrict__ rep,
                                    const double4 *__restrict__ xr,
@@ -58,15 +43,21 @@ __global__ void prepare_abs_kernel(int n, const Grid *__restrict__ grids,
     if (chain_off(ds, gated) || ds->abs_fresh) return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const Grid &g = grids[rep ? rep[i] : 0];
-        double4 r = xr[i];
-        int c = cell[i];
+        const double4 r = xr[i];
+        const int c = cell[i];
         double x = r.x, y = r.y, z = r.z;
         if (c >= 0) {
-            double3 C = cell_centre(c - g.cell0, g);
+            const int cl = c - g.cell0;
+            const int cx = cl % g.nx, cy = (cl / g.nx) % g.ny, cz = cl / (g.nx * g.ny);
+            const double3 C = cell_centre_of(cx, cy, cz, g);
             x = C.x + x; y = C.y + y; z = C.z + z;
+            if (cx == 0 || cx == g.nx - 1 || !below_cell_width(r.x, g)) x = wrap_coord(x, g.L[0]);
+            if (cy == 0 || cy == g.ny - 1 || !below_cell_width(r.y, g)) y = wrap_coord(y, g.L[1]);
+            if (cz == 0 || cz == g.nz - 1 || !below_cell_width(r.z, g)) z = wrap_coord(z, g.L[2]);
+        } else {
+            x = wrap_coord(x, g.L[0]); y = wrap_coord(y, g.L[1]); z = wrap_coord(z, g.L[2]);
         }
-        xabs[i] = make_double4(wrap_coord(x, g.L[0]), wrap_coord(y, g.L[1]),
-                               wrap_coord(z, g.L[2]), 0.0);
+        xabs[i] = make_double4(x, y, z, 0.0);
     }
 }
 
@@ -168,7 +159,8 @@ __global__ void gather_kernel(int n, const Grid *__restrict__ grids,
         int c = new_cell[s];
         const uint16_t r = trep ? trep[s] : 0;
         const Grid &g = grids[r];
-        double3 C = cell_centre(c - g.cell0, g);
+        const int cl = c - g.cell0;
+        const double3 C = cell_centre_of(cl % g.nx, (cl / g.nx) % g.ny, cl / (g.nx * g.ny), g);
         double4 a = tabs[s];
         double rx = a.x - C.x, ry = a.y - C.y, rz = a.z - C.z;
         int o = torig[s];

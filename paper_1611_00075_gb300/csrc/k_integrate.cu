@@ -13,14 +13,6 @@ namespace mdg {
 
 namespace {
 
-// Periodic wrap into [0, L): x - L*floor(x/L), which for |x| < 2L is the
-// single x += L or x -= L; the second test catches x + L rounding up to L.
-__device__ __forceinline__ double wrap_coord(double x, double L) {
-    if (x < 0.0 || x >= L) x -= L * floor(x / L);
-    if (x >= L) x -= L;
-    return x;
-}
-
 __global__ void kick_drift_kernel(int n, double hk, double dt, float half_skin2,
                                   int rebuild_every, double4 *__restrict__ xr,
                                   float4 *__restrict__ xq, const float4 *__restrict__ xq_build,
@@ -131,10 +123,11 @@ __global__ void get_state_kernel(int n, const Grid *__restrict__ grids,
             int c = cell[i];
             if (c >= 0) {
                 c -= g.cell0;
-                int cx = c % g.nx, cy = (c / g.nx) % g.ny, cz = c / (g.nx * g.ny);
-                x = ((double)cx + 0.5) * g.w[0] + x;
-                y = ((double)cy + 0.5) * g.w[1] + y;
-                z = ((double)cz + 0.5) * g.w[2] + z;
+                const double3 C =
+                    cell_centre_of(c % g.nx, (c / g.nx) % g.ny, c / (g.nx * g.ny), g);
+                x = C.x + x;
+                y = C.y + y;
+                z = C.z + z;
             }
             x = wrap_coord(x, g.L[0]);
             y = wrap_coord(y, g.L[1]);

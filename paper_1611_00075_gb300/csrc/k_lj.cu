@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(kBlock, 5) lj_mixed_kernel(ForceArgs a, int st
 //            same window of the sorted atoms, which keeps neighbour gathers
 //            in L2.
 //            The cells after the static ranges (the partition's last parts,
-//            about a ninth of the predicted cost) form a tail that warps
-//            claim from a global counter, two tiles at a time, once their
+//            a fifth of the predicted cost) form a tail that warps
+//            claim from a global counter, one tile at a time, once their
 //            CTA's ranges are done: whichever CTA is early absorbs the error
 //            of the prediction.
 //   DYNAMIC: warps claim tiles from a global counter until none are left.
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kBlock, 5) lj_mixed_kernel(ForceArgs a, int st
 // active atoms and added to their cells (cell_cycles), and each CTA's busy
 // cycles go to cta_cycles -- the training data of the cost model.
 constexpr int kClaim = 8;      // tiles claimed per atomic by the dynamic queue
-constexpr int kClaimTail = 2;  // tiles claimed per atomic from the static mode's tail
+constexpr int kClaimTail = 1;  // tiles claimed per atomic from the static mode's tail
 
 __device__ __forceinline__ void prefetch_l2(const void *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));

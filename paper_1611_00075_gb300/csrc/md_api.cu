@@ -93,7 +93,7 @@ void free_all(md_system *h) {
     F(h->cell_cycles); F(h->cta_cycles); F(h->samp_flag); F(h->samp_bsum); F(h->samp_X);
     F(h->samp_y); F(h->mlp_P); F(h->mlp_G); F(h->mlp_m); F(h->mlp_v); F(h->mlp_scratch);
     F(h->mlp_loss);
-    F(h->grids); F(h->atom_off); F(h->rep); F(h->tmp_rep); F(h->shifts32); F(h->rep_pe);
+    F(h->grids); F(h->ctab); F(h->atom_off); F(h->rep); F(h->tmp_rep); F(h->shifts32); F(h->rep_pe);
     F(h->rep_ke);
     if (h->ds_host) cudaFreeHost(h->ds_host);
     if (h->red_host) cudaFreeHost(h->red_host);
@@ -437,6 +437,13 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
         }
         g.nx = nc[0]; g.ny = nc[1]; g.nz = nc[2];
         g.ncells = nc[0] * nc[1] * nc[2];
+        {
+            // 2^e <= min(w) < 2^(e+1): its high word bounds offsets below a cell width
+            int ex = 0;
+            std::frexp(std::min(g.w[0], std::min(g.w[1], g.w[2])), &ex);
+            const int e = std::max(-1022, std::min(ex - 1, 1023));
+            g.wsmall_hi = (1023 + e) << 20;
+        }
         g.cell0 = cells_total;
         cells_total += g.ncells;
         h->grids_h.push_back(g);
@@ -470,7 +477,10 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
     A(dalloc(&h->new_cell, N)); A(dalloc(&h->slot, N)); A(dalloc(&h->src, N));
     A(dalloc(&h->key, N)); A(dalloc(&h->scan_bsum, scan_len)); A(dalloc(&h->tmp_abs, N));
     A(dalloc(&h->tmp_v, 3 * N)); A(dalloc(&h->tmp_orig, N)); A(dalloc(&h->ncount, N));
-    A(dalloc(&h->grids, (size_t)R)); A(dalloc(&h->atom_off, (size_t)R + 1));
+    size_t ctab_len = 0;
+    for (const Grid &g : h->grids_h) ctab_len += (size_t)g.nx + g.ny + g.nz;
+    A(dalloc(&h->grids, (size_t)R)); A(dalloc(&h->ctab, ctab_len));
+    A(dalloc(&h->atom_off, (size_t)R + 1));
     A(dalloc(&h->rep_pe, (size_t)R)); A(dalloc(&h->rep_ke, (size_t)R));
     if (R > 1) {
         A(dalloc(&h->rep, N)); A(dalloc(&h->tmp_rep, N));
@@ -510,6 +520,18 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
         step(cudaMemcpyAsync(h->shifts32, sh.data(), sh.size() * sizeof(float4),
                              cudaMemcpyHostToDevice, h->stream), "copy shifts");
     }
+    // cell centres (c + 0.5) w of every box, and each box's pointer into them
+    std::vector<double> ctab;
+    ctab.reserve(ctab_len);
+    for (Grid &g : h->grids_h) {
+        g.ctab = h->ctab + ctab.size();
+        const int nd[3] = {g.nx, g.ny, g.nz};
+        for (int d = 0; d < 3; ++d)
+            for (int c = 0; c < nd[d]; ++c) ctab.push_back(((double)c + 0.5) * g.w[d]);
+    }
+    h->g.ctab = h->grids_h[0].ctab;
+    step(cudaMemcpyAsync(h->ctab, ctab.data(), ctab.size() * sizeof(double),
+                         cudaMemcpyHostToDevice, h->stream), "copy cell centres");
     step(cudaMemcpyAsync(h->grids, h->grids_h.data(), R * sizeof(Grid), cudaMemcpyHostToDevice,
                          h->stream), "copy grids");
     step(cudaMemcpyAsync(h->atom_off, h->atom_off_h.data(), (R + 1) * sizeof(int64_t),

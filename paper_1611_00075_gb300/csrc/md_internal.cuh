@@ -91,13 +91,36 @@ struct SchedArgs {
 // independent boxes (replicas); their cells are numbered consecutively and
 // cell0 is the first global cell id of this box.
 struct Grid {
-    int nx, ny, nz, pad0;
+    int nx, ny, nz;
+    int wsmall_hi;      // high word of 2^e, the largest power of two <= every cell width
     int ncells;
     int cell0;
     double L[3];
     double w[3];        // cell widths L / n
     double inv_w[3];    // n / L
+    const double *ctab; // cell centres (c + 0.5) w: nx for x, then ny for y, then nz for z
 };
+
+// Periodic wrap into [0, L): x - L*floor(x/L), which for |x| < 2L is the
+// single x += L or x -= L; the second test catches x + L rounding up to L.
+__device__ __forceinline__ double wrap_coord(double x, double L) {
+    if (x < 0.0 || x >= L) x -= L * floor(x / L);
+    if (x >= L) x -= L;
+    return x;
+}
+
+// Centre of the box-local cell (cx, cy, cz), read from the box's table.  A
+// stored centre makes every kernel that forms centre + offset (or position -
+// centre) round the same single addition.
+__device__ __forceinline__ double3 cell_centre_of(int cx, int cy, int cz, const Grid &g) {
+    return make_double3(g.ctab[cx], g.ctab[g.nx + cy], g.ctab[g.nx + g.ny + cz]);
+}
+
+// |v| < 2^e <= the smallest cell width, from the exponent bits alone (false
+// for NaN and infinities).
+__device__ __forceinline__ bool below_cell_width(double v, const Grid &g) {
+    return (__double2hiint(v) & 0x7fffffff) < g.wsmall_hi;
+}
 
 // Per-launch scalars of the force kernels.
 struct ForceConsts {
@@ -133,6 +156,7 @@ struct md_system {
     std::vector<mdg::Grid> grids_h;
     std::vector<int64_t> atom_off_h;
     mdg::Grid *grids = nullptr;       // device copy of grids_h
+    double *ctab = nullptr;           // cell-centre tables of all boxes (Grid::ctab)
     int64_t *atom_off = nullptr;      // device copy of atom_off_h
     uint16_t *rep = nullptr;          // sorted slot -> replica (batches only)
     uint16_t *tmp_rep = nullptr;
@@ -269,10 +293,10 @@ cudaError_t launch_set_rebuild(md_system *h);
 // ---- scheduler and cost model (k_sched.cu, k_mlp.cu) ----------------------
 constexpr int kMlpParams = 1217;
 // The static schedulers cut the cells into kSchedRounds ranges per CTA, plus
-// a tail of sched_tail_parts() further equal-cost parts (a ninth of the
+// a tail of sched_tail_parts() further equal-cost parts (a fifth of the
 // total) that the persistent kernel hands out dynamically.
 constexpr int kSchedRounds = 4;
-inline int sched_tail_parts(int ctas) { return ctas * kSchedRounds / 8; }
+inline int sched_tail_parts(int ctas) { return ctas * kSchedRounds / 4; }
 inline int sched_parts(int ctas) { return ctas * kSchedRounds + sched_tail_parts(ctas); }
 // features of every cell; with paircount != 0 also cell_cost = list entries
 cudaError_t launch_cell_features(md_system *h, bool paircount, bool gated);
