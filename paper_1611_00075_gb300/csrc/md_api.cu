@@ -324,47 +324,137 @@ __global__ void begin_steps_kernel(DevStatus *ds, int base) { ds->steps_done = b
 // ---- CUDA graphs of one full step ---------------------------------------------
 //
 // The launches of a step that is neither the first nor the last of an md_step
-// call -- the gated rebuild chain and the fused force + kick + drift -- are
-// the same every step except for the double-buffer parity, so they are
-// captured once per parity and replayed.  Kernels that decide on the device
-// (rebuild gate, status word, step counter) keep working under replay.  Any
-// change of buffers or launch choice drops the graphs; capture needs a
-// non-default stream and is skipped while per-launch timing is on.
+// call -- the rebuild chain and the fused force + kick + drift -- are the
+// same every step except for the double-buffer parity, so they are captured
+// once per parity and replayed.  The rebuild chain sits in the body of a
+// conditional (IF) node whose condition a one-thread kernel sets from the
+// device's rebuild flag, so a step without a rebuild launches two kernels
+// instead of the whole gated chain.  Kernels that decide on the device
+// (status word, step counter) keep working under replay.  Any change of
+// buffers or launch choice drops the graphs; capture needs a non-default
+// stream.  With per-launch timing on, the rebuild chain still runs from its
+// graph (a conditional body may hold no event records) and the force launch
+// and the timing events are issued around it.
+
+__global__ void rebuild_cond_kernel(cudaGraphConditionalHandle c, DevStatus *ds) {
+    const unsigned run = (ds->status == 0 && ds->rebuild != 0) ? 1u : 0u;
+    if (run) ds->cond_runs += 1;
+    cudaGraphSetConditional(c, run);
+}
 
 void drop_graphs(md_system *h) {
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < 2; ++b) {
         if (h->gexec[b]) {
             cudaGraphExecDestroy(h->gexec[b]);
             h->gexec[b] = nullptr;
         }
+        if (h->gexec_rb[b]) {
+            cudaGraphExecDestroy(h->gexec_rb[b]);
+            h->gexec_rb[b] = nullptr;
+        }
+    }
 }
 
-md_status capture_full_step(md_system *h, int parity) {
+// Captures, for the current parity, [condition kernel] -> [IF: rebuild chain]
+// and, with with_forces, -> [fused force + kick + drift].  On any failure the
+// handle falls back to plain launches (graphs_ok = false).
+md_status capture_step_graph(md_system *h, bool with_forces, cudaGraphExec_t *out,
+                             long long *uncond_launches) {
     const long long l0 = h->launches;
+    const bool timing = h->timing;
+    h->timing = false;  // no event records inside a graph
+    md_status st = MD_OK;
     cudaGraph_t graph = nullptr;
-    MD_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    md_status st = enqueue_rebuild(h, true);
-    if (st == MD_OK) st = enqueue_forces(h, FM_FUSED_FULL, false, false);
-    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
-    if (st == MD_OK && e == cudaSuccess)
-        e = cudaGraphInstantiate(&h->gexec[parity], graph, 0);
+    cudaGraphConditionalHandle cond = 0;
+    cudaGraphNode_t knode = nullptr, inode = nullptr;
+    cudaGraphNodeParams cp = {};
+    // one stream capture into graph g after the nodes dep[0..ndep)
+    auto capture = [&](cudaGraph_t g, const cudaGraphNode_t *dep, size_t ndep,
+                       const auto &body) -> cudaError_t {
+        cudaError_t r = cudaStreamBeginCaptureToGraph(h->stream, g, dep, nullptr, ndep,
+                                                      cudaStreamCaptureModeThreadLocal);
+        if (r != cudaSuccess) return r;
+        const md_status sb = body();
+        cudaGraph_t gg = g;
+        r = cudaStreamEndCapture(h->stream, &gg);
+        if (sb != MD_OK) {
+            st = sb;
+            return cudaErrorUnknown;
+        }
+        return r;
+    };
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e == cudaSuccess)
+        e = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess)
+        e = capture(graph, nullptr, 0, [&]() -> md_status {
+            rebuild_cond_kernel<<<1, 1, 0, h->stream>>>(cond, h->ds);
+            h->launches += 1;
+            return cudaGetLastError() == cudaSuccess ? MD_OK : MD_ERR_CUDA;
+        });
+    if (e == cudaSuccess) {
+        size_t nn = 1;
+        e = cudaGraphGetNodes(graph, &knode, &nn);
+        if (e == cudaSuccess && nn != 1) e = cudaErrorUnknown;
+    }
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&inode, graph, &knode, nullptr, 1, &cp);
+    }
+    const long long lb = h->launches;
+    if (e == cudaSuccess)
+        e = capture(cp.conditional.phGraph_out[0], nullptr, 0,
+                    [&]() -> md_status { return enqueue_rebuild(h, true); });
+    h->body_launches = h->launches - lb;
+    h->launches = lb;  // the body's launches are counted when it runs
+    if (e == cudaSuccess && with_forces)
+        e = capture(graph, &inode, 1,
+                    [&]() -> md_status { return enqueue_forces(h, FM_FUSED_FULL, false, false); });
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
     if (graph) cudaGraphDestroy(graph);
-    h->graph_launches[parity] = h->launches - l0;
+    *uncond_launches = h->launches - l0;
     h->launches = l0;
-    if (st != MD_OK || e != cudaSuccess) {
+    h->timing = timing;
+    if (st != MD_OK) return st;
+    if (e != cudaSuccess) {
         cudaGetLastError();
-        h->gexec[parity] = nullptr;
+        *out = nullptr;
         h->graphs_ok = false;  // fall back to plain launches for this handle
     }
     return MD_OK;
 }
 
+bool graphs_usable(const md_system *h) { return h->graphs_ok && h->stream != nullptr; }
+
+// The gated rebuild chain of one step: from the parity's conditional graph
+// when graphs work, else as plain gated launches.
+md_status enqueue_rebuild_step(md_system *h) {
+    const int par = h->cur;
+    if (graphs_usable(h)) {
+        long long nl = 0;
+        if (!h->gexec_rb[par]) {
+            md_status st = capture_step_graph(h, false, &h->gexec_rb[par], &nl);
+            if (st != MD_OK) return st;
+        }
+        if (h->gexec_rb[par]) {
+            MD_CK(cudaGraphLaunch(h->gexec_rb[par], h->stream));
+            h->launches += 1;
+            MD_CK(mark(h, K_REBUILD));
+            return MD_OK;
+        }
+    }
+    return enqueue_rebuild(h, true);
+}
+
 // One step between the first and the last of an md_step call (parity h->cur).
 md_status enqueue_full_step(md_system *h) {
     const int par = h->cur;
-    if (h->graphs_ok && !h->timing && h->stream != nullptr) {
+    if (graphs_usable(h) && !h->timing) {
         if (!h->gexec[par]) {
-            md_status st = capture_full_step(h, par);
+            md_status st = capture_step_graph(h, true, &h->gexec[par], &h->graph_launches[par]);
             if (st != MD_OK) return st;
         }
         if (h->gexec[par]) {
@@ -373,7 +463,7 @@ md_status enqueue_full_step(md_system *h) {
             return MD_OK;
         }
     }
-    md_status st = enqueue_rebuild(h, true);
+    md_status st = enqueue_rebuild_step(h);
     if (st != MD_OK) return st;
     return enqueue_forces(h, FM_FUSED_FULL, false, false);
 }
@@ -634,7 +724,7 @@ md_status md_step(md_system *h, int64_t nsteps) {
                 if (st != MD_OK) return st;
                 continue;
             }
-            st = enqueue_rebuild(h, true);
+            st = enqueue_rebuild_step(h);
             if (st != MD_OK) return st;
             st = enqueue_forces(h, FM_FUSED_HALF, false, true);
             if (st != MD_OK) return st;
@@ -964,7 +1054,8 @@ md_status md_stats(md_system *h, char *buf_host, size_t cap) {
                   "\"integrate\": %lld, \"other\": %lld}}",
                   (long long)h->n, h->g.nx, h->g.ny, h->g.nz, h->cap, d.builds,
                   (long long)h->steps_total, d.max_count, d.max_cell, d.status, h->p.precision,
-                  h->p.force_variant, h->p.scheduler, d.list_entries, d.pairs_cut, h->launches,
+                  h->p.force_variant, h->p.scheduler, d.list_entries, d.pairs_cut,
+                  h->launches + d.cond_runs * h->body_launches,
                   h->ms_kind[0], h->ms_kind[1], h->ms_kind[2], h->ms_kind[3], h->n_kind[0],
                   h->n_kind[1], h->n_kind[2], h->n_kind[3]);
     return MD_OK;
@@ -980,6 +1071,8 @@ md_status md_set_timing(md_system *h, int32_t on) {
         h->n_kind[k] = 0;
     }
     h->launches = 0;
+    // rebuild chains run by conditional graph nodes count from here on
+    MD_CK(cudaMemsetAsync(&h->ds->cond_runs, 0, sizeof(long long), h->stream));
     return MD_OK;
 }
 

@@ -73,7 +73,7 @@ struct DevStatus {
     unsigned long long pairs_cut;     // pairs inside r_c of the last energy evaluation
     int tile_counter;                 // dynamic scheduler: next unclaimed tile
     unsigned int done_ctas;           // dynamic scheduler: CTAs finished this launch
-    long long pad1;
+    long long cond_runs;              // rebuild chains run by a graph's IF node
 };
 
 // What the persistent force kernel needs besides ForceArgs.
@@ -231,8 +231,10 @@ struct md_system {
     double *red_host = nullptr;         // pinned
 
     // captured full steps (one per double-buffer parity)
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    long long graph_launches[2] = {0, 0};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};     // one full step, per parity
+    cudaGraphExec_t gexec_rb[2] = {nullptr, nullptr};  // the rebuild chain alone, per parity
+    long long graph_launches[2] = {0, 0};  // unconditional launches of gexec
+    long long body_launches = 0;           // launches of the conditional rebuild chain
     bool graphs_ok = true;
 
     // per-launch timing (md_set_timing)

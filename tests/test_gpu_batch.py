@@ -133,20 +133,28 @@ def test_batch_rejects_unsupported_modes(md):
 
 
 def test_graph_replay_equals_plain_launches(md):
-    """md_step on a non-default stream replays a captured step; with per-launch
-    timing on it launches kernels one by one.  Both must agree bit for bit."""
+    """md_step on a non-default stream replays a captured step, whose rebuild
+    chain sits under a conditional graph node; with per-launch timing on, the
+    force kernels launch one by one around that conditional chain; on the
+    default stream every kernel launches on its own (the gated chain included).
+    All three must agree bit for bit, and the first two must count the same
+    kernel launches (the chain only when it ran)."""
     s = inputs.lj_fcc(nc=8, T=1.0)
-    st = torch.cuda.Stream()
-    out = []
-    for timing in (False, True):
+    out, launches = [], []
+    for mode in ("graphs", "timing", "default_stream"):
+        st = torch.cuda.default_stream() if mode == "default_stream" else torch.cuda.Stream()
         with torch.cuda.stream(st):
             a = md.System(s.pos, s.vel, s.box, precision="mixed", stream=st)
-            md.md_set_timing(a.h, timing)
+            md.md_set_timing(a.h, mode == "timing")
             a.step(40)
             a.step(25)
             out.append(a.state())
             stats = a.stats()
             a.close()
         assert stats["builds"] >= 2
-    for x, y in zip(*out):
-        assert torch.equal(x, y)
+        launches.append(stats["launches"])
+    for other in out[1:]:
+        for x, y in zip(out[0], other):
+            assert torch.equal(x, y)
+    assert launches[0] == launches[1]
+    assert launches[2] > launches[0]  # the gated chain's launches on steps without a rebuild
