@@ -103,15 +103,42 @@ __device__ __forceinline__ void lj_mixed_atom(const ForceArgs &a, const ShiftTab
 }
 
 // One thread per sorted atom; the hardware block scheduler spreads the work.
+// MULTI: a block's atoms are consecutive, so they belong to one or two boxes
+// (more only when a box holds fewer atoms than a block); the shift tables of
+// those boxes go to shared memory like a single box's, and a block that
+// spans more boxes reads the global R x 27 table.
 template <int MODE, bool ENERGY, bool MULTI = false>
 __global__ void __launch_bounds__(kBlock, 5) lj_mixed_kernel(ForceArgs a, int store_f) {
-    __shared__ ShiftTab sh;
-    if (!MULTI) load_shifts_f32(a.g, &sh);
+    __shared__ ShiftTab sh[MULTI ? 2 : 1];
+    __shared__ int s_r0, s_span;
+    if (!MULTI) {
+        load_shifts_f32(a.g, &sh[0]);
+    } else {
+        const int i0 = blockIdx.x * blockDim.x;
+        const int r0 = a.rep[i0], r1 = a.rep[min(a.n, i0 + (int)blockDim.x) - 1];
+        if (threadIdx.x < 2 * kStencil) {
+            const int t = threadIdx.x / kStencil, st = threadIdx.x % kStencil;
+            if (t <= r1 - r0) {
+                const float4 v = a.shifts32[kStencil * (r0 + t) + st];
+                sh[t].x[st] = v.x;
+                sh[t].y[st] = v.y;
+                sh[t].z[st] = v.z;
+            }
+        }
+        if (threadIdx.x == 0) {
+            s_r0 = r0;
+            s_span = r1 - r0;
+        }
+    }
     __syncthreads();
     if (a.ds->status != 0) return;
     step_bookkeeping<MODE>(a);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.n) lj_mixed_atom<MODE, ENERGY, MULTI>(a, &sh, i, store_f);
+    if (i >= a.n) return;
+    if (MULTI && s_span <= 1)
+        lj_mixed_atom<MODE, ENERGY, false>(a, &sh[(int)a.rep[i] - s_r0], i, store_f);
+    else
+        lj_mixed_atom<MODE, ENERGY, MULTI>(a, &sh[0], i, store_f);
 }
 
 // Persistent variant: gridDim.x CTAs stay resident; each warp processes tiles

@@ -35,6 +35,23 @@ def ensemble(count=5):
     return out
 
 
+def tiny_and_large():
+    """Ten dilute replicas of 27-125 atoms (jittered simple-cubic sites 2.9
+    apart, boxes of 3-5 spacings), so that one 256-atom block of the force
+    kernel spans several boxes, then two dense ones from the ensemble."""
+    out = []
+    for r in range(10):
+        m = 3 + r % 3
+        a = 2.9
+        g = np.arange(m) * a
+        site = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3) + 0.5 * a
+        jit = inputs.gaussian(inputs.SEED_BASE + 580 + r, site.size).reshape(-1, 3)
+        vel = 0.3 * inputs.gaussian(inputs.SEED_BASE + 600 + r, site.size).reshape(-1, 3)
+        box = (m * a,) * 3
+        out.append((np.mod(site + 0.25 * jit, box), vel, box))
+    return out + ensemble(2)
+
+
 def near_cutoff(pos, box, off, ids, rc, delta):
     rows = np.repeat(np.arange(len(pos)), np.diff(off))
     d = pos[ids] - pos[rows]
@@ -45,8 +62,13 @@ def near_cutoff(pos, box, off, ids, rc, delta):
     return bad
 
 
-def test_batch_cells_lists_forces_match_oracle(md, orc):
-    reps = ensemble()
+@pytest.mark.parametrize("which", ["uneven", "tiny_and_large"])
+def test_batch_cells_lists_forces_match_oracle(md, orc, which):
+    """Cells and lists bit-exact, forces and energies within the mixed bars,
+    per replica.  With tiny replicas a block of the force kernel spans more
+    than two boxes and reads the global shift table; otherwise the shift
+    tables of its (at most two) boxes sit in shared memory."""
+    reps = ensemble() if which == "uneven" else tiny_and_large()
     with md.Batch(reps, precision="mixed") as b:
         nc, cell_of, start = b.cells()
         off, ids = b.neighbors()
