@@ -137,8 +137,11 @@ md_status md_forces(md_system *h);
 /* Advances nsteps >= 0 velocity-Verlet steps (Sec. 3.3).  Lists are rebuilt
  * on the device when the half-skin rule (or rebuild_every) asks for it; a
  * neighbour-capacity overflow is repaired on the host (capacity grown,
- * list rebuilt) and the remaining steps continue.  Synchronizes the stream
- * once at the end to read the device status word. */
+ * list rebuilt) and the remaining steps continue.  On a non-default stream
+ * the steps replay CUDA graphs captured on first use, the rebuild chain
+ * under a conditional node set from the device's rebuild flag; on the
+ * default stream every kernel is launched on its own.  Synchronizes the
+ * stream once at the end to read the device status word. */
 md_status md_step(md_system *h, int64_t nsteps);
 
 /* Kinetic and potential energy at the current state (host outputs).  The
@@ -206,7 +209,8 @@ md_status md_cost_model(md_system *h, int32_t op, float *loss_out);
 /* Per-launch timing: with on != 0 the library records a CUDA event after
  * each rebuild chain, force evaluation and integrator launch it enqueues
  * (on the handle's stream) and md_stats reports the summed milliseconds and
- * counts per kind, plus the number of kernels enqueued.  Resets the sums.
+ * counts per kind, plus the number of kernels launched (those of a rebuild
+ * chain only when it ran).  Resets the sums and the launch count.
  * Synchronizes. */
 md_status md_set_timing(md_system *h, int32_t on);
 
