@@ -1,5 +1,6 @@
 """Throughput of the MD hot path on GB300: atom-steps/s of the mixed-precision
-path against the plain fp64 path on the porous Lennard-Jones system.
+path under the learned scheduler against the plain fp64 path under the
+pair-count partition, on the porous Lennard-Jones system.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -380,14 +381,19 @@ def run_gpu(args, rank, world, local):
         n = mixed.n
         value = job_throughput(n, args.steps, world, ms)
 
-        # plain fp64 path, same workload
+        # plain fp64 path, same workload, under the pair-count partition (the
+        # persistent schedulers serve Lennard-Jones; Sutton-Chen runs a grid)
         fp64 = None
         if args.fp64_steps > 0:
-            plain = md.System(s.pos, s.vel, s.box, precision="fp64", stream=stream, **kw)
+            sched64 = "paircount" if kw["potential"] == "lj" else "grid"
+            plain = md.System(s.pos, s.vel, s.box, precision="fp64", stream=stream,
+                              scheduler=md.MD_SCHED_PAIRCOUNT if sched64 == "paircount"
+                              else md.MD_SCHED_GRID, **kw)
             md.md_step(plain.h, min(args.warmup, 3))
             ms64, st64 = timed(plain, args.fp64_steps)
             ms64 = max_over_ranks(ms64)
             fp64 = {"value": n * args.fp64_steps * world / (ms64 * 1e-3), "steps": args.fp64_steps,
+                    "scheduler": sched64,
                     "ms_per_step": ms64 / args.fp64_steps,
                     "force_ms_per_launch": st64["ms"]["force"] / max(1, st64["count"]["force"])}
             plain.close()

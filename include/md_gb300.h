@@ -55,7 +55,11 @@ enum { MD_POT_LJ = 0, MD_POT_SC = 1 };
 enum { MD_FP64 = 0, MD_MIXED = 1 };
 /* Newton's-third-law strategy (Sec. 1 race problem, Sec. 2.2 pair loop). */
 enum { MD_FORCE_FULL = 0, MD_FORCE_HALF_COLOR = 1, MD_FORCE_HALF_ATOMIC = 2 };
-/* How force work is spread over the SMs. */
+/* How force work is spread over the SMs.  The static schedulers cut the
+ * cells into equal-cost ranges per persistent CTA and leave the last fifth
+ * of the cost as a tail that CTAs claim tile by tile when their ranges are
+ * done.  The learned model is trained on the mixed kernel's timings, so the
+ * float64 path partitions by list length under MD_SCHED_MLP too. */
 enum {
     MD_SCHED_GRID = 0,      /* one thread per atom, hardware block scheduler */
     MD_SCHED_PAIRCOUNT = 1, /* persistent CTAs, static partition by list length */
@@ -185,8 +189,8 @@ md_status md_get_atom_energy(md_system *h, double *e_dev);
  * when switching between full and half lists, the cell partition for the
  * static schedulers).  Half lists (Newton's third law, each pair once, owned
  * by the lower original id) are built for the mixed-precision Lennard-Jones
- * path; the persistent schedulers drive the mixed full-list Lennard-Jones
- * pass, and every other combination runs one thread per atom. */
+ * path; the persistent schedulers drive the full-list Lennard-Jones pass of
+ * either precision, and every other combination runs one thread per atom. */
 md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler);
 
 /* Colour of every cell of an ncell_host[0] x [1] x [2] grid (each >= 3) as

@@ -102,6 +102,62 @@ __device__ __forceinline__ void lj_mixed_atom(const ForceArgs &a, const ShiftTab
     if (MODE != FM_STORE) vv_epilogue<MODE>(a, i, Fx, Fy, Fz, qi.w);
 }
 
+// Float64 cell shifts (dx, dy, dz) * w of the 27 stencil cells.
+__device__ __forceinline__ void load_shifts_f64(const Grid &g, double3 *sh) {
+    if (threadIdx.x < kStencil) {
+        const int s = threadIdx.x;
+        const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+        sh[s] = make_double3(dx * g.w[0], dy * g.w[1], dz * g.w[2]);
+    }
+}
+
+// The whole per-atom job of the plain float64 path for sorted atom i.
+template <int MODE, bool ENERGY>
+__device__ __forceinline__ void lj_fp64_atom(const ForceArgs &a, const double3 *sh, int i,
+                                             int store_f) {
+    const double4 ri = a.xr[i];
+    const int cnt = min(a.ncount[i], a.cap);
+    const double rc2 = a.fc.rc2, sig2 = a.fc.sig2, e48 = a.fc.eps48;
+    double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0;
+    unsigned npair = 0;
+    for (int k = 0; k < cnt; ++k) {
+        const uint32_t ent = __ldg(a.nlist + list_idx(i, k, a.cap));
+        const double4 rj = a.xr[ent & kIndexMask];
+        const double3 sd = sh[ent >> kIndexBits];
+        const double ex = (rj.x - ri.x) + sd.x;
+        const double ey = (rj.y - ri.y) + sd.y;
+        const double ez = (rj.z - ri.z) + sd.z;
+        const double r2 = ex * ex + ey * ey + ez * ez;
+        if (r2 < rc2) {
+            const double r2i = 1.0 / r2;
+            double s6 = sig2 * r2i;
+            s6 = s6 * s6 * s6;
+            const double fs = e48 * r2i * s6 * (s6 - 0.5);
+            fx -= fs * ex;
+            fy -= fs * ey;
+            fz -= fs * ez;
+            if (ENERGY) {
+                e += a.fc.eps4 * s6 * (s6 - 1.0) - a.fc.shift;
+                ++npair;
+            }
+        }
+    }
+    const size_t n = (size_t)a.n;
+    if (MODE == FM_STORE || store_f) {
+        a.f[i] = fx;
+        a.f[n + i] = fy;
+        a.f[2 * n + i] = fz;
+    }
+    if (ENERGY) {
+        a.e_atom[i] = 0.5 * e;
+        count_pairs(a.ds, npair);
+    }
+    if (MODE != FM_STORE) {
+        const float4 qi = a.xq[i];
+        vv_epilogue<MODE>(a, i, fx, fy, fz, qi.w);
+    }
+}
+
 // One thread per sorted atom; the hardware block scheduler spreads the work.
 // MULTI: a block's atoms are consecutive, so they belong to one or two boxes
 // (more only when a box holds fewer atoms than a block); the shift tables of
@@ -169,14 +225,19 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-template <int MODE, bool ENERGY, bool DYNAMIC, bool TIMING, bool MULTI = false>
-__global__ void __launch_bounds__(kBlock, 5)
+// F64: the same scheduling of the plain float64 per-atom job (the baseline
+// the mixed path is measured against).
+template <int MODE, bool ENERGY, bool DYNAMIC, bool TIMING, bool MULTI = false, bool F64 = false>
+__global__ void __launch_bounds__(kBlock, F64 ? 4 : 5)
 lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
     static_assert(kSchedRounds <= 8, "per-CTA range table holds 8 rounds");
+    static_assert(!(F64 && MULTI), "batches run the mixed path");
     __shared__ ShiftTab sh;
+    __shared__ double3 sh64[F64 ? kStencil : 1];
     __shared__ int s_first[8], s_pre[9], s_next;  // this CTA's ranges (static mode)
     __shared__ int s_stop;
-    if (!MULTI) load_shifts_f32(a.g, &sh);
+    if (F64) load_shifts_f64(a.g, sh64);
+    else if (!MULTI) load_shifts_f32(a.g, &sh);
     // one read of the status word for the whole CTA: every thread must take the
     // same branch, since the CTA meets barriers below
     if (threadIdx.x == 0) s_stop = a.ds->status;
@@ -248,7 +309,8 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
             const int in = (tn << 5) + lane;
             if (in < a.n) {
                 prefetch_l2(a.nlist + list_group(in, a.cap) + ((in & 31) << 2));
-                prefetch_l2(a.xq + in);
+                if (F64) prefetch_l2(a.xr + in);
+                else prefetch_l2(a.xq + in);
                 prefetch_l2(a.ncount + in);
             }
         }
@@ -259,7 +321,10 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
             __syncwarp();
             t0 = clock64();
         }
-        if (active) lj_mixed_atom<MODE, ENERGY, MULTI>(a, &sh, i, store_f);
+        if (active) {
+            if (F64) lj_fp64_atom<MODE, ENERGY>(a, sh64, i, store_f);
+            else lj_mixed_atom<MODE, ENERGY, MULTI>(a, &sh, i, store_f);
+        }
         if (TIMING) {
             __syncwarp();
             const long long dt = clock64() - t0;
@@ -286,57 +351,12 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
 template <int MODE, bool ENERGY>
 __global__ void __launch_bounds__(kBlock) lj_fp64_kernel(ForceArgs a, int store_f) {
     __shared__ double3 sh[kStencil];
-    if (threadIdx.x < kStencil) {
-        int s = threadIdx.x;
-        int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
-        sh[s] = make_double3(dx * a.g.w[0], dy * a.g.w[1], dz * a.g.w[2]);
-    }
+    load_shifts_f64(a.g, sh);
     __syncthreads();
     if (a.ds->status != 0) return;
     step_bookkeeping<MODE>(a);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
-    const double4 ri = a.xr[i];
-    const int cnt = min(a.ncount[i], a.cap);
-    const double rc2 = a.fc.rc2, sig2 = a.fc.sig2, e48 = a.fc.eps48;
-    double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0;
-    unsigned npair = 0;
-    for (int k = 0; k < cnt; ++k) {
-        const uint32_t ent = __ldg(a.nlist + list_idx(i, k, a.cap));
-        const double4 rj = a.xr[ent & kIndexMask];
-        const double3 sd = sh[ent >> kIndexBits];
-        const double ex = (rj.x - ri.x) + sd.x;
-        const double ey = (rj.y - ri.y) + sd.y;
-        const double ez = (rj.z - ri.z) + sd.z;
-        const double r2 = ex * ex + ey * ey + ez * ez;
-        if (r2 < rc2) {
-            const double r2i = 1.0 / r2;
-            double s6 = sig2 * r2i;
-            s6 = s6 * s6 * s6;
-            const double fs = e48 * r2i * s6 * (s6 - 0.5);
-            fx -= fs * ex;
-            fy -= fs * ey;
-            fz -= fs * ez;
-            if (ENERGY) {
-                e += a.fc.eps4 * s6 * (s6 - 1.0) - a.fc.shift;
-                ++npair;
-            }
-        }
-    }
-    const size_t n = (size_t)a.n;
-    if (MODE == FM_STORE || store_f) {
-        a.f[i] = fx;
-        a.f[n + i] = fy;
-        a.f[2 * n + i] = fz;
-    }
-    if (ENERGY) {
-        a.e_atom[i] = 0.5 * e;
-        count_pairs(a.ds, npair);
-    }
-    if (MODE != FM_STORE) {
-        const float4 qi = a.xq[i];
-        vv_epilogue<MODE>(a, i, fx, fy, fz, qi.w);
-    }
+    if (i < a.n) lj_fp64_atom<MODE, ENERGY>(a, sh, i, store_f);
 }
 
 ForceArgs make_force_args(md_system *h) {
@@ -409,11 +429,14 @@ cudaError_t launch_lj(md_system *h, int mode, bool energy, bool store_f) {
 
 namespace mdg {
 
-int persist_ctas_per_sm() {
+int persist_ctas_per_sm(bool f64) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &nb, lj_mixed_persist<FM_FUSED_FULL, false, false, false>, kBlock, 0) != cudaSuccess)
-        nb = 1;
+    const cudaError_t e =
+        f64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &nb, lj_mixed_persist<FM_FUSED_FULL, false, false, false, false, true>, kBlock, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &nb, lj_mixed_persist<FM_FUSED_FULL, false, false, false>, kBlock, 0);
+    if (e != cudaSuccess) nb = 1;
     return nb > 0 ? nb : 1;
 }
 
@@ -449,10 +472,19 @@ cudaError_t launch_lj_persist(md_system *h, int mode, bool store_f, bool dynamic
         else lj_mixed_persist<FM_STORE, false, false, true><<<G, kBlock, 0, s>>>(a, 1, sa);
         return cudaGetLastError();
     }
-#define MDG_P(M)                                                                       \
-    do {                                                                               \
-        if (dynamic) lj_mixed_persist<M, false, true, false><<<G, kBlock, 0, s>>>(a, sf, sa); \
-        else lj_mixed_persist<M, false, false, false><<<G, kBlock, 0, s>>>(a, sf, sa);        \
+    const bool f64 = (h->p.precision == MD_FP64);
+#define MDG_P(M)                                                                               \
+    do {                                                                                       \
+        if (f64) {                                                                             \
+            if (dynamic)                                                                       \
+                lj_mixed_persist<M, false, true, false, false, true><<<G, kBlock, 0, s>>>(a, sf, sa);  \
+            else                                                                               \
+                lj_mixed_persist<M, false, false, false, false, true><<<G, kBlock, 0, s>>>(a, sf, sa); \
+        } else if (dynamic) {                                                                  \
+            lj_mixed_persist<M, false, true, false><<<G, kBlock, 0, s>>>(a, sf, sa);            \
+        } else {                                                                               \
+            lj_mixed_persist<M, false, false, false><<<G, kBlock, 0, s>>>(a, sf, sa);           \
+        }                                                                                      \
     } while (0)
     switch (mode) {
         case FM_STORE: MDG_P(FM_STORE); break;

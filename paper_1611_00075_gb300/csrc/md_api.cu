@@ -163,7 +163,7 @@ void harvest(md_system *h) {
 // force pass; every other combination uses the one-thread-per-atom grid.
 bool persistent_path(const md_system *h) {
     return h->p.scheduler != MD_SCHED_GRID && h->p.potential == MD_POT_LJ &&
-           h->p.precision == MD_MIXED && h->p.force_variant == MD_FORCE_FULL;
+           h->p.force_variant == MD_FORCE_FULL;
 }
 
 bool uses_partition(const md_system *h) {
@@ -178,7 +178,7 @@ md_status ensure_sched(md_system *h) {
     int dev = 0, sms = 0;
     MD_CK(cudaGetDevice(&dev));
     MD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    h->sched_ctas = sms * persist_ctas_per_sm();
+    h->sched_ctas = sms * persist_ctas_per_sm(h->p.precision == MD_FP64);
     const size_t C = (size_t)h->g.ncells;
     cudaError_t e = cudaSuccess;
     auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
@@ -213,7 +213,9 @@ md_status ensure_sched(md_system *h) {
 // CTAs; part of the rebuild chain (gated) or run right away.
 md_status enqueue_sched_prep(md_system *h, bool gated) {
     if (!uses_partition(h)) return MD_OK;
-    const bool pc = (h->p.scheduler == MD_SCHED_PAIRCOUNT);
+    // the cost model learns the mixed kernel's timings; the float64 path
+    // partitions by pair count under either static scheduler
+    const bool pc = (h->p.scheduler == MD_SCHED_PAIRCOUNT) || h->p.precision == MD_FP64;
     MD_CK(launch_cell_features(h, pc, gated));
     if (!pc) MD_CK(launch_predict_costs(h, gated));
     MD_CK(launch_partition_cells(h, gated));

@@ -277,7 +277,7 @@ cudaError_t launch_lj(md_system *h, int mode, bool energy, bool store_f);
 cudaError_t launch_lj_half(md_system *h, int mode, bool energy, int *launches);
 // persistent LJ kernel (mixed precision, full list); timing only with FM_STORE
 cudaError_t launch_lj_persist(md_system *h, int mode, bool store_f, bool dynamic, bool timing);
-int persist_ctas_per_sm();
+int persist_ctas_per_sm(bool f64);
 cudaError_t launch_sc_density(md_system *h);
 cudaError_t launch_sc_force(md_system *h, int mode, bool energy, bool store_f);
 

@@ -87,12 +87,16 @@ def porous(nc=24):
     return inputs.lj_porous(nc=nc, fraction=0.4, rmin=3.0, rmax=8.0)
 
 
-def test_schedulers_bit_identical(md):
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_schedulers_bit_identical(md, precision):
+    """Every scheduler runs the same per-atom code, so forces and states are
+    equal bit for bit whichever CTA (or tile claim) processed an atom.  The
+    float64 path partitions by list length under MD_SCHED_MLP too."""
     s = porous()
     outs = {}
     for name, sched in (("grid", md.MD_SCHED_GRID), ("pair", md.MD_SCHED_PAIRCOUNT),
                         ("dyn", md.MD_SCHED_DYNAMIC), ("mlp", md.MD_SCHED_MLP)):
-        with md.System(s.pos, s.vel, s.box, precision="mixed", scheduler=sched) as a:
+        with md.System(s.pos, s.vel, s.box, precision=precision, scheduler=sched) as a:
             f0 = a.state()[2]
             a.step(30)
             outs[name] = (f0,) + a.state()
