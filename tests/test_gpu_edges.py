@@ -1,0 +1,140 @@
+"""Edge cases of the path, through the C ABI: an empty system, one atom with
+no neighbour, inputs outside the periodic box, atoms exactly on cell faces,
+and a non-finite state reported through the device status word.
+
+Bars as in test_gpu_parity.py: cells and lists bit-exact; forces within
+1e-5 |f| + 1e-9 rms(f) (fp64) or 2e-4 |f| + 1e-5 max(1, rms(f)) (mixed)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1611_00075_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def md():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_00075_gb300 import build
+    build.build()
+    from paper_1611_00075_gb300 import md as _md
+    torch.cuda.set_device(0)
+    _md.lib()
+    return _md
+
+
+def check_forces(f, f0, precision):
+    fn = np.linalg.norm(f0, axis=1)
+    rms = math.sqrt(np.mean(fn * fn))
+    err = np.linalg.norm(f - f0, axis=1)
+    tol = 1e-5 * fn + 1e-9 * rms if precision == "fp64" else 2e-4 * fn + 1e-5 * max(1.0, rms)
+    assert np.all(err <= tol), (precision, int(np.sum(err > tol)))
+
+
+def test_empty_system_is_rejected(md):
+    with pytest.raises(md.MDError) as e:
+        md.System(np.zeros((0, 3)), np.zeros((0, 3)), [10.0, 10.0, 10.0])
+    assert e.value.status == md.MD_ERR_INVALID
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_single_atom_free_flight(md, precision):
+    """No neighbour: zero force and energy, and 400 steps of straight flight
+    that cross cells (with rebuilds) and the periodic boundary in x and y."""
+    box = np.array([9.0, 9.5, 10.0])
+    pos = np.array([[8.95, 0.02, 5.0]])
+    vel = np.array([[1.3, -0.7, 0.2]])
+    with md.System(pos, vel, box, precision=precision) as a:
+        b0 = a.stats()["builds"]
+        a.step(400)
+        p, v, f = (t.cpu().numpy() for t in a.state())
+        ke, pe = a.energy()
+        builds = a.stats()["builds"] - b0
+    assert builds >= 2
+    d = p - np.mod(pos + 400 * 0.005 * vel, box)
+    d -= box * np.round(d / box)
+    assert np.max(np.abs(d)) < 1e-12
+    assert np.all(f == 0.0) and pe == 0.0
+    np.testing.assert_array_equal(v, vel)
+    assert ke == pytest.approx(0.5 * np.sum(vel ** 2), rel=1e-15)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_positions_outside_the_box_are_wrapped(md, orc, precision):
+    """Inputs shifted by -2..2 box lengths per component: the system holds the
+    wrapped positions, and cells, lists and forces are those of the oracle on
+    them."""
+    s = inputs.lj_fcc(nc=6, T=0.72)
+    L = np.asarray(s.box)
+    g = inputs.gaussian(inputs.SEED_BASE + 701, s.pos.size).reshape(-1, 3)
+    pos0 = np.mod(s.pos + 0.05 * g, L)
+    k = (inputs.splitmix64(inputs.SEED_BASE + 702, s.pos.size) % 5).astype(np.int64) - 2
+    shifted = pos0 + k.reshape(-1, 3) * L
+    with md.System(shifted, s.vel, s.box, precision=precision) as a:
+        p, _, f = (t.cpu().numpy() for t in a.state())
+        nc, cell_of, start = a.cells()
+        off, ids = a.neighbors()
+    assert np.all((p >= 0.0) & (p < L))
+    d = p - pos0
+    d -= L * np.round(d / L)
+    assert np.max(np.abs(d)) < 1e-12
+    onc, ocell, ostart, _ = orc.bin_cells(p, L, 2.8)
+    assert list(onc) == nc
+    np.testing.assert_array_equal(cell_of.cpu().numpy(), ocell)
+    np.testing.assert_array_equal(start.cpu().numpy(), ostart)
+    ooff, oids = orc.neighbors_cells(p, L, 2.8)
+    np.testing.assert_array_equal(off.cpu().numpy(), ooff)
+    np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+    prm = orc.make_params(potential=orc.POT_LJ, rc=2.5, skin=0.3, dt=0.005)
+    _, f0 = orc.forces_once(prm, p, L)
+    check_forces(f, f0, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_atoms_on_cell_faces(md, orc, precision):
+    """Simple-cubic sites at whole multiples of the cell width (2.9 > r_list),
+    the body centres, and sites 1.07 from the corners along x: every
+    coordinate of the first set, and y and z of the third, lie on a cell face,
+    where the floor of x * n / L decides the cell.  Cells, lists and forces
+    match the oracle's definition."""
+    n, w = 4, 2.9
+    g = np.arange(n) * w
+    corners = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    pos = np.concatenate([corners, corners + 0.5 * w, corners + np.array([0.37 * w, 0.0, 0.0])])
+    box = np.full(3, n * w)
+    vel = np.zeros_like(pos)
+    with md.System(pos, vel, box, precision=precision) as a:
+        nc, cell_of, start = a.cells()
+        off, ids = a.neighbors()
+        _, _, f = (t.cpu().numpy() for t in a.state())
+    onc, ocell, ostart, _ = orc.bin_cells(pos, box, 2.8)
+    assert list(onc) == nc == [n, n, n]
+    np.testing.assert_array_equal(cell_of.cpu().numpy(), ocell)
+    np.testing.assert_array_equal(start.cpu().numpy(), ostart)
+    ooff, oids = orc.neighbors_cells(pos, box, 2.8)
+    np.testing.assert_array_equal(off.cpu().numpy(), ooff)
+    np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+    prm = orc.make_params(potential=orc.POT_LJ, rc=2.5, skin=0.3, dt=0.005)
+    _, f0 = orc.forces_once(prm, pos, box)
+    check_forces(f, f0, precision)
+
+
+def test_non_finite_state_is_reported(md):
+    """A NaN coordinate gets cell index 0 in that dimension (the float64
+    floor-convert of NaN is clamped into the grid), the atom meets no
+    neighbour (every comparison with NaN is false), and the first drift
+    reports MD_ERR_NONFINITE through the status word; the handle stays usable
+    for inspection."""
+    s = inputs.lj_fcc(nc=6, T=0.72)
+    pos = s.pos.copy()
+    pos[17, 1] = np.nan
+    with md.System(pos, s.vel, s.box, precision="mixed") as a:
+        with pytest.raises(md.MDError) as e:
+            a.step(3)
+        assert e.value.status == md.MD_ERR_NONFINITE
+        assert a.stats()["status"] == md.MD_ERR_NONFINITE
