@@ -97,7 +97,8 @@ typedef struct {
 /* Creates a system of n >= 1 atoms in the orthorhombic periodic box
  * box3_host[3] (each side must hold at least 3 list radii, so that the 27
  * cells around any cell are distinct).  pos_dev / vel_dev: n x 3 float64
- * device arrays, positions inside [0, L); both are copied.  cuda_stream: a
+ * device arrays; both are copied, and positions are wrapped into [0, L) on
+ * the way in (any finite value is accepted).  cuda_stream: a
  * cudaStream_t (NULL = legacy default stream).  Bins atoms (Sec. 2.1),
  * builds the first list with capacity from a counting pass, and evaluates
  * forces.  Energy is L/J units of the potential. */
@@ -157,8 +158,9 @@ md_status md_energy(md_system *h, double *ke_host, double *pe_host);
  * of the last force evaluation. */
 md_status md_get_state(md_system *h, double *pos_dev, double *vel_dev, double *force_dev);
 
-/* Replaces positions and velocities (original order, device arrays); the
- * next force evaluation rebinds and rebuilds the list. */
+/* Replaces positions and velocities (original order, device arrays;
+ * positions wrapped into [0, L) on the way in); the next force evaluation
+ * rebinds and rebuilds the list. */
 md_status md_set_state(md_system *h, const double *pos_dev, const double *vel_dev);
 
 /* Exports the current list as CSR in original order: offsets_dev[n + 1]

@@ -51,8 +51,10 @@ __global__ void kick_drift_kernel(int n, double hk, double dt, float half_skin2,
     if (rebuild_every <= 0 && d2 > half_skin2) ds->rebuild = 1;
 }
 
-// Original-order input: position i becomes slot i with absolute coordinates.
-__global__ void load_state_kernel(int n, const double *__restrict__ pos,
+// Original-order input: position i becomes slot i with absolute coordinates,
+// wrapped into its box [0, L).
+__global__ void load_state_kernel(int n, const Grid *__restrict__ grids,
+                                  const double *__restrict__ pos,
                                   const double *__restrict__ vel, double4 *__restrict__ xr,
                                   float4 *__restrict__ xq, double4 *__restrict__ xabs,
                                   double *__restrict__ v, int32_t *__restrict__ orig,
@@ -66,13 +68,7 @@ __global__ void load_state_kernel(int n, const double *__restrict__ pos,
     if (i >= n) return;
     const size_t N = (size_t)n;
     if (pos) {
-        double4 a = make_double4(pos[3 * (size_t)i], pos[3 * (size_t)i + 1],
-                                 pos[3 * (size_t)i + 2], 0.0);
-        xr[i] = a;
-        xabs[i] = a;
-        xq[i] = make_float4((float)a.x, (float)a.y, (float)a.z, __int_as_float(i));
-        orig[i] = i;
-        cell[i] = -1;
+        int r = 0;
         if (rep) {
             // replica of input row i: the last r with atom_off[r] <= i
             int lo = 0, hi = R - 1;
@@ -82,7 +78,17 @@ __global__ void load_state_kernel(int n, const double *__restrict__ pos,
                 else hi = mid - 1;
             }
             rep[i] = (uint16_t)lo;
+            r = lo;
         }
+        const Grid &g = grids[r];
+        const double4 a = make_double4(wrap_coord(pos[3 * (size_t)i], g.L[0]),
+                                       wrap_coord(pos[3 * (size_t)i + 1], g.L[1]),
+                                       wrap_coord(pos[3 * (size_t)i + 2], g.L[2]), 0.0);
+        xr[i] = a;
+        xabs[i] = a;
+        xq[i] = make_float4((float)a.x, (float)a.y, (float)a.z, __int_as_float(i));
+        orig[i] = i;
+        cell[i] = -1;
     }
     if (vel) {
         v[i] = vel[3 * (size_t)i];
@@ -244,7 +250,7 @@ cudaError_t launch_load_state(md_system *h, const double *pos, const double *vel
     int n = (int)h->n;
     if (pos) {
         load_state_kernel<<<nblocks(n), kBlock, 0, h->stream>>>(
-            n, pos, vel, h->xr64[h->cur], h->xq[h->cur], h->xabs, h->v, h->orig, h->cell,
+            n, h->grids, pos, vel, h->xr64[h->cur], h->xq[h->cur], h->xabs, h->v, h->orig, h->cell,
             h->atom_off, h->R, h->rep, h->ds);
     } else if (vel) {
         load_vel_kernel<<<nblocks(n), kBlock, 0, h->stream>>>(n, vel, h->orig, h->v);
