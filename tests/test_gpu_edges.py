@@ -138,3 +138,51 @@ def test_non_finite_state_is_reported(md):
             a.step(3)
         assert e.value.status == md.MD_ERR_NONFINITE
         assert a.stats()["status"] == md.MD_ERR_NONFINITE
+
+
+def orthorhombic():
+    """A 6 x 8 x 11 fcc block at rho* = 0.8442, perturbed: 3 x 4 x 6 cells
+    whose widths differ between x, y (3.36) and z (3.08)."""
+    a0 = (4.0 / 0.8442) ** (1.0 / 3.0)
+    nc = (6, 8, 11)
+    box = a0 * np.array(nc, dtype=np.float64)
+    g = inputs.gaussian(inputs.SEED_BASE + 710, 3 * 4 * int(np.prod(nc))).reshape(-1, 3)
+    pos = np.mod(inputs.fcc_lattice(nc, a0) + 0.05 * g, box)
+    vel = inputs.maxwell_boltzmann(len(pos), 0.72, 1.0, inputs.SEED_BASE + 711)
+    return pos, vel, box
+
+
+@pytest.mark.parametrize("variant", ["full", "color", "atomic"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_orthorhombic_box(md, orc, precision, variant):
+    """Different cell counts and widths per dimension: cells and lists
+    bit-exact, forces within the bars, and 60 steps with rebuilds against the
+    oracle's total energy (1e-6 relative on the fp64 path, 1e-4 mixed).  The
+    half-list variants (mixed path only) colour a 3 x 4 x 6 grid."""
+    if variant != "full" and precision == "fp64":
+        pytest.skip("half lists are built for the mixed path")
+    pos, vel, box = orthorhombic()
+    code = {"full": md.MD_FORCE_FULL, "color": md.MD_FORCE_HALF_COLOR,
+            "atomic": md.MD_FORCE_HALF_ATOMIC}[variant]
+    with md.System(pos, vel, box, precision=precision, force_variant=code) as a:
+        nc, cell_of, start = a.cells()
+        off, ids = a.neighbors(half=variant != "full")
+        f = a.state()[2].cpu().numpy()
+        b0 = a.stats()["builds"]
+        a.step(60)
+        builds = a.stats()["builds"] - b0
+        ke, pe = a.energy()
+    onc, ocell, ostart, _ = orc.bin_cells(pos, box, 2.8)
+    assert list(onc) == nc == [3, 4, 6]
+    np.testing.assert_array_equal(cell_of.cpu().numpy(), ocell)
+    np.testing.assert_array_equal(start.cpu().numpy(), ostart)
+    ooff, oids = orc.neighbors_cells(pos, box, 2.8, half=variant != "full")
+    np.testing.assert_array_equal(off.cpu().numpy(), ooff)
+    np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+    prm = orc.make_params(potential=orc.POT_LJ, rc=2.5, skin=0.3, dt=0.005)
+    _, f0 = orc.forces_once(prm, pos, box)
+    check_forces(f, f0, precision)
+    assert builds >= 1
+    E = orc.md_run(prm, pos, vel, box, 60)["energies"][-1, 2]
+    tol = 1e-6 if precision == "fp64" else 1e-4
+    assert abs(ke + pe - E) <= tol * abs(E), (ke + pe, E)
