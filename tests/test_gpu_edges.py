@@ -267,3 +267,31 @@ def test_batch_of_orthorhombic_and_shifted_boxes(md, orc):
         np.testing.assert_array_equal(ids[off[a0]:off[a1]], oids + a0)
         _, f0 = orc.forces_once(prm, pr, box_r)
         check_forces(f[a0:a1], f0, "mixed")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_non_unit_parameters_and_fixed_rebuild_interval(md, orc, precision):
+    """eps 1.7, sigma 0.9, mass 2.5 and a list rebuilt every 7 steps (the
+    paper's fixed interval) instead of the half-skin rule: forces at the
+    start and the total energy after 50 steps against the oracle."""
+    eps, sig, mass = 1.7, 0.9, 2.5
+    s = inputs.lj_fcc(nc=6, T=0.72)
+    box = np.asarray(s.box) * sig
+    g = inputs.gaussian(inputs.SEED_BASE + 740, s.pos.size).reshape(-1, 3)
+    pos = np.mod(s.pos * sig + 0.04 * g, box)
+    vel = inputs.maxwell_boltzmann(len(pos), 0.72 * eps, mass, inputs.SEED_BASE + 741)
+    kw = dict(eps=eps, sigma=sig, rc=2.5 * sig, skin=0.3 * sig, dt=0.004, mass=mass,
+              rebuild_every=7)
+    with md.System(pos, vel, box, precision=precision, **kw) as a:
+        f = a.state()[2].cpu().numpy()
+        b0 = a.stats()["builds"]
+        a.step(50)
+        builds = a.stats()["builds"] - b0
+        ke, pe = a.energy()
+    prm = orc.make_params(potential=orc.POT_LJ, **kw)
+    _, f0 = orc.forces_once(prm, pos, box)
+    check_forces(f, f0, precision)
+    assert builds == 50 // 7
+    E = orc.md_run(prm, pos, vel, box, 50)["energies"][-1, 2]
+    tol = 1e-6 if precision == "fp64" else 1e-4
+    assert abs(ke + pe - E) <= tol * abs(E), (ke + pe, E)
