@@ -163,8 +163,15 @@ __device__ __forceinline__ void lj_fp64_atom(const ForceArgs &a, const double3 *
 // (more only when a box holds fewer atoms than a block); the shift tables of
 // those boxes go to shared memory like a single box's, and a block that
 // spans more boxes reads the global R x 27 table.
+// Block shape of the grid kernel, measured on GB300: 128 threads for one
+// box and 256 for batches, each at up to 56 registers (4-9 % faster than
+// 256 threads at 48 registers).
+template <bool MULTI>
+constexpr int grid_block() { return MULTI ? 256 : 128; }
+
 template <int MODE, bool ENERGY, bool MULTI = false>
-__global__ void __launch_bounds__(kBlock, 5) lj_mixed_kernel(ForceArgs a, int store_f) {
+__global__ void __launch_bounds__(grid_block<MULTI>(), MULTI ? 4 : 5)
+lj_mixed_kernel(ForceArgs a, int store_f) {
     __shared__ ShiftTab sh[MULTI ? 2 : 1];
     __shared__ int s_r0, s_span;
     if (!MULTI) {
@@ -396,24 +403,30 @@ cudaError_t launch_lj(md_system *h, int mode, bool energy, bool store_f) {
 #define MDG_LJ(K, M, E) K<M, E><<<nb, kBlock, 0, s>>>(a, sf)
     if (h->R > 1) {
         // several boxes: mixed precision only (checked at creation)
+        constexpr int tb = grid_block<true>();
+        const int nbm = nblocks(a.n, tb);
         switch (mode) {
             case FM_STORE:
-                if (energy) lj_mixed_kernel<FM_STORE, true, true><<<nb, kBlock, 0, s>>>(a, sf);
-                else lj_mixed_kernel<FM_STORE, false, true><<<nb, kBlock, 0, s>>>(a, sf);
+                if (energy) lj_mixed_kernel<FM_STORE, true, true><<<nbm, tb, 0, s>>>(a, sf);
+                else lj_mixed_kernel<FM_STORE, false, true><<<nbm, tb, 0, s>>>(a, sf);
                 break;
             case FM_FUSED_FULL:
-                lj_mixed_kernel<FM_FUSED_FULL, false, true><<<nb, kBlock, 0, s>>>(a, sf);
+                lj_mixed_kernel<FM_FUSED_FULL, false, true><<<nbm, tb, 0, s>>>(a, sf);
                 break;
             default:
-                lj_mixed_kernel<FM_FUSED_HALF, false, true><<<nb, kBlock, 0, s>>>(a, sf);
+                lj_mixed_kernel<FM_FUSED_HALF, false, true><<<nbm, tb, 0, s>>>(a, sf);
                 break;
         }
     } else if (h->p.precision == MD_MIXED) {
+        constexpr int tb = grid_block<false>();
+        const int nbs = nblocks(a.n, tb);
+#define MDG_LJM(M, E) lj_mixed_kernel<M, E><<<nbs, tb, 0, s>>>(a, sf)
         switch (mode) {
-            case FM_STORE: if (energy) MDG_LJ(lj_mixed_kernel, FM_STORE, true); else MDG_LJ(lj_mixed_kernel, FM_STORE, false); break;
-            case FM_FUSED_FULL: if (energy) MDG_LJ(lj_mixed_kernel, FM_FUSED_FULL, true); else MDG_LJ(lj_mixed_kernel, FM_FUSED_FULL, false); break;
-            default: if (energy) MDG_LJ(lj_mixed_kernel, FM_FUSED_HALF, true); else MDG_LJ(lj_mixed_kernel, FM_FUSED_HALF, false); break;
+            case FM_STORE: if (energy) MDG_LJM(FM_STORE, true); else MDG_LJM(FM_STORE, false); break;
+            case FM_FUSED_FULL: if (energy) MDG_LJM(FM_FUSED_FULL, true); else MDG_LJM(FM_FUSED_FULL, false); break;
+            default: if (energy) MDG_LJM(FM_FUSED_HALF, true); else MDG_LJM(FM_FUSED_HALF, false); break;
         }
+#undef MDG_LJM
     } else {
         switch (mode) {
             case FM_STORE: if (energy) MDG_LJ(lj_fp64_kernel, FM_STORE, true); else MDG_LJ(lj_fp64_kernel, FM_STORE, false); break;
