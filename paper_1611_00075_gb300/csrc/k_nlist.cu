@@ -172,8 +172,11 @@ __device__ __noinline__ int list_atom_band(int i, const Grid &g, float lo, float
                                            unused);
 }
 
+// 128-thread blocks measured 1 % faster than 256 for this kernel.
+constexpr int kListBlock = 128;
+
 template <bool PREFILTER, bool WRITE, bool HALF>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kListBlock)
 build_list_kernel(int n, const Grid *__restrict__ grids, const uint16_t *__restrict__ rep,
                   float lo, float hi, double rl2, const float4 *__restrict__ xq,
                   const double4 *__restrict__ xabs, const int32_t *__restrict__ cell,
@@ -307,7 +310,7 @@ cudaError_t launch_build_list(md_system *h, bool write, bool gated) {
     const bool half = (h->p.force_variant != MD_FORCE_FULL);
     reset_max_count_kernel<<<1, 1, 0, s>>>(h->ds, gated);
 #define MDG_LIST(PF, WR, HF)                                                                    \
-    build_list_kernel<PF, WR, HF><<<gs_blocks(n), kBlock, 0, s>>>(                                \
+    build_list_kernel<PF, WR, HF><<<gs_blocks(n) * (kBlock / kListBlock), kListBlock, 0, s>>>(                                \
         n, h->grids, h->rep, h->list_lo, h->list_hi, h->rl2, h->xq[cur], h->xabs, h->cell,   \
         h->cell_start,                                                                         \
         h->nlist, h->ncount, h->cap, h->ds, gated)
