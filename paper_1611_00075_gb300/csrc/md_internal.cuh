@@ -297,7 +297,7 @@ constexpr int kMlpParams = 1217;
 // The static schedulers cut the cells into kSchedRounds ranges per CTA, plus
 // a tail of sched_tail_parts() further equal-cost parts (a fifth of the
 // total) that the persistent kernel hands out dynamically.
-constexpr int kSchedRounds = 4;
+constexpr int kSchedRounds = 8;
 inline int sched_tail_parts(int ctas) { return ctas * kSchedRounds / 4; }
 inline int sched_parts(int ctas) { return ctas * kSchedRounds + sched_tail_parts(ctas); }
 // features of every cell; with paircount != 0 also cell_cost = list entries
