@@ -466,7 +466,7 @@ cudaError_t launch_lj_persist(md_system *h, int mode, bool store_f, bool dynamic
     sa.cell = h->cell;
     sa.cell_cycles = h->cell_cycles;
     sa.cta_cycles = h->cta_cycles;
-    sa.rounds = kSchedRounds;
+    sa.rounds = h->sched_rounds;
     const int G = h->sched_ctas;
     const int sf = store_f ? 1 : 0;
     cudaStream_t s = h->stream;

@@ -182,7 +182,8 @@ md_status ensure_sched(md_system *h) {
     const size_t C = (size_t)h->g.ncells;
     cudaError_t e = cudaSuccess;
     auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-    A(dalloc(&h->part_bounds, (size_t)sched_parts(h->sched_ctas) + 1));
+    h->sched_rounds = sched_rounds(h->n, h->sched_ctas);
+    A(dalloc(&h->part_bounds, (size_t)sched_parts(h->sched_ctas, h->sched_rounds) + 1));
     A(dalloc(&h->cell_cost, C));
     A(dalloc(&h->part_scratch, C + 1 + C / (kBlock * 8) + 8));
     A(dalloc(&h->cell_X, 3 * C));

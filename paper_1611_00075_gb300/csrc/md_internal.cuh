@@ -209,7 +209,8 @@ struct md_system {
 
     // persistent scheduler and learned cost model (allocated on first use)
     int sched_ctas = 0;                 // resident CTAs of the persistent force kernel
-    long long *part_bounds = nullptr;   // sched_parts(sched_ctas) + 1 cell bounds
+    int sched_rounds = 1;               // static ranges per CTA (sched_rounds())
+    long long *part_bounds = nullptr;   // sched_parts(sched_ctas, sched_rounds) + 1 cell bounds
     long long *cell_cost = nullptr;     // quantised per-cell cost (ncells)
     long long *part_scratch = nullptr;  // prefix sums of the partition
     float *cell_X = nullptr;            // features, ncells x 3
@@ -294,12 +295,19 @@ cudaError_t launch_set_rebuild(md_system *h);
 
 // ---- scheduler and cost model (k_sched.cu, k_mlp.cu) ----------------------
 constexpr int kMlpParams = 1217;
-// The static schedulers cut the cells into kSchedRounds ranges per CTA, plus
-// a tail of sched_tail_parts() further equal-cost parts (a fifth of the
-// total) that the persistent kernel hands out dynamically.
+// The static schedulers cut the cells into `rounds` ranges per CTA, plus a
+// tail of sched_tail_parts() further equal-cost parts (a fifth of the total)
+// that the persistent kernel hands out dynamically.  Rounds grow with the
+// system so that a range keeps about kTilesPerRange 32-atom tiles, up to
+// kSchedRounds (measured: one round at 1 M atoms, eight at 9.8 M).
 constexpr int kSchedRounds = 8;
-inline int sched_tail_parts(int ctas) { return ctas * kSchedRounds / 4; }
-inline int sched_parts(int ctas) { return ctas * kSchedRounds + sched_tail_parts(ctas); }
+constexpr int kTilesPerRange = 24;
+inline int sched_rounds(int64_t n, int ctas) {
+    const int64_t r = ((n + 31) / 32) / ((int64_t)ctas * kTilesPerRange);
+    return r < 1 ? 1 : (r > kSchedRounds ? kSchedRounds : (int)r);
+}
+inline int sched_tail_parts(int ctas, int rounds) { return ctas * rounds / 4; }
+inline int sched_parts(int ctas, int rounds) { return ctas * rounds + sched_tail_parts(ctas, rounds); }
 // features of every cell; with paircount != 0 also cell_cost = list entries
 cudaError_t launch_cell_features(md_system *h, bool paircount, bool gated);
 // model inference on cell_X, quantised into cell_cost
