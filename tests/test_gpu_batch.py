@@ -154,19 +154,22 @@ def test_batch_rejects_unsupported_modes(md):
             md.md_cost_model(b.h, md.MD_COST_SAMPLE)
 
 
-def test_graph_replay_equals_plain_launches(md):
+@pytest.mark.parametrize("sched", ["grid", "paircount"])
+def test_graph_replay_equals_plain_launches(md, sched):
     """md_step on a non-default stream replays a captured step, whose rebuild
     chain sits under a conditional graph node; with per-launch timing on, the
     force kernels launch one by one around that conditional chain; on the
     default stream every kernel launches on its own (the gated chain included).
     All three must agree bit for bit, and the first two must count the same
-    kernel launches (the chain only when it ran)."""
+    kernel launches (the chain only when it ran).  Under the pair-count
+    scheduler the chain also recomputes the persistent kernel's partition."""
     s = inputs.lj_fcc(nc=8, T=1.0)
+    code = md.MD_SCHED_GRID if sched == "grid" else md.MD_SCHED_PAIRCOUNT
     out, launches = [], []
     for mode in ("graphs", "timing", "default_stream"):
         st = torch.cuda.default_stream() if mode == "default_stream" else torch.cuda.Stream()
         with torch.cuda.stream(st):
-            a = md.System(s.pos, s.vel, s.box, precision="mixed", stream=st)
+            a = md.System(s.pos, s.vel, s.box, precision="mixed", stream=st, scheduler=code)
             md.md_set_timing(a.h, mode == "timing")
             a.step(40)
             a.step(25)
