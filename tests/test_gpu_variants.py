@@ -95,3 +95,37 @@ def test_switch_variant_rebuilds_list(md):
         md.md_set_variant(a.h, md.MD_FORCE_FULL, md.MD_SCHED_GRID)
         off2, _ = a.neighbors()
         assert torch.equal(off2, off_full)
+
+
+@pytest.mark.parametrize("variant", ["color", "atomic"])
+def test_switch_variant_under_graph_replay(md, orc, variant):
+    """On a non-default stream the step replays captured graphs; switching to
+    a half list must drop them, or a stale full-list force kernel would run on
+    the half list.  After the switch and 30 more steps the forces match the
+    oracle's on the exported positions, and the energy stays within 1e-4 of
+    the oracle's own trajectory."""
+    s, pos = systems()["fcc4000"]
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        with md.System(pos, s.vel, s.box, precision="mixed", stream=st) as a:
+            a.step(30)                      # graphs captured and replayed
+            md.md_set_variant(a.h, variant_code(md, variant), md.MD_SCHED_GRID)
+            a.step(30)
+            md.md_forces(a.h)
+            p, _, f = (t.cpu().numpy() for t in a.state())
+            ke, pe = a.energy()
+    prm = orc.make_params(potential=orc.POT_LJ, rc=2.5, skin=0.3, dt=0.005)
+    _, f0 = orc.forces_once(prm, p, s.box)
+    fn = np.linalg.norm(f0, axis=1)
+    rms = math.sqrt(np.mean(fn * fn))
+    err = np.linalg.norm(f - f0, axis=1)
+    off, ids = orc.neighbors_cells(p, s.box, 2.8)
+    rows = np.repeat(np.arange(len(p)), np.diff(off))
+    d = p[ids] - p[rows]
+    d -= s.box * np.round(d / s.box)
+    r = np.sqrt((d * d).sum(1))
+    bad = np.zeros(len(p), bool)
+    bad[rows[np.abs(r - 2.5) < 1e-5]] = True
+    assert np.all((err <= 2e-4 * fn + 1e-5 * max(1.0, rms)) | bad)
+    E = orc.md_run(prm, pos, s.vel, s.box, 60)["energies"][-1, 2]
+    assert abs(ke + pe - E) < 1e-4 * abs(E), (ke + pe, E)
