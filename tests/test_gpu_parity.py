@@ -314,7 +314,12 @@ def test_invalid_arguments(md):
         assert e.value.status == md.MD_ERR_INVALID
 
 
-def test_capacity_limit_and_regrow(md, orc):
+@pytest.mark.parametrize("stream", ["default", "own"])
+def test_capacity_limit_and_regrow(md, orc, stream):
+    """A state that outgrows the list capacity: creation with a fixed
+    max_neighbors fails with MD_ERR_LIST_OVERFLOW; without it md_step grows
+    the list and repeats the step.  On its own stream the steps replay
+    captured graphs, which the regrowth drops (they hold the old list)."""
     # dilute start: lattice spacing 2.0 -> few neighbours; the list is sized small
     nc = 12
     side = 2.0
@@ -327,7 +332,10 @@ def test_capacity_limit_and_regrow(md, orc):
     with pytest.raises(md.MDError) as e:
         md.System(dense, vel, box, max_neighbors=8)
     assert e.value.status == md.MD_ERR_LIST_OVERFLOW
-    with md.System(dilute, vel, box, precision="fp64") as a:
+    st = torch.cuda.default_stream() if stream == "default" else torch.cuda.Stream()
+    with torch.cuda.stream(st), md.System(dilute, vel, box, precision="fp64", stream=st) as a:
+        a.step(3)                       # on its own stream: graphs captured
+        md.md_set_state(a.h, torch.as_tensor(dilute, device="cuda"), torch.as_tensor(vel, device="cuda"))
         cap0 = a.stats()["cap"]
         md.md_set_state(a.h, torch.as_tensor(dense, device="cuda"), None)
         a.step(5)                       # the rebuild overflows and is repaired
