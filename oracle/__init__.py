@@ -200,8 +200,10 @@ def lj_list(pos, box, offsets, ids, eps=1.0, sigma=1.0, rc=2.5, per_atom=False):
     return (U, f, e) if per_atom else (U, f)
 
 
-def sc_list(pos, box, offsets, ids, eps=1.0, a=1.0, c=39.432, n_exp=9.0, m_exp=6.0, rc=2.0):
-    """Returns (U, f, rho, dF) from a full list."""
+def sc_list(pos, box, offsets, ids, eps=1.0, a=1.0, c=39.432, n_exp=9.0, m_exp=6.0, rc=2.0,
+            per_atom=False):
+    """Returns (U, f, rho, dF) from a full list, and the per-atom energies
+    as a fifth value when per_atom is set."""
     pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
     offsets = np.ascontiguousarray(offsets, np.int64)
     ids = np.ascontiguousarray(ids, np.int32)
@@ -209,10 +211,12 @@ def sc_list(pos, box, offsets, ids, eps=1.0, a=1.0, c=39.432, n_exp=9.0, m_exp=6
     f = np.zeros_like(pos)
     rho = np.zeros(n)
     dF = np.zeros(n)
+    e = np.zeros(n) if per_atom else None
     U = lib().orc_sc_list(n, _P(pos, C.c_double), _P(box, C.c_double), eps, a, c, n_exp, m_exp,
                           rc, _P(offsets, C.c_int64), _P(ids, C.c_int32), _P(f, C.c_double),
-                          _P(rho, C.c_double), _P(dF, C.c_double), None)
-    return U, f, rho, dF
+                          _P(rho, C.c_double), _P(dF, C.c_double),
+                          _P(e, C.c_double) if per_atom else None)
+    return (U, f, rho, dF, e) if per_atom else (U, f, rho, dF)
 
 
 def sc_brute(pos, box, eps=1.0, a=1.0, c=39.432, n_exp=9.0, m_exp=6.0, rc=2.0):
@@ -323,13 +327,14 @@ def forces_sample(params: Params, pos, box, idx):
     return f, e
 
 
-def neighbors_sample(pos, box, r_list, idx):
-    """List rows (ascending original id) of the sampled atoms idx."""
+def neighbors_sample(pos, box, r_list, idx, cap=None):
+    """List rows (ascending original id) of the sampled atoms idx; cap is the
+    room for entries in all (default 512 per sampled atom)."""
     L = _sample_sigs()
     pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
     idx = np.ascontiguousarray(idx, np.int64)
     off = np.zeros(idx.size + 1, np.int64)
-    cap = 512 * max(1, idx.size)
+    cap = int(cap) if cap is not None else 512 * max(1, idx.size)
     ids = np.zeros(cap, np.int32)
     t = L.orc_neighbors_sample(pos.shape[0], _P(pos, C.c_double), _P(box, C.c_double),
                                float(r_list), idx.size, _P(idx, C.c_int64), _P(off, C.c_int64),
