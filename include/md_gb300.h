@@ -47,7 +47,8 @@ typedef enum {
     MD_ERR_CUDA = -3,          /* a CUDA runtime call failed */
     MD_ERR_LIST_OVERFLOW = -4, /* neighbour capacity exceeded (md_step regrows and retries) */
     MD_ERR_NONFINITE = -5,     /* a position or force became NaN/Inf */
-    MD_ERR_TIMEOUT = -6,       /* a bounded device wait gave up */
+    MD_ERR_TIMEOUT = -6,       /* a bounded device wait gave up (reserved: no kernel of this
+                                  library waits on another, so no call returns it) */
     MD_ERR_STATE = -7          /* handle unusable: destroy it */
 } md_status;
 
@@ -136,7 +137,10 @@ md_status md_bin_cells(md_system *h);
 md_status md_build_neighbors(md_system *h);
 
 /* Forces (and per-atom energies) at the current positions, rebuilding the
- * list first when it is stale.  Asynchronous. */
+ * list first when it is stale.  Pair potentials follow the pair loop of
+ * Sec. 2.2, f_i = sum_j -(1/d) dPhi/dr (r_i - r_j) over list entries with
+ * r < r_c; the many-body potential follows Eq. 1-2 in the three steps of
+ * Sec. 3.1 (density, embedding derivative, forces).  Asynchronous. */
 md_status md_forces(md_system *h);
 
 /* Advances nsteps >= 0 velocity-Verlet steps (Sec. 3.3).  Lists are rebuilt
@@ -150,21 +154,30 @@ md_status md_forces(md_system *h);
 md_status md_step(md_system *h, int64_t nsteps);
 
 /* Kinetic and potential energy at the current state (host outputs).  The
- * potential energy comes from a fresh force evaluation; synchronizes. */
+ * potential energy is U of Eq. 1 (for a pair potential its F term is zero:
+ * U = 1/2 sum_{i != j} Phi(r_ij) over r < r_c) from a fresh force
+ * evaluation; KE = 1/2 m sum_i |v_i|^2 with the full-step velocities of the
+ * velocity-Verlet scheme of Sec. 3.3.  Synchronizes. */
 md_status md_energy(md_system *h, double *ke_host, double *pe_host);
 
 /* Copies the state out in original atom order; any pointer may be NULL.
- * pos_dev positions are wrapped into [0, L).  force_dev receives the forces
- * of the last force evaluation. */
+ * The state is that of the velocity-Verlet scheme of Sec. 3.3 between two
+ * steps: positions x(t) wrapped into [0, L), full-step velocities v(t), and
+ * (force_dev) the forces f(t) of the last force evaluation (Sec. 2.2). */
 md_status md_get_state(md_system *h, double *pos_dev, double *vel_dev, double *force_dev);
 
 /* Replaces positions and velocities (original order, device arrays;
- * positions wrapped into [0, L) on the way in); the next force evaluation
- * rebinds and rebuilds the list. */
+ * positions wrapped into [0, L) on the way in): the state x(t), v(t) of the
+ * velocity-Verlet scheme of Sec. 3.3.  The next force evaluation rebinds
+ * the cells (Sec. 2.1) and rebuilds the list, as after any list-invalidating
+ * move (Sec. 3.3), so a restored state continues like an uninterrupted run
+ * that rebuilt its list at the same step. */
 md_status md_set_state(md_system *h, const double *pos_dev, const double *vel_dev);
 
-/* Exports the current list as CSR in original order: offsets_dev[n + 1]
- * (int64) and ids_dev (int32 original ids, ascending within each row).
+/* Exports the current Verlet list (Sec. 2.1: built per cell from the 27
+ * surrounding cells; Sec. 3.3: radius r_list = r_c + skin) as CSR in
+ * original order: offsets_dev[n + 1] (int64) and ids_dev (int32 original
+ * ids, ascending within each row).
  * half != 0 keeps only j > i.  cap = capacity of ids_dev in entries.
  * *total_host receives the entry count; if it exceeds cap nothing is
  * written to ids_dev and MD_ERR_LIST_OVERFLOW is returned.  Synchronizes. */
@@ -265,7 +278,8 @@ md_status md_mlp_adam(float *P_dev, const float *G_dev, float *m_dev, float *v_d
 /* Contiguous equal-cost partition of ncells integer costs into nparts:
  * bounds_dev[b] = first cell k with (inclusive prefix of cost through k) *
  * nparts > b * total; bounds_dev[0] = 0, bounds_dev[nparts] = ncells.
- * Asynchronous on stream. */
+ * Costs must be >= 0 with total * nparts < 2^63 (the comparisons are exact
+ * int64 products; larger sums give wrong bounds).  Asynchronous on stream. */
 md_status md_partition(const int64_t *cost_dev, int64_t ncells, int32_t nparts,
                        int64_t *bounds_dev, void *cuda_stream);
 
@@ -280,8 +294,11 @@ md_status md_partition(const int64_t *cost_dev, int64_t ncells, int32_t nparts,
  *  - ncells must be <= 1,048,576; larger sizes return MD_ERR_INVALID and
  *    md_last_error(NULL) says why (use md_partition for them).
  *  - The first call on a device looks up the array's device address with
- *    cudaGetSymbolAddress (once per device, with that device current); make
- *    that first call before any stream capture.
+ *    cudaGetSymbolAddress (once per device, with that device current) and
+ *    keeps it for the life of the process; make that first call before any
+ *    stream capture.  A device reset (cudaDeviceReset) while the library
+ *    stays loaded is not supported: the kept address would be stale.
+ *  - Costs must be >= 0 with total * nparts < 2^63, as for md_partition.
  *  - All calls share the one array and nothing in it needs to start at zero
  *    (the scan overwrites every word it reads).  Calls that overlap on the
  *    GPU -- different streams, or different host threads -- race on it; the

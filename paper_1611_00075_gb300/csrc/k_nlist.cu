@@ -64,9 +64,13 @@ enum ListMode {
 };
 
 struct BandNote {
-    int count;  // band candidates met
-    int k, j, s;  // the first one: its slot in the row, its index, its stencil cell
+    int count;    // band candidates met
+    int k, j, s;  // the last one: its slot in the row; its index and stencil cell
+                  // (kept only when the row is not written: a written row holds them)
 };
+
+// Offset of entry k in a row of the quad layout: (k / 4) * 128 + k % 4.
+__device__ __forceinline__ int row_off(int k) { return k + (k >> 2) * 124; }
 
 // The list of sorted atom i: scans the 27 cells around its cell and writes
 // its row (entries in stencil order, then ascending index).  Returns the
@@ -108,7 +112,9 @@ __device__ __forceinline__ int list_atom(int i, const Grid &g, float lo, float h
                 const int b = start[cn], e = start[cn + 1];
                 const int skip = (s == 13) ? i : -1;  // the atom itself, home cell only
                 if (LM == LM_DEFER) {
-                    // branch-free acceptance: predicated store and count
+                    // branch-free acceptance: a predicated store, a counted
+                    // slot; a band candidate only notes its slot (the row
+                    // holds its index and stencil cell)
 #pragma unroll 4
                     for (int j = b; j < e; ++j) {
                         const float4 qj = xq[j];
@@ -116,19 +122,17 @@ __device__ __forceinline__ int list_atom(int i, const Grid &g, float lo, float h
                         const float r2f = ex * ex + ey * ey + ez * ez;
                         bool acc = (r2f < hi) & (j != skip);
                         if (HALF) acc = acc & (__float_as_int(qj.w) > myo);
-                        if (acc) {
-                            if (WRITE && cnt < cap)
-                                row[(size_t)(((cnt >> 2) << 7) | (cnt & 3))] = sbits | (uint32_t)j;
-                            if (r2f >= lo) {
-                                if (band.count == 0) {
-                                    band.k = cnt;
-                                    band.j = j;
-                                    band.s = s;
-                                }
-                                ++band.count;
-                            }
-                            ++cnt;
+                        if (WRITE) {
+                            if (acc & (cnt < cap)) row[row_off(cnt)] = sbits | (uint32_t)j;
+                        } else {
+                            const bool bq = acc & (r2f >= lo);
+                            band.j = bq ? j : band.j;
+                            band.s = bq ? s : band.s;
                         }
+                        const bool bnd = acc & (r2f >= lo);
+                        band.k = bnd ? cnt : band.k;
+                        band.count += bnd ? 1 : 0;
+                        cnt += acc ? 1 : 0;
                     }
                 } else {
 #pragma unroll 4
@@ -198,9 +202,16 @@ build_list_kernel(int n, const Grid *__restrict__ grids, const uint16_t *__restr
         } else {
             cnt = list_atom<LM_DEFER, WRITE, HALF>(i, g, lo, hi, rl2, xq, xabs, c, start, row, cap,
                                                    band);
-            if (band.count == 1) {
+            if (band.count == 1 && WRITE && band.k >= cap) {
+                overflow = 1;  // the entry was not stored: the row is regrown anyway
+            } else if (band.count == 1) {
                 // verify the one provisional entry; drop it if the float64
                 // definition rejects it
+                if (WRITE) {
+                    const uint32_t ent = row[row_off(band.k)];
+                    band.j = (int)(ent & kIndexMask);
+                    band.s = (int)(ent >> kIndexBits);
+                }
                 const int cx = c % g.nx, cy = (c / g.nx) % g.ny, cz = c / (g.nx * g.ny);
                 double shx, shy, shz;
                 stencil_shift64(g, cx, cy, cz, band.s, shx, shy, shz);
@@ -208,8 +219,7 @@ build_list_kernel(int n, const Grid *__restrict__ grids, const uint16_t *__restr
                     overflow |= (cnt > cap);  // a full row lost its tail: regrow
                     if (WRITE)
                         for (int k = band.k; k + 1 < min(cnt, cap); ++k)
-                            row[(size_t)(((k >> 2) << 7) | (k & 3))] =
-                                row[(size_t)((((k + 1) >> 2) << 7) | ((k + 1) & 3))];
+                            row[row_off(k)] = row[row_off(k + 1)];
                     --cnt;
                 }
             } else if (band.count > 1) {

@@ -268,7 +268,18 @@ def md_mlp_adam(P, G, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream
                              beta2, eps, _stream(stream)), None, "md_mlp_adam")
 
 
+def _partition_args(cost, nparts, bounds, what):
+    """The C calls read cost as ncells int64 words and write nparts + 1 int64
+    bounds on the device: anything else is refused before the call."""
+    for name, t, need in (("cost", cost, 1), ("bounds", bounds, int(nparts) + 1)):
+        if (not isinstance(t, torch.Tensor) or t.dtype != torch.int64 or not t.is_cuda
+                or not t.is_contiguous() or t.numel() < need):
+            raise MDError(MD_ERR_INVALID, "%s: %s must be a contiguous int64 CUDA tensor of at "
+                                          "least %d elements" % (what, name, need))
+
+
 def md_partition(cost: torch.Tensor, nparts: int, bounds: torch.Tensor, stream=None):
+    _partition_args(cost, nparts, bounds, "md_partition")
     _check(lib().md_partition(_ptr(cost), cost.numel(), int(nparts), _ptr(bounds),
                               _stream(stream)), None, "md_partition")
 
@@ -276,6 +287,7 @@ def md_partition(cost: torch.Tensor, nparts: int, bounds: torch.Tensor, stream=N
 def md_partition_noalloc(cost: torch.Tensor, nparts: int, bounds: torch.Tensor, stream=None):
     """md_partition without any device allocation (fixed scratch inside the
     library; ncells <= 1,048,576; overlapping calls race on the scratch)."""
+    _partition_args(cost, nparts, bounds, "md_partition_noalloc")
     _check(lib().md_partition_noalloc(_ptr(cost), cost.numel(), int(nparts), _ptr(bounds),
                                       _stream(stream)), None, "md_partition_noalloc")
 

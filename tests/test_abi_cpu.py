@@ -91,3 +91,20 @@ def test_cell_colouring_is_conflict_free(libpath, ncell):
             nb = neigh(c)
             assert not (nb & seen), (ncell, c)
             seen |= nb
+
+
+@pytest.mark.parametrize("fn", ["md_partition", "md_partition_noalloc"])
+def test_partition_binding_refuses_bad_tensors(fn):
+    """The binding refuses, before any call into the library, cost or
+    bounds tensors the C call would read or write out of bounds."""
+    torch = pytest.importorskip("torch")
+    from paper_1611_00075_gb300 import md
+    call = getattr(md, fn)
+    good = torch.zeros(8, dtype=torch.int64)  # a host tensor: refused as well
+    for cost, bounds in ((torch.zeros(8, dtype=torch.int32), good),
+                         (good, torch.zeros(3, dtype=torch.int64)),
+                         (good, good[::2]),
+                         (good, good)):
+        with pytest.raises(md.MDError) as e:
+            call(cost, 4, bounds)
+        assert e.value.status == md.MD_ERR_INVALID

@@ -51,3 +51,15 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(md):
         md.md_partition_noalloc(c, 8, b)
     assert e.value.status == md.MD_ERR_INVALID
     assert "scratch limit" in str(e.value)
+
+
+def test_noalloc_at_its_exact_size_limit(md):
+    # 2^20 cells fill the scratch to its last tile sum; an awkward part count
+    for seed, nparts in ((903, 4861), (904, 3)):
+        c = costs(seed, 1 << 20)
+        ref = torch.empty(nparts + 1, dtype=torch.int64, device="cuda")
+        got = torch.full((nparts + 1,), -1, dtype=torch.int64, device="cuda")
+        md.md_partition(c, nparts, ref)
+        md.md_partition_noalloc(c, nparts, got)
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref), (seed, nparts)
