@@ -9,10 +9,17 @@
 // state in the new order as float64 positions relative to the cell centre
 // plus their float32 copy (the layout the force kernels read).
 //
+// Traffic: the counting pass also writes each atom's absolute position and
+// velocity (with its original id, new cell and replica packed into the spare
+// fourth words) into two 32-byte records, so the gather reads two aligned
+// sectors per atom instead of seven scattered words.
+//
 // A system of several boxes (replicas) numbers its cells consecutively, box
 // after box, so each box's atoms stay one contiguous range of the sorted
 // order; every kernel reads the geometry of the atom's own box.
 #include "k_scan.cuh"
+
+#include <algorithm>
 
 namespace mdg {
 
@@ -31,34 +38,40 @@ __device__ __forceinline__ int cell_coord(double x, double inv_w, int n) {
     return q < 0 ? 0 : (q > n - 1 ? n - 1 : q);
 }
 
-// Absolute positions from the relative state (skipped when they are exact).
-// An atom of an interior cell whose offset is below the cell width lies
-// strictly inside the box, so only boundary cells and stray offsets need the
-// periodic wrap.
-__global__ void prepare_abs_kernel(int n, const Grid *__restrict__ grids,
-                                   const uint16_t *__restrict__ rep,
-                                   const double4 *__restrict__ xr,
-                                   const int32_t *__restrict__ cell, double4 *__restrict__ xabs,
-                                   const DevStatus *ds, bool gated) {
-    if (chain_off(ds, gated) || ds->abs_fresh) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const Grid &g = grids[rep ? rep[i] : 0];
-        const double4 r = xr[i];
-        const int c = cell[i];
-        double x = r.x, y = r.y, z = r.z;
-        if (c >= 0) {
-            const int cl = c - g.cell0;
-            const int cx = cl % g.nx, cy = (cl / g.nx) % g.ny, cz = cl / (g.nx * g.ny);
-            const double3 C = cell_centre_of(cx, cy, cz, g);
-            x = C.x + x; y = C.y + y; z = C.z + z;
-            if (cx == 0 || cx == g.nx - 1 || !below_cell_width(r.x, g)) x = wrap_coord(x, g.L[0]);
-            if (cy == 0 || cy == g.ny - 1 || !below_cell_width(r.y, g)) y = wrap_coord(y, g.L[1]);
-            if (cz == 0 || cz == g.nz - 1 || !below_cell_width(r.z, g)) z = wrap_coord(z, g.L[2]);
-        } else {
-            x = wrap_coord(x, g.L[0]); y = wrap_coord(y, g.L[1]); z = wrap_coord(z, g.L[2]);
-        }
-        xabs[i] = make_double4(x, y, z, 0.0);
+// Absolute position of sorted atom i: exact in xabs right after a build or a
+// load (abs_fresh); otherwise the cell centre plus the relative position.  An
+// atom of an interior cell whose offset is below the cell width lies strictly
+// inside the box, so only boundary cells and stray offsets need the periodic
+// wrap.  cell < 0: xr holds the absolute position (a loaded state).
+__device__ __forceinline__ double3 absolute_position(int i, const Grid &g, bool fresh,
+                                                     const double4 *__restrict__ xr,
+                                                     const int32_t *__restrict__ cell,
+                                                     const double4 *__restrict__ xabs) {
+    if (fresh) {
+        const double4 a = xabs[i];
+        return make_double3(a.x, a.y, a.z);
     }
+    const double4 r = xr[i];
+    const int c = cell[i];
+    double x = r.x, y = r.y, z = r.z;
+    if (c >= 0) {
+        const int cl = c - g.cell0;
+        const int cx = cl % g.nx, cy = (cl / g.nx) % g.ny, cz = cl / (g.nx * g.ny);
+        const double3 C = cell_centre_of(cx, cy, cz, g);
+        x = C.x + x; y = C.y + y; z = C.z + z;
+        if (cx == 0 || cx == g.nx - 1 || !below_cell_width(r.x, g)) x = wrap_coord(x, g.L[0]);
+        if (cy == 0 || cy == g.ny - 1 || !below_cell_width(r.y, g)) y = wrap_coord(y, g.L[1]);
+        if (cz == 0 || cz == g.nz - 1 || !below_cell_width(r.z, g)) z = wrap_coord(z, g.L[2]);
+    } else {
+        x = wrap_coord(x, g.L[0]); y = wrap_coord(y, g.L[1]); z = wrap_coord(z, g.L[2]);
+    }
+    return make_double3(x, y, z);
+}
+
+// Spare fourth words of the gather records: (new cell << 32 | original id)
+// beside the position, the replica beside the velocity.
+__device__ __forceinline__ double pack2(int hi, int lo) {
+    return __longlong_as_double(((long long)hi << 32) | (long long)(unsigned)lo);
 }
 
 __global__ void zero_counts_kernel(int ncells, int32_t *count, DevStatus *ds, bool gated) {
@@ -68,24 +81,34 @@ __global__ void zero_counts_kernel(int ncells, int32_t *count, DevStatus *ds, bo
         count[c] = 0;
 }
 
+// Cell of every atom, its slot in the cell (atomic count) and its gather
+// records: (x, y, z, new cell | original id) and (v, replica).
 __global__ void bin_count_kernel(int n, const Grid *__restrict__ grids,
                                  const uint16_t *__restrict__ rep,
+                                 const double4 *__restrict__ xr,
+                                 const int32_t *__restrict__ cell,
                                  const double4 *__restrict__ xabs,
+                                 const double *__restrict__ v, const int32_t *__restrict__ orig,
                                  int32_t *__restrict__ count, int32_t *__restrict__ new_cell,
-                                 int32_t *__restrict__ slot, DevStatus *ds, bool gated) {
+                                 int32_t *__restrict__ slot, double4 *__restrict__ tabs,
+                                 double4 *__restrict__ tv, DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
+    const bool fresh = ds->abs_fresh != 0;
     int maxs = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const Grid &g = grids[rep ? rep[i] : 0];
-        double4 x = xabs[i];
-        int cx = cell_coord(x.x, g.inv_w[0], g.nx);
-        int cy = cell_coord(x.y, g.inv_w[1], g.ny);
-        int cz = cell_coord(x.z, g.inv_w[2], g.nz);
-        int c = g.cell0 + (cz * g.ny + cy) * g.nx + cx;
+        const int r = rep ? rep[i] : 0;
+        const Grid &g = grids[r];
+        const double3 x = absolute_position(i, g, fresh, xr, cell, xabs);
+        const int cx = cell_coord(x.x, g.inv_w[0], g.nx);
+        const int cy = cell_coord(x.y, g.inv_w[1], g.ny);
+        const int cz = cell_coord(x.z, g.inv_w[2], g.nz);
+        const int c = g.cell0 + (cz * g.ny + cy) * g.nx + cx;
         new_cell[i] = c;
-        int s = atomicAdd(&count[c], 1);
-        slot[i] = s;
-        maxs = max(maxs, s + 1);
+        const int sl = atomicAdd(&count[c], 1);
+        slot[i] = sl;
+        maxs = max(maxs, sl + 1);
+        tabs[i] = make_double4(x.x, x.y, x.z, pack2(c, orig[i]));
+        tv[i] = make_double4(v[i], v[n + i], v[2 * (size_t)n + i], pack2(0, r));
     }
     // all lanes arrive here (grid-stride loop): one atomic per warp
     maxs = __reduce_max_sync(0xffffffffu, (unsigned)maxs);
@@ -105,49 +128,49 @@ __global__ void scatter_kernel(int n, const int32_t *__restrict__ new_cell,
     }
 }
 
-// Orders each cell's range by original id (insertion sort; cells hold tens of atoms).
-__global__ void cell_sort_kernel(int ncells, const int32_t *__restrict__ start,
-                                 int32_t *__restrict__ key, int32_t *__restrict__ src,
-                                 const DevStatus *ds, bool gated) {
+// Orders each cell's range by original id.  One warp per cell: a cell of up
+// to 32 atoms is ranked by shuffles (lane l's rank = how many keys of the cell
+// are smaller; the keys are distinct original ids); a larger cell (dense
+// systems) is insertion-sorted by one lane.
+constexpr int kSortBlock = 256;
+
+__global__ void __launch_bounds__(kSortBlock)
+cell_sort_kernel(int ncells, const int32_t *__restrict__ start, int32_t *__restrict__ key,
+                 int32_t *__restrict__ src, const DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
-        int b = start[c], e = start[c + 1];
-        for (int a = b + 1; a < e; ++a) {
-            int k = key[a], s = src[a];
-            int q = a - 1;
-            while (q >= b && key[q] > k) {
-                key[q + 1] = key[q];
-                src[q + 1] = src[q];
-                --q;
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (kSortBlock / 32);
+    for (int c = blockIdx.x * (kSortBlock / 32) + (threadIdx.x >> 5); c < ncells; c += nw) {
+        const int b = start[c], m = start[c + 1] - b;
+        if (m <= 1) continue;
+        if (m <= 32) {
+            const int k = lane < m ? key[b + lane] : 0x7fffffff;
+            const int sv = lane < m ? src[b + lane] : 0;
+            int rank = 0;
+            for (int q = 0; q < m; ++q) rank += (__shfl_sync(0xffffffffu, k, q) < k) ? 1 : 0;
+            if (lane < m) {
+                key[b + rank] = k;
+                src[b + rank] = sv;
             }
-            key[q + 1] = k;
-            src[q + 1] = s;
+        } else if (lane == 0) {
+            for (int a = b + 1; a < b + m; ++a) {
+                const int k = key[a], sv = src[a];
+                int q = a - 1;
+                while (q >= b && key[q] > k) {
+                    key[q + 1] = key[q];
+                    src[q + 1] = src[q];
+                    --q;
+                }
+                key[q + 1] = k;
+                src[q + 1] = sv;
+            }
         }
     }
 }
 
-__global__ void copy_src_kernel(int n, const double4 *__restrict__ xabs,
-                                const double *__restrict__ v, const int32_t *__restrict__ orig,
-                                const uint16_t *__restrict__ rep, double4 *__restrict__ tabs,
-                                double *__restrict__ tv, int32_t *__restrict__ torig,
-                                uint16_t *__restrict__ trep, const DevStatus *ds, bool gated) {
-    if (chain_off(ds, gated)) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        tabs[i] = xabs[i];
-        tv[i] = v[i];
-        tv[n + i] = v[n + i];
-        tv[2 * (size_t)n + i] = v[2 * (size_t)n + i];
-        torig[i] = orig[i];
-        if (rep) trep[i] = rep[i];
-    }
-}
-
 __global__ void gather_kernel(int n, const Grid *__restrict__ grids,
-                              const int32_t *__restrict__ src,
-                              const int32_t *__restrict__ new_cell,
-                              const double4 *__restrict__ tabs, const double *__restrict__ tv,
-                              const int32_t *__restrict__ torig,
-                              const uint16_t *__restrict__ trep, double4 *__restrict__ xr,
+                              const int32_t *__restrict__ src, const double4 *__restrict__ tabs,
+                              const double4 *__restrict__ tv, double4 *__restrict__ xr,
                               float4 *__restrict__ xq, float4 *__restrict__ xq_build,
                               double4 *__restrict__ xabs, double *__restrict__ v,
                               int32_t *__restrict__ orig, int32_t *__restrict__ cell,
@@ -155,26 +178,28 @@ __global__ void gather_kernel(int n, const Grid *__restrict__ grids,
     if (chain_off(ds, gated)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) ds->abs_fresh = 1;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        int s = src[k];
-        int c = new_cell[s];
-        const uint16_t r = trep ? trep[s] : 0;
+        const int s = src[k];
+        const double4 a = tabs[s];
+        const double4 u = tv[s];
+        const long long pa = __double_as_longlong(a.w);
+        const int o = (int)(unsigned)(pa & 0xffffffffll);
+        const int c = (int)(pa >> 32);
+        const int r = (int)(__double_as_longlong(u.w) & 0xffff);
         const Grid &g = grids[r];
         const int cl = c - g.cell0;
         const double3 C = cell_centre_of(cl % g.nx, (cl / g.nx) % g.ny, cl / (g.nx * g.ny), g);
-        double4 a = tabs[s];
-        double rx = a.x - C.x, ry = a.y - C.y, rz = a.z - C.z;
-        int o = torig[s];
+        const double rx = a.x - C.x, ry = a.y - C.y, rz = a.z - C.z;
         xr[k] = make_double4(rx, ry, rz, 0.0);
-        float4 q = make_float4((float)rx, (float)ry, (float)rz, __int_as_float(o));
+        const float4 q = make_float4((float)rx, (float)ry, (float)rz, __int_as_float(o));
         xq[k] = q;
         xq_build[k] = q;
-        xabs[k] = a;
-        v[k] = tv[s];
-        v[n + k] = tv[n + s];
-        v[2 * (size_t)n + k] = tv[2 * (size_t)n + s];
+        xabs[k] = make_double4(a.x, a.y, a.z, 0.0);
+        v[k] = u.x;
+        v[n + k] = u.y;
+        v[2 * (size_t)n + k] = u.z;
         orig[k] = o;
         cell[k] = c;
-        if (rep) rep[k] = r;
+        if (rep) rep[k] = (uint16_t)r;
     }
 }
 
@@ -198,28 +223,24 @@ cudaError_t launch_bin(md_system *h, bool gated) {
     int n = (int)h->n;
     cudaStream_t s = h->stream;
     int cur = h->cur;
-    prepare_abs_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->grids, h->rep, h->xr64[cur], h->cell,
-                                                       h->xabs, h->ds, gated);
     zero_counts_kernel<<<gs_blocks(h->g.ncells), kBlock, 0, s>>>(h->g.ncells, h->cell_count,
                                                                  h->ds, gated);
-    bin_count_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->grids, h->rep, h->xabs,
-                                                     h->cell_count, h->new_cell, h->slot, h->ds,
-                                                     gated);
+    bin_count_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->grids, h->rep, h->xr64[cur], h->cell,
+                                                     h->xabs, h->v, h->orig, h->cell_count,
+                                                     h->new_cell, h->slot, h->tmp_abs, h->tmp_v,
+                                                     h->ds, gated);
     cudaError_t e = launch_scan_i32(h->cell_count, h->cell_start, h->g.ncells, h->scan_bsum,
                                     h->ds, gated, s);
     if (e != cudaSuccess) return e;
     scatter_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->new_cell, h->slot, h->cell_start,
                                                    h->orig, h->src, h->key, h->ds, gated);
-    cell_sort_kernel<<<gs_blocks(h->g.ncells), kBlock, 0, s>>>(h->g.ncells, h->cell_start, h->key,
-                                                               h->src, h->ds, gated);
-    copy_src_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->xabs, h->v, h->orig, h->rep,
-                                                    h->tmp_abs, h->tmp_v, h->tmp_orig,
-                                                    h->tmp_rep, h->ds, gated);
-    gather_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->grids, h->src, h->new_cell, h->tmp_abs,
-                                                  h->tmp_v, h->tmp_orig,
-                                                  h->rep ? h->tmp_rep : nullptr, h->xr64[cur],
-                                                  h->xq[cur], h->xq_build, h->xabs, h->v, h->orig,
-                                                  h->cell, h->rep, h->ds, gated);
+    const int sort_blocks = std::min((h->g.ncells + kSortBlock / 32 - 1) / (kSortBlock / 32),
+                                     kGridCap * 2);
+    cell_sort_kernel<<<std::max(sort_blocks, 1), kSortBlock, 0, s>>>(h->g.ncells, h->cell_start,
+                                                                     h->key, h->src, h->ds, gated);
+    gather_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->grids, h->src, h->tmp_abs, h->tmp_v,
+                                                  h->xr64[cur], h->xq[cur], h->xq_build, h->xabs,
+                                                  h->v, h->orig, h->cell, h->rep, h->ds, gated);
     return cudaGetLastError();
 }
 

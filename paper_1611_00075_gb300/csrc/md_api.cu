@@ -86,14 +86,14 @@ void free_all(md_system *h) {
     for (int b = 0; b < 2; ++b) { F(h->xr64[b]); F(h->xq[b]); }
     F(h->xq_build); F(h->xabs); F(h->v); F(h->f); F(h->e_atom); F(h->orig); F(h->cell);
     F(h->cell_start); F(h->cell_count); F(h->new_cell); F(h->slot); F(h->src); F(h->key);
-    F(h->scan_bsum); F(h->tmp_abs); F(h->tmp_v); F(h->tmp_orig); F(h->nlist); F(h->ncount);
+    F(h->scan_bsum); F(h->tmp_abs); F(h->tmp_v); F(h->nlist); F(h->ncount);
     F(h->rho); F(h->dF32); F(h->dF64); F(h->xqf); F(h->partials); F(h->red_out); F(h->ds);
     F(h->exp_tmp);
     F(h->part_bounds); F(h->cell_cost); F(h->part_scratch); F(h->cell_X); F(h->cell_pred);
     F(h->cell_cycles); F(h->cta_cycles); F(h->samp_flag); F(h->samp_bsum); F(h->samp_X);
     F(h->samp_y); F(h->mlp_P); F(h->mlp_G); F(h->mlp_m); F(h->mlp_v); F(h->mlp_scratch);
     F(h->mlp_loss);
-    F(h->grids); F(h->ctab); F(h->atom_off); F(h->rep); F(h->tmp_rep); F(h->shifts32); F(h->rep_pe);
+    F(h->grids); F(h->ctab); F(h->atom_off); F(h->rep); F(h->shifts32); F(h->rep_pe);
     F(h->rep_ke);
     if (h->ds_host) cudaFreeHost(h->ds_host);
     if (h->red_host) cudaFreeHost(h->red_host);
@@ -229,7 +229,7 @@ md_status enqueue_sched_prep(md_system *h, bool gated) {
 md_status enqueue_rebuild(md_system *h, bool gated) {
     MD_CK(launch_bin(h, gated));
     MD_CK(launch_build_list(h, true, gated));
-    h->launches += 13;
+    h->launches += kBinLaunches + 3;  // binning, list reset and build, finish
     md_status st = enqueue_sched_prep(h, gated);
     if (st != MD_OK) return st;
     MD_CK(launch_finish_rebuild(h, gated));
@@ -569,14 +569,14 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
     A(dalloc(&h->cell, N)); A(dalloc(&h->cell_start, C + 1)); A(dalloc(&h->cell_count, C));
     A(dalloc(&h->new_cell, N)); A(dalloc(&h->slot, N)); A(dalloc(&h->src, N));
     A(dalloc(&h->key, N)); A(dalloc(&h->scan_bsum, scan_len)); A(dalloc(&h->tmp_abs, N));
-    A(dalloc(&h->tmp_v, 3 * N)); A(dalloc(&h->tmp_orig, N)); A(dalloc(&h->ncount, N));
+    A(dalloc(&h->tmp_v, N)); A(dalloc(&h->ncount, N));
     size_t ctab_len = 0;
     for (const Grid &g : h->grids_h) ctab_len += (size_t)g.nx + g.ny + g.nz;
     A(dalloc(&h->grids, (size_t)R)); A(dalloc(&h->ctab, ctab_len));
     A(dalloc(&h->atom_off, (size_t)R + 1));
     A(dalloc(&h->rep_pe, (size_t)R)); A(dalloc(&h->rep_ke, (size_t)R));
     if (R > 1) {
-        A(dalloc(&h->rep, N)); A(dalloc(&h->tmp_rep, N));
+        A(dalloc(&h->rep, N));
         A(dalloc(&h->shifts32, (size_t)R * kStencil));
     }
     if (p->potential == MD_POT_SC) {

@@ -159,7 +159,6 @@ struct md_system {
     double *ctab = nullptr;           // cell-centre tables of all boxes (Grid::ctab)
     int64_t *atom_off = nullptr;      // device copy of atom_off_h
     uint16_t *rep = nullptr;          // sorted slot -> replica (batches only)
-    uint16_t *tmp_rep = nullptr;
     float4 *shifts32 = nullptr;       // R x 27 float32 cell shifts (batches only)
     double *rep_ke = nullptr, *rep_pe = nullptr;  // per-replica sums (device)
     mdg::ForceConsts fc{};
@@ -184,9 +183,8 @@ struct md_system {
     int32_t *cell_count = nullptr;  // ncells
     int32_t *new_cell = nullptr, *slot = nullptr, *src = nullptr, *key = nullptr;
     int32_t *scan_bsum = nullptr;
-    double4 *tmp_abs = nullptr;
-    double *tmp_v = nullptr;
-    int32_t *tmp_orig = nullptr;
+    double4 *tmp_abs = nullptr;  // gather records: (x, y, z, new cell | original id)
+    double4 *tmp_v = nullptr;    //                 (vx, vy, vz, replica)
 
     // neighbour list: warp-interleaved [n/32][cap][32] entries + counts
     uint32_t *nlist = nullptr;
@@ -257,8 +255,10 @@ struct md_system {
 namespace mdg {
 
 // ---- binning (k_bin.cu) --------------------------------------------------
-// Gated chain: reconstruct absolute positions, count per cell, scan, scatter,
-// order each cell by original id, gather the new sorted state.
+// Gated chain: count per cell (with the absolute positions and gather
+// records), scan, scatter, order each cell by original id, gather the new
+// sorted state.  kBinLaunches kernels.
+constexpr int kBinLaunches = 8;
 cudaError_t launch_bin(md_system *h, bool gated);
 // Exclusive scan of int32 counts into int32 starts (starts[n] = total).
 cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int n, int32_t *bsum,
