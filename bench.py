@@ -131,8 +131,10 @@ def make_workload(name: str, nc: int = 0):
     elif name == "fcc":
         k = nc or 64
         s = inputs.lj_fcc(nc=k, T=1.2)
-        desc = ("Lennard-Jones fcc %d^3 cells = %d atoms, rho*=0.8442, T*=1.2, rc=2.5, skin=0.3"
-                % (k, s.n))
+        desc = ("Lennard-Jones liquid %d^3 fcc cells = %d atoms melted from fcc at rho*=0.8442 "
+                "(2,000 untimed mixed-precision steps, velocities rescaled every 50 steps to "
+                "T*=2.4 for 1,000 steps, then to T*=1.2), T*=1.2, rc=2.5, skin=0.3, dt=0.005, "
+                "half-skin rebuilds" % (k, s.n))
     else:
         k = nc or 128
         s = inputs.sc_fcc(nc=k)
@@ -284,8 +286,18 @@ def run_gpu(args, rank, world, local):
                              stream=stream, **kw)
         else:
             mixed = md.System(s.pos, s.vel, s.box, precision="mixed", stream=stream, **kw)
-        md.md_step(mixed.h, args.warmup)
         sched_info = {}
+        if args.workload == "fcc":
+            # config 2 is a liquid melted from the crystal; the melted state is
+            # the start of every leg below
+            t0 = time.perf_counter()
+            gpu_melt(md, mixed, kw["mass"], dev)
+            p_m, v_m, _ = mixed.state()
+            s = inputs.System(name=s.name + "_melted", pos=p_m.cpu().numpy(), vel=v_m.cpu().numpy(),
+                              box=s.box, params=s.params)
+            sched_info["melt"] = {"seconds": time.perf_counter() - t0, "steps": sum(
+                k for _, k in inputs.MELT_SCHEDULE), "schedule": inputs.MELT_SCHEDULE}
+        md.md_step(mixed.h, args.warmup)
         if ensemble:
             s0 = mixed.state()[:2]
 
@@ -344,6 +356,18 @@ def run_gpu(args, rank, world, local):
                         "force_ms_per_launch": stx["ms"]["force"] / max(1, stx["count"]["force"])}
                     if code != md.MD_SCHED_GRID:
                         sched_info[name]["cta_imbalance"] = md.md_cost_model(mixed.h, md.MD_COST_PROFILE)
+                # the same static partitions with no dynamically claimed tail:
+                # the cost estimate alone balances the CTAs
+                for name, code in (("paircount", md.MD_SCHED_PAIRCOUNT), ("mlp", md.MD_SCHED_MLP)):
+                    from_s0(md.MD_FORCE_FULL, code)
+                    md.md_set_schedule(mixed.h, 0, 0)
+                    msx, stx = timed(mixed, args.compare_steps)
+                    sched_info[name + "_static"] = {
+                        "atom_steps_per_s": n_of(mixed) * args.compare_steps / (msx * 1e-3),
+                        "force_ms_per_launch": stx["ms"]["force"] / max(1, stx["count"]["force"]),
+                        "cta_imbalance": md.md_cost_model(mixed.h, md.MD_COST_PROFILE),
+                        "note": "static ranges only (md_set_schedule tail_percent = 0)"}
+                    md.md_set_schedule(mixed.h, 0, 20)
                 # the Newton's-third-law variants (half lists) against the full list
                 variants = {}
                 for name, code in (("half_color", md.MD_FORCE_HALF_COLOR),
@@ -427,6 +451,20 @@ def run_gpu(args, rank, world, local):
                    "d2h_bytes_per_step": nbytes / args.steps,
                    "note": "per run: upload pos+vel, md_set_state, md_step(K), md_get_state, "
                            "download pos+vel; bytes amortised over K steps"}
+        # the force check of the CPU leg runs at generator positions (the start
+        # perturbed by a seeded Gaussian) loaded into the running system: the
+        # oracle never sees positions the GPU produced
+        if ensemble:
+            pos_chk = np.concatenate([np.mod(r.pos + 0.05 * inputs.gaussian(
+                inputs.SEED_BASE + 98 + k, r.pos.size).reshape(-1, 3), r.box)
+                for k, r in enumerate(reps)])
+        else:
+            pos_chk = np.mod(s.pos + 0.03 * inputs.gaussian(inputs.SEED_BASE + 98, s.pos.size)
+                             .reshape(-1, 3), s.box)
+        md.md_set_state(mixed.h, torch.as_tensor(pos_chk, device=dev), None)
+        md.md_forces(mixed.h)
+        force = mixed.state()[2]
+        pos = pos_chk
         mixed.close()
 
     peaks, peak_src = measured_peaks()
@@ -472,7 +510,7 @@ def run_gpu(args, rank, world, local):
             "fp32": {"achieved_tflops": ach_flops, "peak_tflops": fp32_peak,
                      "frac": ach_flops / fp32_peak,
                      "peak_note": "SMs x 128 fp32 lanes x 2 x max SM clock"}}
-    pos, force, box, n_chk = pos.cpu().numpy(), force.cpu().numpy(), s.box, n
+    force, box, n_chk = force.cpu().numpy(), s.box, n
     if ensemble:
         # the force check runs on the largest replica (its own box)
         k = int(np.argmax([r.n for r in reps]))
@@ -482,6 +520,26 @@ def run_gpu(args, rank, world, local):
                 clk=clk, desc=desc, pos=pos, force=force, n_check=n_chk,
                 box=box, params=s.params, ke=ke, pe=pe, builds_timed=builds_timed,
                 sched_info=sched_info)
+
+
+def gpu_melt(md, sysobj, mass, device):
+    """Melts the system in place on the GPU (untimed input preparation):
+    inputs.MELT_SCHEDULE with the velocities rescaled to each stage's
+    temperature every inputs.MELT_RESCALE_EVERY steps and once at the end."""
+    import torch
+    every = inputs.MELT_RESCALE_EVERY
+
+    def rescale(T):
+        v = sysobj.state()[1].cpu().numpy()
+        v = torch.from_numpy(inputs.rescale_velocities(v, T, mass)).to(device)
+        md.md_set_state(sysobj.h, None, v)
+
+    for T, nsteps in inputs.MELT_SCHEDULE:
+        for _ in range(nsteps // every):
+            rescale(T)
+            md.md_step(sysobj.h, every)
+    rescale(inputs.MELT_SCHEDULE[-1][0])
+    torch.cuda.synchronize()
 
 
 def per_replica(md, reps, kw, stream, steps, warmup):
@@ -509,13 +567,22 @@ def per_replica(md, reps, kw, stream, steps, warmup):
 
 # ------------------------------------------------------------------ CPU legs
 
-def oracle_sample_system(args):
+def oracle_sample_system(args, orc):
     """Bounded sample of the workload for the CPU oracle: the same generator
     at a smaller size (porous: 72^3 fcc cells, same density and void radii)."""
     if args.workload == "porous":
         return inputs.lj_porous(nc=72), "porous LJ 72^3 fcc cells (same rho*, voids U(3,15), >=40%)"
     if args.workload == "fcc":
-        return inputs.lj_fcc(nc=32, T=1.2), "LJ fcc 32^3 cells"
+        s = inputs.lj_fcc(nc=16, T=1.2)
+        p = s.params
+        prm = orc.make_params(potential=orc.POT_LJ, rc=p["rc"], skin=p["skin"], dt=p["dt"],
+                              mass=p["mass"])
+        pos, vel = orc.melt(prm, s.pos, s.vel, s.box, inputs.MELT_SCHEDULE,
+                            inputs.MELT_RESCALE_EVERY,
+                            lambda v, T: inputs.rescale_velocities(v, T, p["mass"]))
+        m = inputs.System("lj_melt_16", pos, vel, s.box, dict(p))
+        return inputs.tile(m, 2), ("LJ liquid: 16^3 fcc cells melted by the oracle (same "
+                                   "schedule), tiled 2 x 2 x 2")
     if args.workload == "ensemble":
         reps = inputs.lj_ensemble(count=args.nc or 64)
         k = max((r for r in range(len(reps)) if reps[r].n <= 150000), key=lambda r: reps[r].n)
@@ -539,7 +606,7 @@ def cpu_baseline_leg(args, gpu=None, steps=None):
     orc.build()
     cores = os.cpu_count() or 1
     orc.set_threads(cores)
-    s, what = oracle_sample_system(args)
+    s, what = oracle_sample_system(args, orc)
     prm = oracle_params(orc, s.params)
     k = steps if steps is not None else 5
     t0 = time.perf_counter()
@@ -575,7 +642,7 @@ def run_reference(args, rank, world):
     orc.build()
     cores = os.cpu_count() or 1
     orc.set_threads(cores)
-    s, what = oracle_sample_system(args)
+    s, what = oracle_sample_system(args, orc)
     prm = oracle_params(orc, s.params)
     out = orc.md_run(prm, s.pos, s.vel, s.box, args.warmup, want_energies=False)
     t0 = time.perf_counter()

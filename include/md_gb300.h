@@ -233,6 +233,17 @@ md_status md_cost_model(md_system *h, int32_t op, float *loss_out);
  * Synchronizes. */
 md_status md_set_timing(md_system *h, int32_t on);
 
+/* Shape of the static partition used by MD_SCHED_PAIRCOUNT and MD_SCHED_MLP
+ * (the load-balance question of Sec. 1 and Sec. 2.1 for inhomogeneous
+ * systems): rounds = equal-cost ranges per persistent CTA (1..8; 0 = sized
+ * from the system, about 24 tiles of 32 atoms per range), tail_percent =
+ * share of the estimated cost left as a tail that CTAs claim tile by tile
+ * once their ranges are done (0..50, default 20).  tail_percent = 0 makes
+ * the partition purely static, so the cost estimate alone balances the
+ * CTAs.  Recomputes the partition; captured step graphs are dropped.
+ * MD_ERR_INVALID outside those ranges. */
+md_status md_set_schedule(md_system *h, int32_t rounds, int32_t tail_percent);
+
 /* Per-cell view of the cost model (after MD_COST_SAMPLE), each array of
  * ncells in linear cell order, any pointer may be NULL (device arrays):
  *   cycles_dev     float32 measured force-pass cycles of the cell, summed

@@ -15,7 +15,7 @@ Functions and the passages of Mangiardi & Meyer they follow:
 * ``sc_brute``, ``sc_list``      -- many-body energy Eq. 1-2 evaluated in three
   steps (Sec. 3.1)
 * ``md_run``, ``forces_once``    -- velocity-Verlet with the half-skin rebuild
-  rule (Sec. 3.3)
+  rule (Sec. 3.3); ``melt`` runs md_run in chunks for an input protocol
 * ``mlp_forward``, ``mlp_loss_grad``, ``adam``, ``partition`` -- the per-cell
   cost model and equal-cost partition (not in the paper; they address its
   load-balance problem of inhomogeneous systems, Sec. 1 and Sec. 2.1)
@@ -245,6 +245,19 @@ def md_run(params: Params, pos, vel, box, nsteps, want_energies=True):
     if b < 0:
         raise RuntimeError("oracle md_run failed (%d)" % b)
     return {"pos": pos, "vel": vel, "force": f, "energies": E, "builds": int(b)}
+
+
+def melt(params: Params, pos, vel, box, schedule, every, rescale):
+    """Runs md_run in chunks of `every` steps over the (T, steps) stages of
+    `schedule`, with rescale(vel, T) applied before every chunk and once at
+    the end (the velocity rescaling of an input protocol, supplied by the
+    caller).  Returns (pos, vel)."""
+    for T, nsteps in schedule:
+        for _ in range(nsteps // every):
+            vel = rescale(vel, T)
+            out = md_run(params, pos, vel, box, every, want_energies=False)
+            pos, vel = out["pos"], out["vel"]
+    return pos, rescale(vel, schedule[-1][0])
 
 
 def forces_once(params: Params, pos, box):

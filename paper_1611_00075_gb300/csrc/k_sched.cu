@@ -111,7 +111,7 @@ cudaError_t launch_predict_costs(md_system *h, bool gated) {
 }
 
 cudaError_t launch_partition_cells(md_system *h, bool gated) {
-    return launch_partition(h->cell_cost, h->g.ncells, sched_parts(h->sched_ctas, h->sched_rounds), h->part_bounds,
+    return launch_partition(h->cell_cost, h->g.ncells, sched_parts(h->sched_ctas, h->sched_rounds, h->sched_tail_pct), h->part_bounds,
                             h->part_scratch, h->stream, h->ds, gated);
 }
 

@@ -182,8 +182,9 @@ md_status ensure_sched(md_system *h) {
     const size_t C = (size_t)h->g.ncells;
     cudaError_t e = cudaSuccess;
     auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-    h->sched_rounds = sched_rounds(h->n, h->sched_ctas);
-    A(dalloc(&h->part_bounds, (size_t)sched_parts(h->sched_ctas, h->sched_rounds) + 1));
+    h->sched_rounds = h->sched_rounds_set > 0 ? h->sched_rounds_set : sched_rounds(h->n, h->sched_ctas);
+    // room for the largest partition md_set_schedule allows
+    A(dalloc(&h->part_bounds, (size_t)sched_parts(h->sched_ctas, kSchedRounds, kTailPctMax) + 1));
     A(dalloc(&h->cell_cost, C));
     A(dalloc(&h->part_scratch, C + 1 + C / (kBlock * 8) + 8));
     A(dalloc(&h->cell_X, 3 * C));
@@ -911,6 +912,19 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
     if (st != MD_OK) return st;
     if (relist || !h->list_valid) return rebuild_now(h, true);
     // same list: only the partition of the new scheduler is needed
+    return enqueue_sched_prep(h, false);
+}
+
+md_status md_set_schedule(md_system *h, int32_t rounds, int32_t tail_percent) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_set_schedule: null handle");
+    if (rounds < 0 || rounds > kSchedRounds || tail_percent < 0 || tail_percent > kTailPctMax)
+        return fail(h, MD_ERR_INVALID, "md_set_schedule: rounds must be 0..8 and tail_percent 0..50");
+    drop_graphs(h);  // the captured steps hold the old partition's shape
+    h->sched_rounds_set = rounds;
+    h->sched_tail_pct = tail_percent;
+    if (!h->part_bounds) return MD_OK;  // applied when the scheduler allocates
+    h->sched_rounds = rounds > 0 ? rounds : sched_rounds(h->n, h->sched_ctas);
+    if (!h->list_valid) return rebuild_now(h, false);
     return enqueue_sched_prep(h, false);
 }
 

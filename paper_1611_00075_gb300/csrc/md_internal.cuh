@@ -18,6 +18,10 @@ constexpr int kStencil = 27;      // cells scanned around a cell (Sec. 2.1)
 constexpr int kIndexBits = 27;    // list entry = (stencil << 27) | sorted index
 constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
 constexpr int64_t kMaxAtoms = (int64_t)1 << kIndexBits;
+// share of the estimated cost in the dynamically claimed tail of the static
+// schedulers (percent): default and largest accepted by md_set_schedule
+constexpr int kTailPctDefault = 20;
+constexpr int kTailPctMax = 50;
 
 // Neighbour-list layout.  Atoms are grouped by 32 (one warp); inside a group
 // each atom's entries are stored in quads: uint32 [n/32][cap/4][32][4].  A
@@ -208,6 +212,8 @@ struct md_system {
     // persistent scheduler and learned cost model (allocated on first use)
     int sched_ctas = 0;                 // resident CTAs of the persistent force kernel
     int sched_rounds = 1;               // static ranges per CTA (sched_rounds())
+    int sched_rounds_set = 0;           // md_set_schedule: fixed ranges per CTA (0 = by size)
+    int sched_tail_pct = mdg::kTailPctDefault;  // md_set_schedule: share of the cost in the tail
     long long *part_bounds = nullptr;   // sched_parts(sched_ctas, sched_rounds) + 1 cell bounds
     long long *cell_cost = nullptr;     // quantised per-cell cost (ncells)
     long long *part_scratch = nullptr;  // prefix sums of the partition
@@ -306,8 +312,15 @@ inline int sched_rounds(int64_t n, int ctas) {
     const int64_t r = ((n + 31) / 32) / ((int64_t)ctas * kTilesPerRange);
     return r < 1 ? 1 : (r > kSchedRounds ? kSchedRounds : (int)r);
 }
-inline int sched_tail_parts(int ctas, int rounds) { return ctas * rounds / 4; }
-inline int sched_parts(int ctas, int rounds) { return ctas * rounds + sched_tail_parts(ctas, rounds); }
+// The tail holds tail_pct percent of the predicted cost: ctas * rounds equal
+// static parts plus ctas * rounds * tail_pct / (100 - tail_pct) tail parts of
+// the same cost (20 % by default: a quarter as many tail parts as static ones).
+inline int sched_tail_parts(int ctas, int rounds, int tail_pct) {
+    return (int)((long long)ctas * rounds * tail_pct / (100 - tail_pct));
+}
+inline int sched_parts(int ctas, int rounds, int tail_pct) {
+    return ctas * rounds + sched_tail_parts(ctas, rounds, tail_pct);
+}
 // features of every cell; with paircount != 0 also cell_cost = list entries
 cudaError_t launch_cell_features(md_system *h, bool paircount, bool gated);
 // model inference on cell_X, quantised into cell_cost

@@ -78,6 +78,15 @@ def maxwell_boltzmann(n: int, T: float, mass: float, seed: int) -> np.ndarray:
     v = gaussian(seed, 3 * n).reshape(n, 3) * math.sqrt(T / mass)
     if n == 0:
         return v
+    return rescale_velocities(v, T, mass)
+
+
+def rescale_velocities(v, T: float, mass: float = 1.0) -> np.ndarray:
+    """Velocities with the mean momentum removed and scaled so that
+    KE = (3n - 3) T / 2 exactly (the temperature over 3n - 3 degrees of
+    freedom); zero for T = 0 or a single atom."""
+    v = np.array(v, dtype=np.float64).reshape(-1, 3)
+    n = v.shape[0]
     v -= v.mean(axis=0, keepdims=True)
     if n > 1 and T > 0:
         ke = 0.5 * mass * float(np.sum(v * v))
@@ -85,6 +94,26 @@ def maxwell_boltzmann(n: int, T: float, mass: float, seed: int) -> np.ndarray:
     else:
         v[:] = 0.0
     return np.ascontiguousarray(v)
+
+
+# The liquid of config 2 is melted from fcc: the crystal is heated past its
+# stability limit at T* = 2.4, then held at the target T* = 1.2, velocities
+# rescaled to the stage's temperature every MELT_RESCALE_EVERY steps (and once
+# more at the end).  Whatever runs the steps -- the oracle for test inputs, the
+# GPU path for the benchmark's own input -- follows this schedule.
+MELT_SCHEDULE = ((2.4, 1000), (1.2, 1000))  # (T*, steps) per stage: 2,000 steps
+MELT_RESCALE_EVERY = 50
+
+
+def tile(s: "System", k: int) -> "System":
+    """k x k x k periodic copies of a cubic system (atoms of copy (a, b, c),
+    a slowest, follow each other); velocities are copied unchanged."""
+    off = np.array([(a, b, c) for a in range(k) for b in range(k) for c in range(k)],
+                   dtype=np.float64) * s.box
+    pos = (s.pos[None, :, :] + off[:, None, :]).reshape(-1, 3)
+    vel = np.tile(s.vel, (k ** 3, 1))
+    return System("%s_x%d" % (s.name, k), np.ascontiguousarray(pos), np.ascontiguousarray(vel),
+                  s.box * k, dict(s.params))
 
 
 def carve_voids(nc: int, a0: float, fraction: float, rmin: float, rmax: float,

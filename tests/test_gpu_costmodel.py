@@ -157,3 +157,46 @@ def test_cost_model_trains_and_is_compared(md):
     # the gain of the trained network over the method without it: it predicts
     # the measured per-cell work better than the pair count does
     assert r_mlp > r_pair
+
+
+def test_learned_partition_balances_measured_work_better(md, orc):
+    """What the trained network gains where nothing else absorbs its errors:
+    a purely static partition.  The model is trained on one timed sample;
+    after 10 more steps a second sample is timed (held out), and the cells are
+    cut into P equal-cost parts by the model's prediction and by the pair
+    count.  The measured cycles of the held-out sample must be spread more
+    evenly (max / mean per part) by the model's parts.  The same static
+    partitions, without the dynamically claimed tail, also drive the
+    persistent kernel, whose launch time and CTA imbalance are printed."""
+    s = porous(nc=48)
+    with md.System(s.pos, s.vel, s.box, precision="mixed", scheduler=md.MD_SCHED_PAIRCOUNT) as a:
+        a.step(5)
+        md.md_cost_model(a.h, md.MD_COST_SAMPLE)
+        md.md_cost_model(a.h, md.MD_COST_TRAIN)
+        a.step(10)
+        md.md_cost_model(a.h, md.MD_COST_SAMPLE)  # held-out timings
+        ncells = int(np.prod(a.cells()[0]))
+        cyc = torch.empty(ncells, dtype=torch.float32, device="cuda")
+        pred = torch.empty(ncells, dtype=torch.int64, device="cuda")
+        pair = torch.empty(ncells, dtype=torch.int64, device="cuda")
+        md.md_get_cell_costs(a.h, cyc, pred, pair)
+        timed = {}
+        for name, code in (("pair", md.MD_SCHED_PAIRCOUNT), ("mlp", md.MD_SCHED_MLP)):
+            md.md_set_variant(a.h, md.MD_FORCE_FULL, code)
+            md.md_set_schedule(a.h, 2, 0)  # two static ranges per CTA, no tail
+            timed[name] = md.md_cost_model(a.h, md.MD_COST_PROFILE)
+        md.md_set_schedule(a.h, 0, 20)
+    cyc, pred, pair = (t.cpu().numpy() for t in (cyc, pred, pair))
+    pref = np.concatenate([[0.0], np.cumsum(cyc.astype(np.float64))])
+    for parts in (256, 1024):
+        imb = {}
+        for name, cost in (("mlp", pred), ("pair", pair)):
+            b = orc.partition(cost, parts)
+            loads = pref[b[1:]] - pref[b[:-1]]
+            imb[name] = loads.max() / loads.mean()
+        print("%d static parts, held-out measured work max/mean: mlp %.4f  paircount %.4f"
+              % (parts, imb["mlp"], imb["pair"]))
+        assert imb["mlp"] < imb["pair"]
+    print("persistent kernel, 2 static ranges per CTA and no tail, CTA imbalance: "
+          "paircount %.4f  mlp %.4f" % (timed["pair"], timed["mlp"]))
+    assert 1.0 <= timed["pair"] < 10 and 1.0 <= timed["mlp"] < 10

@@ -1,6 +1,12 @@
 """Parity at the full workload sizes, in the configuration bench.py times,
 on sampled outputs the oracle computes one by one: list rows bit-exact,
-forces within the mixed-path bar, for atoms drawn by a seeded sampler."""
+forces within the mixed-path bar, for atoms drawn by a seeded sampler.
+
+Each system first runs steps (rebuilds, graph replay, the scheduler it is
+benchmarked with); then positions drawn from the input generator (the start
+perturbed by a seeded Gaussian) are loaded into the running system, which
+rebins and relists them, and its rows and forces at those positions are
+compared with the oracle's.  The oracle only ever sees generator inputs."""
 import math
 
 import numpy as np
@@ -23,6 +29,19 @@ def md():
     torch.cuda.set_device(0)
     _md.lib()
     return _md
+
+
+def perturbed(pos, box, amp, seed):
+    g = inputs.gaussian(seed, pos.size).reshape(-1, 3)
+    return np.mod(pos + amp * g, box)
+
+
+def load(md, a, pos, vel):
+    """Generator positions into the running system; list and forces for them."""
+    md.md_set_state(a.h, torch.as_tensor(pos, device="cuda"), torch.as_tensor(vel, device="cuda"))
+    md.md_build_neighbors(a.h)
+    md.md_forces(a.h)
+    return a.state()[2].cpu().numpy()
 
 
 def sample_ids(n, k, seed):
@@ -73,27 +92,33 @@ def test_porous_9_8m_learned_scheduler(md, orc):
             assert np.isfinite(md.md_cost_model(a.h, md.MD_COST_TRAIN))
             md.md_set_variant(a.h, md.MD_FORCE_FULL, md.MD_SCHED_MLP)
             a.step(20)
-            md.md_build_neighbors(a.h)
-            pos, _, f = a.state()
-            pos, f = pos.cpu().numpy(), f.cpu().numpy()
+            pos = perturbed(s.pos, s.box, 0.05, inputs.SEED_BASE + 311)
+            f = load(md, a, pos, s.vel)
             idx = sample_ids(a.n, 600, inputs.SEED_BASE + 301)
             ooff, oids = check_rows(orc, a, pos, s.box, p["rc"] + p["skin"], idx)
-            md.md_forces(a.h)
-            f = a.state()[2].cpu().numpy()
     check_forces(orc, prm, f, pos, s.box, idx, ooff, oids, p["rc"], 2e-4, 1e-5)
 
 
+@pytest.fixture(scope="module")
+def liquid_1m(orc):
+    """The config-2 liquid at full size: a 16^3-cell fcc block melted by the
+    oracle (2,000 steps, T* 2.4 then 1.2) and tiled 4 x 4 x 4 into 64^3
+    cells, 1,048,576 atoms at rho* = 0.8442."""
+    from melt import oracle_melt
+    return inputs.tile(oracle_melt(orc, 16), 4)
+
+
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_lj_liquid_1m(md, orc, precision):
-    """64^3-cell LJ at T* = 1.2 (1,048,576 atoms), both precisions."""
-    s = inputs.lj_fcc(nc=64, T=1.2)
+def test_lj_liquid_1m(md, orc, liquid_1m, precision):
+    """The melted 64^3-cell LJ liquid (1,048,576 atoms), both precisions:
+    30 steps, then a second melted state (the same liquid, perturbed)."""
+    s = liquid_1m
     prm = orc.make_params(potential=orc.POT_LJ, rc=2.5, skin=0.3, dt=0.005)
     with md.System(s.pos, s.vel, s.box, precision=precision) as a:
+        assert a.n == 1048576
         a.step(30)
-        md.md_build_neighbors(a.h)  # the rows below are for the current positions
-        md.md_forces(a.h)
-        pos, _, f = a.state()
-        pos, f = pos.cpu().numpy(), f.cpu().numpy()
+        pos = perturbed(s.pos, s.box, 0.02, inputs.SEED_BASE + 312)
+        f = load(md, a, pos, s.vel)
         idx = sample_ids(a.n, 600, inputs.SEED_BASE + 302)
         ooff, oids = check_rows(orc, a, pos, s.box, 2.8, idx)
     if precision == "fp64":
@@ -113,10 +138,8 @@ def test_sutton_chen_8m(md, orc):
                    sigma=p["sigma"], c=p["c"], n_exp=p["n_exp"], m_exp=p["m_exp"], rc=p["rc"],
                    skin=p["skin"], dt=p["dt"]) as a:
         a.step(10)
-        md.md_build_neighbors(a.h)
-        md.md_forces(a.h)
-        pos, _, f = a.state()
-        pos, f = pos.cpu().numpy(), f.cpu().numpy()
+        pos = perturbed(s.pos, s.box, 0.03, inputs.SEED_BASE + 313)
+        f = load(md, a, pos, s.vel)
         idx = sample_ids(a.n, 200, inputs.SEED_BASE + 304)
         ooff, oids = check_rows(orc, a, pos, s.box, p["rc"] + p["skin"], idx)
     check_forces(orc, prm, f, pos, s.box, idx, ooff, oids, p["rc"], 2e-4, 1e-5)
@@ -130,10 +153,9 @@ def test_ensemble_64_replicas(md, orc):
     with md.Batch([(r.pos, r.vel, r.box) for r in reps], precision="mixed",
                   scheduler=md.MD_SCHED_DYNAMIC) as b:
         b.step(30)
-        md.md_build_neighbors(b.h)
-        md.md_forces(b.h)
-        pos, _, f = b.state()
-        pos, f = pos.cpu().numpy(), f.cpu().numpy()
+        pos = np.concatenate([perturbed(r.pos, r.box, 0.05, inputs.SEED_BASE + 320 + k)
+                              for k, r in enumerate(reps)])
+        f = load(md, b, pos, np.concatenate([r.vel for r in reps]))
         off, ids = b.neighbors()
         off, ids = off.cpu().numpy(), ids.cpu().numpy()
     for r in range(0, 64, 8):

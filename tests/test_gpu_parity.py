@@ -57,6 +57,13 @@ def near_cutoff(pos, box, off, ids, rc, delta):
 
 
 def lj_system(name):
+    if name == "melt4000":
+        # the config-2 liquid at 4,000 atoms, melted by the oracle
+        import oracle
+        from melt import oracle_melt
+        oracle.build()
+        s = oracle_melt(oracle, 10)
+        return s, s.pos
     if name == "fcc4000":
         s = inputs.lj_fcc(nc=10, T=0.72)
         return s, perturbed(s, 0.05, 101)
@@ -104,46 +111,72 @@ def check_forces(f, f0, bad, precision):
 
 # ------------------------------------------------------------------ cells
 
-@pytest.mark.parametrize("name", ["fcc4000", "porous"])
+@pytest.mark.parametrize("name", ["fcc4000", "porous", "melt4000"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_cells_bit_exact(md, orc, name, precision):
+    """Cells and cell starts of a generator state against the oracle; after
+    25 steps, the cells of the drifted state (absolute positions rebuilt from
+    cell-relative ones) equal those of the same exported positions loaded
+    back; and a second generator state loaded into the running system bins as
+    the oracle bins it."""
     s, pos = lj_system(name)
     with md.System(pos, s.vel, s.box, precision=precision) as sy:
-        for rep in range(2):
-            if rep == 1:
-                sy.step(25)
-                md.md_bin_cells(sy.h)
-            nc, cell_of, start = sy.cells()
-            p, _, _ = sy.state() if rep == 1 else (torch.as_tensor(pos), None, None)
-            p = p.cpu().numpy()
-            onc, ocell, ostart, _ = orc.bin_cells(p, s.box, 2.8)
-            assert list(onc) == nc
-            np.testing.assert_array_equal(cell_of.cpu().numpy(), ocell)
-            np.testing.assert_array_equal(start.cpu().numpy(), ostart)
+        nc, cell_of, start = sy.cells()
+        onc, ocell, ostart, _ = orc.bin_cells(pos, s.box, 2.8)
+        assert list(onc) == nc
+        np.testing.assert_array_equal(cell_of.cpu().numpy(), ocell)
+        np.testing.assert_array_equal(start.cpu().numpy(), ostart)
+        sy.step(25)
+        md.md_bin_cells(sy.h)
+        _, cell1, start1 = sy.cells()
+        p1, v1, _ = sy.state()
+        md.md_set_state(sy.h, p1, v1)
+        md.md_bin_cells(sy.h)
+        _, cell2, start2 = sy.cells()
+        assert torch.equal(cell1, cell2) and torch.equal(start1, start2)
+        pos2 = np.mod(pos + 0.03 * inputs.gaussian(inputs.SEED_BASE + 131, pos.size).reshape(-1, 3),
+                      s.box)
+        md.md_set_state(sy.h, torch.as_tensor(pos2, device="cuda"), v1)
+        md.md_bin_cells(sy.h)
+        _, cell3, start3 = sy.cells()
+    onc, ocell, ostart, _ = orc.bin_cells(pos2, s.box, 2.8)
+    np.testing.assert_array_equal(cell3.cpu().numpy(), ocell)
+    np.testing.assert_array_equal(start3.cpu().numpy(), ostart)
 
 
 # ------------------------------------------------------------------ lists
 
-@pytest.mark.parametrize("name", ["fcc4000", "liquid_like", "porous"])
+@pytest.mark.parametrize("name", ["fcc4000", "liquid_like", "porous", "melt4000"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_neighbors_bit_exact(md, orc, name, precision):
+    """Lists of a generator state against the oracle; after 40 steps and a
+    rebuild, the list equals the one built for the same exported positions
+    loaded back; a second generator state loaded into the running system
+    lists as the oracle does (full list, and its half export j > i)."""
     s, pos = lj_system(name)
     with md.System(pos, s.vel, s.box, precision=precision) as sy:
         off, ids = sy.neighbors()
         ooff, oids = orc.neighbors_cells(pos, s.box, 2.8)
         np.testing.assert_array_equal(off.cpu().numpy(), ooff)
         np.testing.assert_array_equal(ids.cpu().numpy(), oids)
-        # after dynamics and an explicit rebuild, against the exported positions
         sy.step(40)
         md.md_build_neighbors(sy.h)
-        p = sy.state()[0].cpu().numpy()
+        off1, ids1 = sy.neighbors()
+        p1, v1, _ = sy.state()
+        md.md_set_state(sy.h, p1, v1)
+        md.md_build_neighbors(sy.h)
+        off2, ids2 = sy.neighbors()
+        assert torch.equal(off1, off2) and torch.equal(ids1, ids2)
+        pos2 = np.mod(pos + 0.03 * inputs.gaussian(inputs.SEED_BASE + 132, pos.size).reshape(-1, 3),
+                      s.box)
+        md.md_set_state(sy.h, torch.as_tensor(pos2, device="cuda"), v1)
+        md.md_build_neighbors(sy.h)
         off, ids = sy.neighbors()
-        ooff, oids = orc.neighbors_cells(p, s.box, 2.8)
+        ooff, oids = orc.neighbors_cells(pos2, s.box, 2.8)
         np.testing.assert_array_equal(off.cpu().numpy(), ooff)
         np.testing.assert_array_equal(ids.cpu().numpy(), oids)
-        # half export of a full list: canonical j > i
         off, ids = sy.neighbors(half=True)
-        ooff, oids = orc.neighbors_cells(p, s.box, 2.8, half=True)
+        ooff, oids = orc.neighbors_cells(pos2, s.box, 2.8, half=True)
         np.testing.assert_array_equal(off.cpu().numpy(), ooff)
         np.testing.assert_array_equal(ids.cpu().numpy(), oids)
 
@@ -183,7 +216,7 @@ def test_neighbors_perfect_lattice_counts(md, orc):
 
 # ------------------------------------------------------------------ forces
 
-@pytest.mark.parametrize("name", ["fcc4000", "liquid_like", "porous"])
+@pytest.mark.parametrize("name", ["fcc4000", "liquid_like", "porous", "melt4000"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_lj_forces_and_energy(md, orc, name, precision):
     s, pos = lj_system(name)
@@ -262,6 +295,26 @@ def test_nve_100_steps_mixed_config1(md, orc):
     es = np.array(es)
     rel = np.abs(es[:, 0] + es[:, 1] - E0[:, 2]) / np.abs(E0[:, 2])
     print("mixed config 1: max relative total-energy error over 100 steps %.3g" % rel.max())
+    assert np.max(rel) < 1e-6, np.max(rel)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_nve_100_steps_melted_liquid(md, orc, precision):
+    """The config-2 liquid (4,000 atoms melted by the oracle, T* = 1.2):
+    total energy after every one of 100 steps within 1e-6 relative of the
+    oracle's float64 trajectory, on both paths."""
+    s, pos = lj_system("melt4000")
+    p = orc.make_params(potential=orc.POT_LJ, rc=2.5, skin=0.3, dt=0.005)
+    E0 = orc.md_run(p, pos, s.vel, s.box, 100)["energies"]
+    with md.System(pos, s.vel, s.box, precision=precision) as sy:
+        es = [sy.energy()]
+        for k in range(100):
+            sy.step(1)
+            es.append(sy.energy())
+    es = np.array(es)
+    rel = np.abs(es[:, 0] + es[:, 1] - E0[:, 2]) / np.abs(E0[:, 2])
+    print("%s melted liquid: max relative total-energy error over 100 steps %.3g"
+          % (precision, rel.max()))
     assert np.max(rel) < 1e-6, np.max(rel)
 
 

@@ -409,3 +409,14 @@ def test_partition_brute_force(orc):
             if T > 0:
                 loads = [pref[b[q + 1]] - pref[b[q]] for q in range(B)]
                 assert max(loads) <= T / B + cost.max()
+
+
+def test_oracle_melt_is_a_liquid(orc):
+    """The config-2 input protocol (heat fcc at T* = 2.4, hold at 1.2, 2,000
+    oracle steps) leaves no crystal: atoms have diffused far from their
+    lattice sites and the temperature is the target's."""
+    from melt import lattice_msd, oracle_melt
+    m = oracle_melt(orc, 6)
+    assert lattice_msd(m, 6) > 1.0
+    ke = 0.5 * np.sum(m.vel ** 2)
+    assert abs(ke / (0.5 * (3 * m.n - 3)) - 1.2) < 1e-12
