@@ -14,6 +14,8 @@ Functions and the passages of Mangiardi & Meyer they follow:
 * ``lj_brute``, ``lj_list``      -- pair forces F = -(1/d) dPhi/dr R (Sec. 2.2)
 * ``sc_brute``, ``sc_list``      -- many-body energy Eq. 1-2 evaluated in three
   steps (Sec. 3.1)
+* ``eam_brute``, ``eam_list``    -- the same with piecewise cubic pair and
+  density functions, the form of the paper's Fe potential (Sec. 3.1, Table 2)
 * ``md_run``, ``forces_once``    -- velocity-Verlet with the half-skin rebuild
   rule (Sec. 3.3); ``melt`` runs md_run in chunks for an input protocol
 * ``mlp_forward``, ``mlp_loss_grad``, ``adam``, ``partition`` -- the per-cell
@@ -37,6 +39,8 @@ _lib = None
 
 POT_LJ = 0
 POT_SC = 1
+POT_EAM = 2
+EAM_MAX_KNOTS = 16
 
 
 def build(force: bool = False) -> str:
@@ -50,16 +54,42 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+class EamTable(C.Structure):
+    """Piecewise embedded-atom functions: Phi(r) = sum_k a_k (r_k - r)^3 and
+    psi(r) = sum_k b_k (s_k - r)^3 over the knots beyond r, and
+    F(rho) = -F_sqrt sqrt(rho) + F_quad rho^2."""
+    _fields_ = [("n_phi", C.c_int32), ("n_psi", C.c_int32),
+                ("phi_r", C.c_double * EAM_MAX_KNOTS), ("phi_a", C.c_double * EAM_MAX_KNOTS),
+                ("psi_r", C.c_double * EAM_MAX_KNOTS), ("psi_a", C.c_double * EAM_MAX_KNOTS),
+                ("F_sqrt", C.c_double), ("F_quad", C.c_double)]
+
+
+def make_eam(phi_r, phi_a, psi_r, psi_a, F_sqrt, F_quad) -> EamTable:
+    t = EamTable()
+    t.n_phi, t.n_psi = len(phi_r), len(psi_r)
+    for k, (r, a) in enumerate(zip(phi_r, phi_a)):
+        t.phi_r[k], t.phi_a[k] = r, a
+    for k, (r, a) in enumerate(zip(psi_r, psi_a)):
+        t.psi_r[k], t.psi_a[k] = r, a
+    t.F_sqrt, t.F_quad = F_sqrt, F_quad
+    return t
+
+
 class Params(C.Structure):
     _fields_ = [("potential", C.c_int32), ("rebuild_every", C.c_int32),
                 ("eps", C.c_double), ("sigma", C.c_double), ("c", C.c_double),
                 ("n_exp", C.c_double), ("m_exp", C.c_double), ("rc", C.c_double),
-                ("skin", C.c_double), ("dt", C.c_double), ("mass", C.c_double)]
+                ("skin", C.c_double), ("dt", C.c_double), ("mass", C.c_double),
+                ("eam", C.POINTER(EamTable))]
 
 
 def make_params(potential=POT_LJ, eps=1.0, sigma=1.0, c=0.0, n_exp=12.0, m_exp=6.0,
-                rc=2.5, skin=0.3, dt=0.005, mass=1.0, rebuild_every=0) -> Params:
-    return Params(potential, rebuild_every, eps, sigma, c, n_exp, m_exp, rc, skin, dt, mass)
+                rc=2.5, skin=0.3, dt=0.005, mass=1.0, rebuild_every=0, eam=None) -> Params:
+    """eam: an EamTable (potential POT_EAM); kept alive by the returned Params."""
+    p = Params(potential, rebuild_every, eps, sigma, c, n_exp, m_exp, rc, skin, dt, mass,
+               C.pointer(eam) if eam is not None else None)
+    p._eam_ref = eam
+    return p
 
 
 def _P(a, dtype):
@@ -91,6 +121,11 @@ def lib():
             L.orc_sc_list.argtypes = [i64, pd, pd, d, d, d, d, d, d, pi64, pi32, pd, pd, pd, pd]
             L.orc_sc_brute.restype = d
             L.orc_sc_brute.argtypes = [i64, pd, pd, d, d, d, d, d, d, pd, pd]
+            L.orc_eam_list.restype = d
+            L.orc_eam_list.argtypes = [i64, pd, pd, C.POINTER(EamTable), d, pi64, pi32, pd, pd,
+                                       pd, pd]
+            L.orc_eam_brute.restype = d
+            L.orc_eam_brute.argtypes = [i64, pd, pd, C.POINTER(EamTable), d, pd, pd]
             L.orc_md_run.restype = i64
             L.orc_md_run.argtypes = [C.POINTER(Params), i64, pd, pd, pd, i64, pd, pd]
             L.orc_forces_once.restype = d
@@ -225,6 +260,30 @@ def sc_brute(pos, box, eps=1.0, a=1.0, c=39.432, n_exp=9.0, m_exp=6.0, rc=2.0):
     rho = np.zeros(pos.shape[0])
     U = lib().orc_sc_brute(pos.shape[0], _P(pos, C.c_double), _P(box, C.c_double), eps, a, c,
                            n_exp, m_exp, rc, _P(f, C.c_double), _P(rho, C.c_double))
+    return U, f, rho
+
+
+def eam_list(pos, box, offsets, ids, table: EamTable, rc):
+    """Returns (U, f, rho, dF, e_atom) from a full list."""
+    pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    ids = np.ascontiguousarray(ids, np.int32)
+    n = pos.shape[0]
+    f = np.zeros_like(pos)
+    rho, dF, e = np.zeros(n), np.zeros(n), np.zeros(n)
+    U = lib().orc_eam_list(n, _P(pos, C.c_double), _P(box, C.c_double), C.byref(table), rc,
+                           _P(offsets, C.c_int64), _P(ids, C.c_int32), _P(f, C.c_double),
+                           _P(rho, C.c_double), _P(dF, C.c_double), _P(e, C.c_double))
+    return U, f, rho, dF, e
+
+
+def eam_brute(pos, box, table: EamTable, rc):
+    """Returns (U, f, rho) over all pairs."""
+    pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
+    f = np.zeros_like(pos)
+    rho = np.zeros(pos.shape[0])
+    U = lib().orc_eam_brute(pos.shape[0], _P(pos, C.c_double), _P(box, C.c_double),
+                            C.byref(table), rc, _P(f, C.c_double), _P(rho, C.c_double))
     return U, f, rho
 
 

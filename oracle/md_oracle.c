@@ -260,6 +260,7 @@ typedef struct {
     double skin;            /* list skin; r_list = rc + skin */
     double dt;              /* time step */
     double mass;            /* atom mass */
+    const struct orc_eam_s *eam;  /* embedded-atom tables (potential 2), else NULL */
 } orc_params;
 
 /* Lennard-Jones, truncated and energy-shifted at r_c:
@@ -441,6 +442,134 @@ double orc_sc_brute(int64_t n, const double *pos, const double *box, double eps,
     return U;
 }
 
+/* Embedded-atom method with piecewise functions, the form of the paper's Fe
+ * potential (Sec. 3.1: pair and density functions that are sums of truncated
+ * cubics, which is why the force step dominates for Fe126 in Table 2):
+ *   Phi(r) = sum_k a_k (r_k - r)^3 for the knots with r < r_k
+ *   psi(r) = sum_k b_k (s_k - r)^3 for the knots with r < s_k
+ *   F(rho) = -A sqrt(rho) + B rho^2
+ * in the many-body form of Eq. 1-2, cut at r_c (every knot <= r_c).  Forces
+ * by differentiating U as for Sutton-Chen:
+ *   f_i = -sum_j [Phi'(r) + (F'(rho_i) + F'(rho_j)) psi'(r)] (r_i - r_j)/r
+ * evaluated in the paper's three steps (Sec. 3.1). */
+typedef struct orc_eam_s {
+    int32_t n_phi, n_psi;
+    double phi_r[16], phi_a[16];
+    double psi_r[16], psi_a[16];
+    double F_sqrt, F_quad;
+} orc_eam;
+
+/* value (*d = derivative) of sum_k c_k (k_k - r)^3 over the knots beyond r */
+static double piecewise_cubic(int nk, const double *knot, const double *c, double r, double *d) {
+    double v = 0.0, dv = 0.0;
+    for (int k = 0; k < nk; ++k) {
+        if (r < knot[k]) {
+            double t = knot[k] - r;
+            v += c[k] * t * t * t;
+            dv += -3.0 * c[k] * t * t;
+        }
+    }
+    if (d) *d = dv;
+    return v;
+}
+static double eam_F(const orc_eam *t, double rho) {
+    return -t->F_sqrt * sqrt(rho) + t->F_quad * rho * rho;
+}
+static double eam_dF(const orc_eam *t, double rho) {
+    double d = 2.0 * t->F_quad * rho;
+    if (rho > 0.0) d += -t->F_sqrt / (2.0 * sqrt(rho));
+    return d;
+}
+
+/* EAM from a full neighbour list; rho_out, dF_out (F'(rho_i)) and e_atom are
+ * optional outputs.  Returns U. */
+double orc_eam_list(int64_t n, const double *pos, const double *box, const orc_eam *t,
+                    double rc, const int64_t *offsets, const int32_t *ids, double *f,
+                    double *rho_out, double *dF_out, double *e_atom) {
+    double rc2 = rc * rc;
+    double *rho = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *dF = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    /* step 1: localization function rho_i (Eq. 2) */
+    #pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n; ++i) {
+        double sum = 0.0;
+        for (int64_t k = offsets[i]; k < offsets[i + 1]; ++k) {
+            double dx, dy, dz;
+            double r2 = pair_r2(pos, box, i, ids[k], &dx, &dy, &dz);
+            if (!(r2 < rc2)) continue;
+            sum += piecewise_cubic(t->n_psi, t->psi_r, t->psi_a, sqrt(r2), NULL);
+        }
+        rho[i] = sum;
+    }
+    /* step 2: embedding derivative, atom loop */
+    for (int64_t i = 0; i < n; ++i) dF[i] = eam_dF(t, rho[i]);
+    /* step 3: pair term and forces */
+    double U = 0.0;
+    #pragma omp parallel for schedule(dynamic, 256) reduction(+ : U)
+    for (int64_t i = 0; i < n; ++i) {
+        double fx = 0.0, fy = 0.0, fz = 0.0, ep = 0.0;
+        for (int64_t k = offsets[i]; k < offsets[i + 1]; ++k) {
+            int64_t j = ids[k];
+            double dx, dy, dz;
+            double r2 = pair_r2(pos, box, i, j, &dx, &dy, &dz);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2), dPhi, dpsi;
+            double Phi = piecewise_cubic(t->n_phi, t->phi_r, t->phi_a, r, &dPhi);
+            piecewise_cubic(t->n_psi, t->psi_r, t->psi_a, r, &dpsi);
+            double g = dPhi + (dF[i] + dF[j]) * dpsi;  /* dU/dr_ij */
+            fx += g * dx / r; fy += g * dy / r; fz += g * dz / r;
+            ep += 0.5 * Phi;
+        }
+        f[3 * i + 0] = fx; f[3 * i + 1] = fy; f[3 * i + 2] = fz;
+        double ei = ep + eam_F(t, rho[i]);
+        if (e_atom) e_atom[i] = ei;
+        U += ei;
+    }
+    if (rho_out) memcpy(rho_out, rho, sizeof(double) * (size_t)n);
+    if (dF_out) memcpy(dF_out, dF, sizeof(double) * (size_t)n);
+    free(rho); free(dF);
+    return U;
+}
+
+/* EAM over all pairs i < j (O(N^2)), same three steps without a list. */
+double orc_eam_brute(int64_t n, const double *pos, const double *box, const orc_eam *t,
+                     double rc, double *f, double *rho_out) {
+    double rc2 = rc * rc;
+    double *rho = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *dF = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j) {
+            double dx, dy, dz;
+            double r2 = pair_r2(pos, box, i, j, &dx, &dy, &dz);
+            if (!(r2 < rc2)) continue;
+            double psi = piecewise_cubic(t->n_psi, t->psi_r, t->psi_a, sqrt(r2), NULL);
+            rho[i] += psi;
+            rho[j] += psi;
+        }
+    double U = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        U += eam_F(t, rho[i]);
+        dF[i] = eam_dF(t, rho[i]);
+    }
+    memset(f, 0, sizeof(double) * 3 * (size_t)n);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j) {
+            double dx, dy, dz;
+            double r2 = pair_r2(pos, box, i, j, &dx, &dy, &dz);
+            if (!(r2 < rc2)) continue;
+            double r = sqrt(r2), dPhi, dpsi;
+            double Phi = piecewise_cubic(t->n_phi, t->phi_r, t->phi_a, r, &dPhi);
+            piecewise_cubic(t->n_psi, t->psi_r, t->psi_a, r, &dpsi);
+            double g = dPhi + (dF[i] + dF[j]) * dpsi;
+            f[3 * i + 0] += g * dx / r; f[3 * i + 1] += g * dy / r; f[3 * i + 2] += g * dz / r;
+            f[3 * j + 0] -= g * dx / r; f[3 * j + 1] -= g * dy / r; f[3 * j + 2] -= g * dz / r;
+            U += Phi;
+        }
+    if (rho_out) memcpy(rho_out, rho, sizeof(double) * (size_t)n);
+    free(rho); free(dF);
+    return U;
+}
+
 /* Forces (and per-atom energies) of a sample of atoms, for systems too large
  * for the all-atom routines: the 27 cells around each sampled atom are
  * scanned for pairs with r^2 < r_c^2 (same definitions as above).  For the
@@ -519,6 +648,36 @@ int orc_forces_sample(const orc_params *p, int64_t n, const double *pos, const d
                 fx -= fs * dx; fy -= fs * dy; fz -= fs * dz;
                 ei += 0.5 * (lj_phi(r2, p->eps, p->sigma) - shift);
             }
+        } else if (p->potential == 2) {
+            /* EAM: step 1 for i and each neighbour j, step 2 for each, step 3 for i */
+            const orc_eam *t = p->eam;
+            double rho_i = 0.0;
+            for (int64_t q = 0; q < cnt; ++q)
+                rho_i += piecewise_cubic(t->n_psi, t->psi_r, t->psi_a,
+                                         sqrt(orc_pair_r2(pos, box, i, nb[q])), NULL);
+            double dFi = eam_dF(t, rho_i);
+            double ep = 0.0;
+            for (int64_t q = 0; q < cnt; ++q) {
+                int64_t j = nb[q];
+                int64_t c2 = cell_neighbors(j, pos, box, p->rc, ncell, cell_of, start, order,
+                                            nb2, CAP);
+                if (c2 > CAP) { bad = 1; break; }
+                qsort(nb2, (size_t)c2, sizeof(int64_t), cmp_i64);
+                double rho_j = 0.0;
+                for (int64_t u = 0; u < c2; ++u)
+                    rho_j += piecewise_cubic(t->n_psi, t->psi_r, t->psi_a,
+                                             sqrt(orc_pair_r2(pos, box, j, nb2[u])), NULL);
+                double dFj = eam_dF(t, rho_j);
+                double dx, dy, dz;
+                double r2 = pair_r2(pos, box, i, j, &dx, &dy, &dz);
+                double r = sqrt(r2), dPhi, dpsi;
+                double Phi = piecewise_cubic(t->n_phi, t->phi_r, t->phi_a, r, &dPhi);
+                piecewise_cubic(t->n_psi, t->psi_r, t->psi_a, r, &dpsi);
+                double g = dPhi + (dFi + dFj) * dpsi;
+                fx += g * dx / r; fy += g * dy / r; fz += g * dz / r;
+                ep += 0.5 * Phi;
+            }
+            ei = ep + eam_F(t, rho_i);
         } else {
             /* step 1 for i and each neighbour j, step 2 for each, step 3 for i */
             double rho_i = 0.0;
@@ -619,6 +778,8 @@ static double forces(const orc_params *p, int64_t n, const double *pos, const do
                      const orc_list *L, double *f) {
     if (p->potential == 0)
         return orc_lj_list(n, pos, box, p->eps, p->sigma, p->rc, L->offsets, L->ids, f, NULL);
+    if (p->potential == 2)
+        return orc_eam_list(n, pos, box, p->eam, p->rc, L->offsets, L->ids, f, NULL, NULL, NULL);
     return orc_sc_list(n, pos, box, p->eps, p->sigma, p->c, p->n_exp, p->m_exp, p->rc,
                        L->offsets, L->ids, f, NULL, NULL, NULL);
 }

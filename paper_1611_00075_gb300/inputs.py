@@ -12,6 +12,8 @@ are not available, so these stand in for them:
 * ``lj_porous``   -- fcc solid with random spherical voids (stands in for the
   inhomogeneous Porous and PnC systems)
 * ``sc_fcc``      -- many-body fcc metal at its lattice constant
+* ``eam_bcc``     -- bcc metal under a piecewise embedded-atom potential
+  (stands in for Fe126)
 * ``lj_ensemble`` -- a batch of independent replicas of uneven size
 
 Random numbers come from splitmix64 (Steele, Lea & Flood 2014): output k of a
@@ -31,6 +33,7 @@ _M1 = np.uint64(0xBF58476D1CE4E5B9)
 _M2 = np.uint64(0x94D049BB133111EB)
 
 FCC_BASIS = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.0], [0.5, 0.0, 0.5], [0.0, 0.5, 0.5]])
+BCC_BASIS = np.array([[0.0, 0.0, 0.0], [0.5, 0.5, 0.5]])
 
 
 def splitmix64(seed: int, count: int, offset: int = 0) -> np.ndarray:
@@ -61,14 +64,19 @@ def gaussian(seed: int, count: int, offset: int = 0) -> np.ndarray:
     return g[:count]
 
 
-def fcc_lattice(nc, a0: float) -> np.ndarray:
+def fcc_lattice(nc, a0: float, basis=FCC_BASIS) -> np.ndarray:
     """Sites a0 * (cell + basis_k) of an nc[0] x nc[1] x nc[2] fcc block,
     ordered by (ix, iy, iz, k)."""
     nx, ny, nz = (nc, nc, nc) if np.isscalar(nc) else nc
     ix, iy, iz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
     cells = np.stack([ix, iy, iz], axis=-1).reshape(-1, 1, 3).astype(np.float64)
-    pos = a0 * (cells + FCC_BASIS[None, :, :])
+    pos = a0 * (cells + basis[None, :, :])
     return np.ascontiguousarray(pos.reshape(-1, 3))
+
+
+def bcc_lattice(nc, a0: float) -> np.ndarray:
+    """Sites a0 * (cell + basis_k) of a bcc block, ordered by (ix, iy, iz, k)."""
+    return fcc_lattice(nc, a0, BCC_BASIS)
 
 
 def maxwell_boltzmann(n: int, T: float, mass: float, seed: int) -> np.ndarray:
@@ -213,6 +221,32 @@ def sc_fcc(nc: int = 128, a0: float = 1.0, seed: int = SEED_BASE + 4, **over) ->
                   dict(potential="sc", eps=p["eps"], sigma=p["a"], c=p["c"], n_exp=p["n_exp"],
                        m_exp=p["m_exp"], rc=p["rc"], skin=p["skin"], dt=p["dt"],
                        mass=p["mass"], T=p["T"]))
+
+
+# A synthetic many-body metal with the piecewise embedded-atom form of the
+# paper's Fe potential (its tables are not public here): bcc with a0 = 1,
+# pair and density functions that are sums of truncated cubics on knots
+# (Phi: seven knots, psi: one), F(rho) = -F_sqrt sqrt(rho) + F_quad rho^2.
+# The pair knots' coefficients were fitted to a Morse shape (depth 0.25,
+# stiffness 4.5) whose minimum was placed so that the bcc lattice with
+# a0 = 1 sits at its energy minimum (cohesive energy -3.008 per atom); the
+# cutoff 1.8 keeps shells 1-5 (58 neighbours).  T* = 0.018 is the ratio of
+# 300 K to iron's cohesive energy (0.026 / 4.28 eV) times 3.008.
+EAM_FE_LIKE = dict(phi_r=(0.9, 1.05, 1.2, 1.35, 1.5, 1.65, 1.8),
+                   phi_a=(160.6, -23.87, 26.45, -11.78, 5.545, -1.215, -0.5516),
+                   psi_r=(1.8,), psi_a=(1.0,), F_sqrt=0.5, F_quad=0.0,
+                   rc=1.8, skin=0.15, T=0.018, dt=0.002, mass=1.0)
+
+
+def eam_bcc(nc: int = 126, a0: float = 1.0, seed: int = SEED_BASE + 6, **over) -> System:
+    """bcc crystal of nc^3 cells (2 nc^3 atoms) under the piecewise EAM
+    (126^3 cells: 4,000,752 atoms, the size of the paper's Fe126)."""
+    p = dict(EAM_FE_LIKE)
+    p.update(over)
+    pos = bcc_lattice(nc, a0)
+    vel = maxwell_boltzmann(pos.shape[0], p["T"], p["mass"], seed)
+    box = np.full(3, nc * a0)
+    return System("eam_bcc_%d" % nc, pos, vel, box, dict(potential="eam", **p))
 
 
 def lj_ensemble(count: int = 64, nmin: int = 1000, nmax: int = 200000,
