@@ -69,7 +69,8 @@ def parse_args(argv):
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="porous", choices=["porous", "fcc", "sc", "ensemble"])
+    ap.add_argument("--workload", default="porous",
+                    choices=["porous", "fcc", "sc", "eam", "ensemble"])
     ap.add_argument("--compare-steps", type=int, default=100,
                     help="steps timed for each other scheduler (0 = skip the comparison)")
     ap.add_argument("--scheduler", default="mlp",
@@ -135,6 +136,12 @@ def make_workload(name: str, nc: int = 0):
                 "(2,000 untimed mixed-precision steps, velocities rescaled every 50 steps to "
                 "T*=2.4 for 1,000 steps, then to T*=1.2), T*=1.2, rc=2.5, skin=0.3, dt=0.005, "
                 "half-skin rebuilds" % (k, s.n))
+    elif name == "eam":
+        k = nc or 126
+        s = inputs.eam_bcc(nc=k)
+        desc = ("piecewise embedded-atom bcc metal (Fe126 size) %d^3 cells = %d atoms, a0=1, "
+                "Phi: 7 truncated-cubic knots, psi: 1, F = -0.5 sqrt(rho), rc=1.8, skin=0.15, "
+                "T*=0.018, dt=0.002" % (k, s.n))
     else:
         k = nc or 128
         s = inputs.sc_fcc(nc=k)
@@ -152,10 +159,14 @@ def make_workload_desc(args):
 
 def md_kwargs(s):
     p = dict(s.params)
-    kw = dict(eps=p["eps"], sigma=p["sigma"], rc=p["rc"], skin=p["skin"], dt=p["dt"],
-              mass=p["mass"], potential=p["potential"])
+    kw = dict(eps=p.get("eps", 1.0), sigma=p.get("sigma", 1.0), rc=p["rc"], skin=p["skin"],
+              dt=p["dt"], mass=p["mass"], potential=p["potential"])
     if p["potential"] == "sc":
         kw.update(c=p["c"], n_exp=p["n_exp"], m_exp=p["m_exp"])
+    if p["potential"] == "eam":
+        kw.update(eam={k: p[k] for k in ("phi_r", "phi_a", "psi_r", "psi_a", "F_sqrt",
+                                         "F_quad")})
+        del kw["eps"], kw["sigma"]
     return kw
 
 
@@ -246,6 +257,8 @@ def run_gpu(args, rank, world, local):
             args.scheduler = "grid"  # measured faster than the dynamic queue for batches
         args.fp64_steps = 0  # batches run the mixed path; per-replica fp64 is not the comparison
     kw = md_kwargs(s)
+    if kw["potential"] != "lj" and args.scheduler != "grid":
+        args.scheduler = "grid"  # the persistent schedulers drive the Lennard-Jones kernel
     sched = {"grid": md.MD_SCHED_GRID, "paircount": md.MD_SCHED_PAIRCOUNT,
              "mlp": md.MD_SCHED_MLP, "dynamic": md.MD_SCHED_DYNAMIC}[args.scheduler]
 
@@ -476,6 +489,13 @@ def run_gpu(args, rank, world, local):
     if kw["potential"] == "lj":
         flops = 12.0 * entries + 14.0 * pairs
         bytes_ = 168.0 * n + 4.0 * entries
+    elif kw["potential"] == "eam":
+        # both passes: the distance test per entry; per in-cutoff pair r (2)
+        # and, per knot, max, square, cube and multiply-adds (5 for rho; 6
+        # for value and derivative in the force pass) plus the force (7)
+        nphi, npsi = len(s.params["phi_r"]), len(s.params["psi_r"])
+        flops = 2 * (12.0 * entries) + pairs * (2 + 5 * npsi) + pairs * (2 + 6 * (nphi + npsi) + 7)
+        bytes_ = 2 * 4.0 * entries + 250.0 * n
     else:
         flops = 2 * (12.0 * entries) + 10.0 * pairs + 26.0 * pairs
         bytes_ = 2 * 4.0 * entries + 250.0 * n
@@ -502,7 +522,8 @@ def run_gpu(args, rank, world, local):
             "traffic": traffic,
             "traffic_note": traffic_note,
             "kernel": ("lj_mixed_persist<FM_FUSED_FULL> (%s)" % args.scheduler if args.scheduler != "grid"
-                       else "lj_mixed_kernel<FM_FUSED_FULL>") if kw["potential"] == "lj" else "sc_force_mixed",
+                       else "lj_mixed_kernel<FM_FUSED_FULL>") if kw["potential"] == "lj" else
+                      ("eam_force_mixed" if kw["potential"] == "eam" else "sc_force_mixed"),
             "multi_box": ensemble,
             "peak_source": peak_src,
             "algorithmic_bytes_per_launch": bytes_, "algorithmic_flops_per_launch": flops,
@@ -587,10 +608,16 @@ def oracle_sample_system(args, orc):
         reps = inputs.lj_ensemble(count=args.nc or 64)
         k = max((r for r in range(len(reps)) if reps[r].n <= 150000), key=lambda r: reps[r].n)
         return reps[k], "ensemble replica %d (the largest with <= 150,000 atoms)" % k
+    if args.workload == "eam":
+        return inputs.eam_bcc(nc=40), "piecewise-EAM bcc 40^3 cells"
     return inputs.sc_fcc(nc=48), "Sutton-Chen fcc 48^3 cells"
 
 
 def oracle_params(orc, p: dict):
+    if p["potential"] == "eam":
+        t = orc.make_eam(p["phi_r"], p["phi_a"], p["psi_r"], p["psi_a"], p["F_sqrt"], p["F_quad"])
+        return orc.make_params(potential=orc.POT_EAM, rc=p["rc"], skin=p["skin"], dt=p["dt"],
+                               mass=p["mass"], eam=t)
     if p["potential"] == "lj":
         return orc.make_params(potential=orc.POT_LJ, eps=p["eps"], sigma=p["sigma"], rc=p["rc"],
                                skin=p["skin"], dt=p["dt"], mass=p["mass"])

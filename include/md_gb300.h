@@ -52,7 +52,7 @@ typedef enum {
     MD_ERR_STATE = -7          /* handle unusable: destroy it */
 } md_status;
 
-enum { MD_POT_LJ = 0, MD_POT_SC = 1 };
+enum { MD_POT_LJ = 0, MD_POT_SC = 1, MD_POT_EAM = 2 };
 enum { MD_FP64 = 0, MD_MIXED = 1 };
 /* Newton's-third-law strategy (Sec. 1 race problem, Sec. 2.2 pair loop). */
 enum { MD_FORCE_FULL = 0, MD_FORCE_HALF_COLOR = 1, MD_FORCE_HALF_ATOMIC = 2 };
@@ -105,6 +105,35 @@ typedef struct {
  * forces.  Energy is L/J units of the potential. */
 md_status md_create(md_system **out, const md_params *p, int64_t n, const double *box3_host,
                     const double *pos_dev, const double *vel_dev, void *cuda_stream);
+
+/* Piecewise embedded-atom functions, the form of the paper's Fe potential
+ * (Sec. 3.1; its force step dominates Table 2 because such pieces
+ * vectorise poorly): the many-body energy of Eq. 1-2 with
+ *   Phi(r) = sum_k phi_a[k] (phi_r[k] - r)^3   over the knots with r < phi_r[k]
+ *   psi(r) = sum_k psi_a[k] (psi_r[k] - r)^3   over the knots with r < psi_r[k]
+ *   F(rho) = -F_sqrt sqrt(rho) + F_quad rho^2
+ * and forces f_i = -sum_j [Phi'(r) + (F'(rho_i) + F'(rho_j)) psi'(r)]
+ * (r_i - r_j) / r over r < r_c.  1 <= n_phi, n_psi <= MD_EAM_MAX_KNOTS, every
+ * knot in (0, r_c]. */
+#define MD_EAM_MAX_KNOTS 16
+typedef struct {
+    int32_t n_phi;
+    int32_t n_psi;
+    double phi_r[MD_EAM_MAX_KNOTS];
+    double phi_a[MD_EAM_MAX_KNOTS];
+    double psi_r[MD_EAM_MAX_KNOTS];
+    double psi_a[MD_EAM_MAX_KNOTS];
+    double F_sqrt;
+    double F_quad;
+} md_eam;
+
+/* md_create for the embedded-atom potential: p->potential must be
+ * MD_POT_EAM (p->eps, sigma, c, n_exp and m_exp are not used); eam_host is a
+ * host struct, copied.  Full lists under MD_SCHED_GRID; md_get_density
+ * reports rho_i and F'(rho_i).  MD_ERR_INVALID for bad tables. */
+md_status md_create_eam(md_system **out, const md_params *p, const md_eam *eam_host, int64_t n,
+                        const double *box3_host, const double *pos_dev, const double *vel_dev,
+                        void *cuda_stream);
 
 /* A batch of n_replicas independent systems advanced together: replica r
  * has n_each_host[r] atoms in the box box3_each_host[3r .. 3r+2]; pos_dev /
@@ -191,8 +220,8 @@ md_status md_get_cells(md_system *h, int32_t *cell_of_atom_dev, int64_t *cell_st
                        int32_t *ncell_host);
 
 /* Many-body intermediate results of the last force evaluation (Sutton-
- * Chen only; original order, float64 device arrays of n): rho_i (Eq. 2)
- * and F'(rho_i).  Either pointer may be NULL. */
+ * Chen or embedded-atom; original order, float64 device arrays of n): rho_i
+ * (Eq. 2) and F'(rho_i).  Either pointer may be NULL. */
 md_status md_get_density(md_system *h, double *rho_dev, double *dF_dev);
 
 /* Per-atom potential energy of the last force evaluation with energy

@@ -53,7 +53,8 @@ md_status check_params(const md_params *p, int64_t n, const double *box, std::st
     auto bad = [&](const char *m) { *why = m; return MD_ERR_INVALID; };
     if (n < 1) return bad("n must be >= 1");
     if (n >= kMaxAtoms) return bad("n must be below 2^27");
-    if (p->potential != MD_POT_LJ && p->potential != MD_POT_SC) return bad("unknown potential");
+    if (p->potential != MD_POT_LJ && p->potential != MD_POT_SC && p->potential != MD_POT_EAM)
+        return bad("unknown potential");
     if (p->precision != MD_FP64 && p->precision != MD_MIXED) return bad("unknown precision");
     if (p->force_variant < MD_FORCE_FULL || p->force_variant > MD_FORCE_HALF_ATOMIC)
         return bad("unknown force_variant");
@@ -61,9 +62,12 @@ md_status check_params(const md_params *p, int64_t n, const double *box, std::st
         return bad("unknown scheduler");
     if (p->rebuild_every < 0) return bad("rebuild_every must be >= 0");
     if (p->max_neighbors < 0) return bad("max_neighbors must be >= 0");
-    if (!(p->rc > 0) || !(p->skin >= 0) || !(p->dt > 0) || !(p->mass > 0) || !(p->eps > 0) ||
-        !(p->sigma > 0) || !std::isfinite(p->rc + p->skin + p->dt + p->mass + p->eps + p->sigma))
-        return bad("rc, dt, mass, eps, sigma must be > 0 and skin >= 0");
+    if (!(p->rc > 0) || !(p->skin >= 0) || !(p->dt > 0) || !(p->mass > 0) ||
+        !std::isfinite(p->rc + p->skin + p->dt + p->mass))
+        return bad("rc, dt, mass must be > 0 and skin >= 0");
+    if (p->potential != MD_POT_EAM &&
+        (!(p->eps > 0) || !(p->sigma > 0) || !std::isfinite(p->eps + p->sigma)))
+        return bad("eps and sigma must be > 0");
     if (p->potential == MD_POT_SC) {
         if (!(p->c > 0) || !std::isfinite(p->c)) return bad("Sutton-Chen c must be > 0");
         if (!is_int_valued(p->n_exp, 1, 30) || !is_int_valued(p->m_exp, 1, 30))
@@ -277,6 +281,10 @@ md_status enqueue_forces(md_system *h, int mode, bool energy, bool store_f) {
         MD_CK(launch_sc_density(h));
         MD_CK(launch_sc_force(h, mode, energy, store_f));
         h->launches += 2;
+    } else if (h->p.potential == MD_POT_EAM) {
+        MD_CK(launch_eam_density(h));
+        MD_CK(launch_eam_force(h, mode, energy, store_f));
+        h->launches += 2;
     } else if (h->p.force_variant != MD_FORCE_FULL) {
         int nl = 0;
         MD_CK(launch_lj_half(h, mode, energy, &nl));
@@ -480,9 +488,39 @@ extern "C" {
 
 // Shared by md_create (one box) and md_create_batch (R boxes, atoms and
 // positions concatenated box after box).
+// EAM tables, checked and converted for the kernels.
+static md_status eam_table(const md_params *p, const md_eam *e, EamTab *t, std::string *why) {
+    auto bad = [&](const char *m) { *why = m; return MD_ERR_INVALID; };
+    if (!e) return bad("MD_POT_EAM needs md_create_eam");
+    if (e->n_phi < 1 || e->n_phi > kEamMaxKnots || e->n_psi < 1 || e->n_psi > kEamMaxKnots)
+        return bad("knot counts must be in [1, 16]");
+    if (!std::isfinite(e->F_sqrt) || !std::isfinite(e->F_quad))
+        return bad("F_sqrt and F_quad must be finite");
+    *t = EamTab{};
+    t->nphi = e->n_phi;
+    t->npsi = e->n_psi;
+    for (int k = 0; k < kEamMaxKnots; ++k) {
+        const bool ip = k < e->n_phi, iq = k < e->n_psi;
+        if ((ip && !(e->phi_r[k] > 0 && e->phi_r[k] <= p->rc && std::isfinite(e->phi_a[k]))) ||
+            (iq && !(e->psi_r[k] > 0 && e->psi_r[k] <= p->rc && std::isfinite(e->psi_a[k]))))
+            return bad("every knot must lie in (0, rc] with a finite coefficient");
+        t->prd[k] = ip ? e->phi_r[k] : 0.0;
+        t->pad[k] = ip ? e->phi_a[k] : 0.0;
+        t->qrd[k] = iq ? e->psi_r[k] : 0.0;
+        t->qad[k] = iq ? e->psi_a[k] : 0.0;
+        t->pr[k] = (float)t->prd[k];
+        t->pa[k] = (float)t->pad[k];
+        t->qr[k] = (float)t->qrd[k];
+        t->qa[k] = (float)t->qad[k];
+    }
+    t->A = e->F_sqrt;
+    t->B = e->F_quad;
+    return MD_OK;
+}
+
 static md_status create_impl(md_system **out, const md_params *p, int R, const int64_t *n_each,
                              const double *boxes, const double *pos_dev, const double *vel_dev,
-                             void *cuda_stream, const char *who) {
+                             void *cuda_stream, const char *who, const md_eam *eam = nullptr) {
     md_system *h = nullptr;
     const std::string W(who);
     if (!out || !p || !boxes || !pos_dev || !n_each || R < 1)
@@ -498,7 +536,17 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
         n += n_each[r];
     }
     if (n >= kMaxAtoms) return fail(nullptr, MD_ERR_INVALID, W + ": too many atoms in total");
-    if (p->force_variant != MD_FORCE_FULL && p->potential == MD_POT_SC)
+    EamTab eam_t{};
+    if (p->potential == MD_POT_EAM) {
+        if (eam_table(p, eam, &eam_t, &why) != MD_OK)
+            return fail(nullptr, MD_ERR_INVALID, W + ": " + why);
+        if (p->force_variant != MD_FORCE_FULL || p->scheduler != MD_SCHED_GRID)
+            return fail(nullptr, MD_ERR_INVALID,
+                        W + ": the embedded-atom potential runs full lists under MD_SCHED_GRID");
+    } else if (eam) {
+        return fail(nullptr, MD_ERR_INVALID, W + ": an EAM table needs MD_POT_EAM");
+    }
+    if (p->force_variant != MD_FORCE_FULL && p->potential != MD_POT_LJ)
         return fail(nullptr, MD_ERR_INVALID, W + ": half lists are built for Lennard-Jones only");
     if (p->force_variant != MD_FORCE_FULL && p->precision != MD_MIXED)
         return fail(nullptr, MD_ERR_INVALID, W + ": half lists are built for the mixed path");
@@ -511,6 +559,7 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
     h = new (std::nothrow) md_system();
     if (!h) return fail(nullptr, MD_ERR_OOM, W + ": host allocation failed");
     h->p = *p;
+    h->eam = eam_t;
     h->n = n;
     h->R = R;
     h->stream = (cudaStream_t)cuda_stream;
@@ -580,7 +629,7 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
         A(dalloc(&h->rep, N));
         A(dalloc(&h->shifts32, (size_t)R * kStencil));
     }
-    if (p->potential == MD_POT_SC) {
+    if (p->potential == MD_POT_SC || p->potential == MD_POT_EAM) {
         A(dalloc(&h->rho, N)); A(dalloc(&h->dF32, N)); A(dalloc(&h->dF64, N));
         if (p->precision == MD_MIXED) A(dalloc(&h->xqf, N));
     }
@@ -653,6 +702,14 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
 md_status md_create(md_system **out, const md_params *p, int64_t n, const double *box3_host,
                     const double *pos_dev, const double *vel_dev, void *cuda_stream) {
     return create_impl(out, p, 1, &n, box3_host, pos_dev, vel_dev, cuda_stream, "md_create");
+}
+
+md_status md_create_eam(md_system **out, const md_params *p, const md_eam *eam_host, int64_t n,
+                        const double *box3_host, const double *pos_dev, const double *vel_dev,
+                        void *cuda_stream) {
+    if (!eam_host) return fail(nullptr, MD_ERR_INVALID, "md_create_eam: null table");
+    return create_impl(out, p, 1, &n, box3_host, pos_dev, vel_dev, cuda_stream, "md_create_eam",
+                       eam_host);
 }
 
 md_status md_create_batch(md_system **out, const md_params *p, int32_t n_replicas,
@@ -871,7 +928,8 @@ md_status md_get_cells(md_system *h, int32_t *cell_of_atom_dev, int64_t *cell_st
 
 md_status md_get_density(md_system *h, double *rho_dev, double *dF_dev) {
     if (!h) return fail(nullptr, MD_ERR_INVALID, "md_get_density: null handle");
-    if (h->p.potential != MD_POT_SC) return fail(h, MD_ERR_INVALID, "md_get_density: not many-body");
+    if (h->p.potential != MD_POT_SC && h->p.potential != MD_POT_EAM)
+        return fail(h, MD_ERR_INVALID, "md_get_density: not many-body");
     if (!h->forces_valid) {
         md_status st = forces_now(h, false);
         if (st != MD_OK) return st;
@@ -895,6 +953,9 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
     if (force_variant < MD_FORCE_FULL || force_variant > MD_FORCE_HALF_ATOMIC ||
         scheduler < MD_SCHED_GRID || scheduler > MD_SCHED_DYNAMIC)
         return fail(h, MD_ERR_INVALID, "md_set_variant: unknown variant or scheduler");
+    if (h->p.potential == MD_POT_EAM && (force_variant != MD_FORCE_FULL || scheduler != MD_SCHED_GRID))
+        return fail(h, MD_ERR_INVALID,
+                    "md_set_variant: the embedded-atom potential runs full lists under MD_SCHED_GRID");
     if (force_variant != MD_FORCE_FULL && h->p.potential == MD_POT_SC)
         return fail(h, MD_ERR_INVALID, "md_set_variant: half lists are built for Lennard-Jones only");
     if (force_variant != MD_FORCE_FULL && h->p.precision != MD_MIXED)

@@ -139,6 +139,18 @@ struct ForceConsts {
     float half_skin2f;
 };
 
+// Piecewise embedded-atom tables (MD_POT_EAM), passed to the kernels by value
+// (parameter space: warp-uniform reads).  Knot radii r_k / s_k and
+// coefficients a_k / b_k of Phi and psi, in float32 and float64; F(rho) =
+// -A sqrt(rho) + B rho^2.
+constexpr int kEamMaxKnots = 16;
+struct EamTab {
+    int nphi, npsi;
+    float pr[kEamMaxKnots], pa[kEamMaxKnots], qr[kEamMaxKnots], qa[kEamMaxKnots];
+    double prd[kEamMaxKnots], pad[kEamMaxKnots], qrd[kEamMaxKnots], qad[kEamMaxKnots];
+    double A, B;
+};
+
 enum ForceMode {
     FM_STORE = 0,       // forces (and optional energies) to f
     FM_FUSED_FULL = 1,  // forces, kick dt, drift dt (two half kicks merged)
@@ -166,6 +178,7 @@ struct md_system {
     float4 *shifts32 = nullptr;       // R x 27 float32 cell shifts (batches only)
     double *rep_ke = nullptr, *rep_pe = nullptr;  // per-replica sums (device)
     mdg::ForceConsts fc{};
+    mdg::EamTab eam{};  // MD_POT_EAM only
     double r_list = 0.0;
     float list_lo = 0.f, list_hi = 0.f;  // fp32 prefilter band around r_list^2
     double rl2 = 0.0;
@@ -287,6 +300,8 @@ cudaError_t launch_lj_persist(md_system *h, int mode, bool store_f, bool dynamic
 int persist_ctas_per_sm(bool f64);
 cudaError_t launch_sc_density(md_system *h);
 cudaError_t launch_sc_force(md_system *h, int mode, bool energy, bool store_f);
+cudaError_t launch_eam_density(md_system *h);  // k_eam.cu
+cudaError_t launch_eam_force(md_system *h, int mode, bool energy, bool store_f);
 
 // ---- integrator and state (k_integrate.cu) --------------------------------
 cudaError_t launch_kick_drift(md_system *h);

@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "MD_OK", -1: "MD_ERR_INVALID", -2: "MD_ERR_OOM", -3: "MD_ERR_
                 -4: "MD_ERR_LIST_OVERFLOW", -5: "MD_ERR_NONFINITE", -6: "MD_ERR_TIMEOUT",
                 -7: "MD_ERR_STATE"}
 
-MD_POT_LJ, MD_POT_SC = 0, 1
+MD_POT_LJ, MD_POT_SC, MD_POT_EAM = 0, 1, 2
+MD_EAM_MAX_KNOTS = 16
 MD_FP64, MD_MIXED = 0, 1
 MD_FORCE_FULL, MD_FORCE_HALF_COLOR, MD_FORCE_HALF_ATOMIC = 0, 1, 2
 MD_SCHED_GRID, MD_SCHED_PAIRCOUNT, MD_SCHED_MLP, MD_SCHED_DYNAMIC = 0, 1, 2, 3
@@ -52,6 +53,24 @@ class md_params(C.Structure):
                 ("skin", C.c_double), ("dt", C.c_double), ("mass", C.c_double)]
 
 
+class md_eam(C.Structure):
+    _fields_ = [("n_phi", C.c_int32), ("n_psi", C.c_int32),
+                ("phi_r", C.c_double * MD_EAM_MAX_KNOTS), ("phi_a", C.c_double * MD_EAM_MAX_KNOTS),
+                ("psi_r", C.c_double * MD_EAM_MAX_KNOTS), ("psi_a", C.c_double * MD_EAM_MAX_KNOTS),
+                ("F_sqrt", C.c_double), ("F_quad", C.c_double)]
+
+
+def make_eam(phi_r, phi_a, psi_r, psi_a, F_sqrt, F_quad) -> md_eam:
+    t = md_eam()
+    t.n_phi, t.n_psi = len(phi_r), len(psi_r)
+    for k, (r, a) in enumerate(zip(phi_r, phi_a)):
+        t.phi_r[k], t.phi_a[k] = r, a
+    for k, (r, a) in enumerate(zip(psi_r, psi_a)):
+        t.psi_r[k], t.psi_a[k] = r, a
+    t.F_sqrt, t.F_quad = F_sqrt, F_quad
+    return t
+
+
 _lib = None
 
 
@@ -66,6 +85,8 @@ def lib() -> C.CDLL:
     vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
     sig = {
         "md_create": [C.POINTER(vp), C.POINTER(md_params), i64, vp, vp, vp, vp],
+        "md_create_eam": [C.POINTER(vp), C.POINTER(md_params), C.POINTER(md_eam), i64, vp, vp,
+                          vp, vp],
         "md_bin_cells": [vp], "md_build_neighbors": [vp], "md_forces": [vp],
         "md_step": [vp, i64], "md_energy": [vp, vp, vp],
         "md_get_state": [vp, vp, vp, vp], "md_set_state": [vp, vp, vp],
@@ -120,7 +141,7 @@ def make_params(potential="lj", precision="mixed", force_variant=MD_FORCE_FULL,
                 rebuild_every=0, scheduler=MD_SCHED_GRID, max_neighbors=0, eps=1.0, sigma=1.0,
                 c=0.0, n_exp=12.0, m_exp=6.0, rc=2.5, skin=0.3, dt=0.005, mass=1.0,
                 **_ignored) -> md_params:
-    pot = {"lj": MD_POT_LJ, "sc": MD_POT_SC}.get(potential, potential)
+    pot = {"lj": MD_POT_LJ, "sc": MD_POT_SC, "eam": MD_POT_EAM}.get(potential, potential)
     prec = {"fp64": MD_FP64, "mixed": MD_MIXED}.get(precision, precision)
     return md_params(pot, prec, force_variant, rebuild_every, scheduler, max_neighbors, 0, 0,
                      eps, sigma, c, n_exp, m_exp, rc, skin, dt, mass)
@@ -137,6 +158,18 @@ def md_create(params: md_params, pos: torch.Tensor, vel: torch.Tensor | None, bo
     st = lib().md_create(C.byref(h), C.byref(params), n, C.cast(box_arr, C.c_void_p),
                          _ptr(pos), _ptr(vel), _stream(stream))
     _check(st, None, "md_create")
+    return h.value
+
+
+def md_create_eam(params: md_params, eam: md_eam, pos: torch.Tensor, vel: torch.Tensor | None,
+                  box, stream=None) -> int:
+    n = pos.shape[0]
+    assert pos.dtype == torch.float64 and pos.shape == (n, 3)
+    box_arr = (C.c_double * 3)(*[float(b) for b in box])
+    h = C.c_void_p()
+    st = lib().md_create_eam(C.byref(h), C.byref(params), C.byref(eam), n,
+                             C.cast(box_arr, C.c_void_p), _ptr(pos), _ptr(vel), _stream(stream))
+    _check(st, None, "md_create_eam")
     return h.value
 
 
@@ -303,8 +336,15 @@ class System:
     """Owns one md_system handle.  pos/vel: (n, 3) float64 tensors (any device;
     copied to the GPU), box: 3 floats, params: md_params or keyword dict."""
 
-    def __init__(self, pos, vel, box, params=None, stream=None, **kw):
+    def __init__(self, pos, vel, box, params=None, stream=None, eam=None, **kw):
+        """eam: an md_eam table (or a dict of make_eam's arguments) for the
+        embedded-atom potential (md_create_eam)."""
         self.h = None
+        if eam is not None:
+            kw.setdefault("potential", "eam")
+            if isinstance(eam, dict):
+                eam = make_eam(*[eam[k] for k in ("phi_r", "phi_a", "psi_r", "psi_a",
+                                                  "F_sqrt", "F_quad")])
         if params is None:
             params = make_params(**kw)
         elif isinstance(params, dict):
@@ -316,7 +356,10 @@ class System:
         v = None if vel is None else torch.as_tensor(vel, dtype=torch.float64).to(dev).contiguous()
         self.n = p.shape[0]
         self.box = [float(b) for b in box]
-        self.h = md_create(params, p, v, self.box, stream)
+        if eam is not None:
+            self.h = md_create_eam(params, eam, p, v, self.box, stream)
+        else:
+            self.h = md_create(params, p, v, self.box, stream)
 
     def close(self):
         if getattr(self, "h", None):

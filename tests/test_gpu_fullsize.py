@@ -145,6 +145,26 @@ def test_sutton_chen_8m(md, orc):
     check_forces(orc, prm, f, pos, s.box, idx, ooff, oids, p["rc"], 2e-4, 1e-5)
 
 
+def test_eam_fe126_4m(md, orc):
+    """126^3-cell bcc under the piecewise embedded-atom potential (4,000,752
+    atoms, the size of the paper's Fe126), mixed path, both passes."""
+    s = inputs.eam_bcc(nc=126)
+    p = s.params
+    keys = ("phi_r", "phi_a", "psi_r", "psi_a", "F_sqrt", "F_quad")
+    t_orc = orc.make_eam(*[p[k] for k in keys])
+    prm = orc.make_params(potential=orc.POT_EAM, rc=p["rc"], skin=p["skin"], dt=p["dt"],
+                          eam=t_orc)
+    with md.System(s.pos, s.vel, s.box, precision="mixed", eam=md.make_eam(*[p[k] for k in keys]),
+                   rc=p["rc"], skin=p["skin"], dt=p["dt"], mass=p["mass"]) as a:
+        assert a.n == 4000752
+        a.step(10)
+        pos = perturbed(s.pos, s.box, 0.04, inputs.SEED_BASE + 314)
+        f = load(md, a, pos, s.vel)
+        idx = sample_ids(a.n, 300, inputs.SEED_BASE + 306)
+        ooff, oids = check_rows(orc, a, pos, s.box, p["rc"] + p["skin"], idx)
+    check_forces(orc, prm, f, pos, s.box, idx, ooff, oids, p["rc"], 2e-4, 1e-5)
+
+
 def test_ensemble_64_replicas(md, orc):
     """The 64-replica ensemble (2,428,400 atoms) as one batch: sampled atoms
     of each of eight replicas against the oracle on that replica's box."""
