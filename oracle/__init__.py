@@ -11,7 +11,8 @@ Functions and the passages of Mangiardi & Meyer they follow:
 * ``cell_grid``, ``bin_cells``   -- cell decomposition (Sec. 2.1)
 * ``neighbors_brute``, ``neighbors_cells`` -- Verlet lists with r_list =
   r_c + skin (Sec. 2.1, Sec. 3.3)
-* ``lj_brute``, ``lj_list``      -- pair forces F = -(1/d) dPhi/dr R (Sec. 2.2)
+* ``lj_brute``, ``lj_list``      -- pair forces F = -(1/d) dPhi/dr R (Sec. 2.2);
+  ``lj_typed_*`` with per-species parameters (the Cu-Au systems of Sec. 3.1)
 * ``sc_brute``, ``sc_list``      -- many-body energy Eq. 1-2 evaluated in three
   steps (Sec. 3.1)
 * ``eam_brute``, ``eam_list``    -- the same with piecewise cubic pair and
@@ -80,15 +81,31 @@ class Params(C.Structure):
                 ("eps", C.c_double), ("sigma", C.c_double), ("c", C.c_double),
                 ("n_exp", C.c_double), ("m_exp", C.c_double), ("rc", C.c_double),
                 ("skin", C.c_double), ("dt", C.c_double), ("mass", C.c_double),
-                ("eam", C.POINTER(EamTable))]
+                ("eam", C.POINTER(EamTable)),
+                ("ntypes", C.c_int32), ("types", C.POINTER(C.c_int32)),
+                ("t_eps", C.POINTER(C.c_double)), ("t_sigma", C.POINTER(C.c_double)),
+                ("t_mass", C.POINTER(C.c_double))]
 
 
 def make_params(potential=POT_LJ, eps=1.0, sigma=1.0, c=0.0, n_exp=12.0, m_exp=6.0,
-                rc=2.5, skin=0.3, dt=0.005, mass=1.0, rebuild_every=0, eam=None) -> Params:
-    """eam: an EamTable (potential POT_EAM); kept alive by the returned Params."""
+                rc=2.5, skin=0.3, dt=0.005, mass=1.0, rebuild_every=0, eam=None,
+                types=None, t_eps=None, t_sigma=None, t_mass=None) -> Params:
+    """eam: an EamTable (potential POT_EAM).  types (n int32 species),
+    t_eps / t_sigma (nt x nt) and t_mass (nt): a multi-element Lennard-Jones
+    system.  The arrays are kept alive by the returned Params."""
     p = Params(potential, rebuild_every, eps, sigma, c, n_exp, m_exp, rc, skin, dt, mass,
                C.pointer(eam) if eam is not None else None)
     p._eam_ref = eam
+    if types is not None:
+        tt = np.ascontiguousarray(types, np.int32)
+        te = np.ascontiguousarray(t_eps, np.float64).ravel()
+        ts = np.ascontiguousarray(t_sigma, np.float64).ravel()
+        tm = np.ascontiguousarray(t_mass, np.float64).ravel()
+        assert te.size == ts.size == tm.size ** 2
+        p.ntypes = tm.size
+        p.types, p.t_eps = _P(tt, C.c_int32), _P(te, C.c_double)
+        p.t_sigma, p.t_mass = _P(ts, C.c_double), _P(tm, C.c_double)
+        p._typed_ref = (tt, te, ts, tm)
     return p
 
 
@@ -121,6 +138,10 @@ def lib():
             L.orc_sc_list.argtypes = [i64, pd, pd, d, d, d, d, d, d, pi64, pi32, pd, pd, pd, pd]
             L.orc_sc_brute.restype = d
             L.orc_sc_brute.argtypes = [i64, pd, pd, d, d, d, d, d, d, pd, pd]
+            L.orc_lj_typed_brute.restype = d
+            L.orc_lj_typed_brute.argtypes = [i64, pd, pd, i32, pi32, pd, pd, d, pd]
+            L.orc_lj_typed_list.restype = d
+            L.orc_lj_typed_list.argtypes = [i64, pd, pd, i32, pi32, pd, pd, d, pi64, pi32, pd, pd]
             L.orc_eam_list.restype = d
             L.orc_eam_list.argtypes = [i64, pd, pd, C.POINTER(EamTable), d, pi64, pi32, pd, pd,
                                        pd, pd]
@@ -261,6 +282,36 @@ def sc_brute(pos, box, eps=1.0, a=1.0, c=39.432, n_exp=9.0, m_exp=6.0, rc=2.0):
     U = lib().orc_sc_brute(pos.shape[0], _P(pos, C.c_double), _P(box, C.c_double), eps, a, c,
                            n_exp, m_exp, rc, _P(f, C.c_double), _P(rho, C.c_double))
     return U, f, rho
+
+
+def lj_typed_brute(pos, box, types, t_eps, t_sigma, rc=2.5):
+    """Multi-element LJ over all pairs: (U, f)."""
+    pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
+    tt = np.ascontiguousarray(types, np.int32)
+    te, ts = _f64(t_eps).ravel(), _f64(t_sigma).ravel()
+    nt = int(round(te.size ** 0.5))
+    f = np.zeros_like(pos)
+    U = lib().orc_lj_typed_brute(pos.shape[0], _P(pos, C.c_double), _P(box, C.c_double), nt,
+                                 _P(tt, C.c_int32), _P(te, C.c_double), _P(ts, C.c_double), rc,
+                                 _P(f, C.c_double))
+    return U, f
+
+
+def lj_typed_list(pos, box, offsets, ids, types, t_eps, t_sigma, rc=2.5):
+    """Multi-element LJ from a full list: (U, f, e_atom)."""
+    pos, box = _f64(pos, (-1, 3)), _f64(box, (3,))
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    ids = np.ascontiguousarray(ids, np.int32)
+    tt = np.ascontiguousarray(types, np.int32)
+    te, ts = _f64(t_eps).ravel(), _f64(t_sigma).ravel()
+    nt = int(round(te.size ** 0.5))
+    f = np.zeros_like(pos)
+    e = np.zeros(pos.shape[0])
+    U = lib().orc_lj_typed_list(pos.shape[0], _P(pos, C.c_double), _P(box, C.c_double), nt,
+                                _P(tt, C.c_int32), _P(te, C.c_double), _P(ts, C.c_double), rc,
+                                _P(offsets, C.c_int64), _P(ids, C.c_int32), _P(f, C.c_double),
+                                _P(e, C.c_double))
+    return U, f, e
 
 
 def eam_list(pos, box, offsets, ids, table: EamTable, rc):

@@ -261,6 +261,12 @@ typedef struct {
     double dt;              /* time step */
     double mass;            /* atom mass */
     const struct orc_eam_s *eam;  /* embedded-atom tables (potential 2), else NULL */
+    /* multi-element Lennard-Jones (potential 0 with ntypes > 0): the species
+     * of every atom, pair parameters t_eps[a * ntypes + b], t_sigma[...] and
+     * masses t_mass[a]; eps, sigma and mass above are then not used */
+    int32_t ntypes;
+    const int32_t *types;
+    const double *t_eps, *t_sigma, *t_mass;
 } orc_params;
 
 /* Lennard-Jones, truncated and energy-shifted at r_c:
@@ -318,6 +324,55 @@ double orc_lj_list(int64_t n, const double *pos, const double *box, double eps, 
             double fs = lj_fscalar(r2, eps, sigma);
             fx -= fs * dx; fy -= fs * dy; fz -= fs * dz;
             ei += 0.5 * (lj_phi(r2, eps, sigma) - shift);
+        }
+        f[3 * i + 0] = fx; f[3 * i + 1] = fy; f[3 * i + 2] = fz;
+        if (e_atom) e_atom[i] = ei;
+        U += ei;
+    }
+    return U;
+}
+
+/* Multi-element Lennard-Jones (the Cu-Au alloy and layer systems of
+ * Sec. 3.1): the pair (i, j) takes eps and sigma of its two species,
+ * eps[t_i * nt + t_j], and its energy is shifted to zero at r_c with those
+ * parameters.  Same loops as orc_lj_brute / orc_lj_list otherwise. */
+double orc_lj_typed_brute(int64_t n, const double *pos, const double *box, int32_t nt,
+                          const int32_t *types, const double *eps, const double *sigma, double rc,
+                          double *f) {
+    double rc2 = rc * rc, U = 0.0;
+    memset(f, 0, sizeof(double) * 3 * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = i + 1; j < n; ++j) {
+            double dx, dy, dz;
+            double r2 = pair_r2(pos, box, i, j, &dx, &dy, &dz);
+            if (!(r2 < rc2)) continue;
+            int t = types[i] * nt + types[j];
+            double fs = lj_fscalar(r2, eps[t], sigma[t]);
+            double Fx = -fs * dx, Fy = -fs * dy, Fz = -fs * dz;
+            f[3 * i + 0] += Fx; f[3 * i + 1] += Fy; f[3 * i + 2] += Fz;
+            f[3 * j + 0] -= Fx; f[3 * j + 1] -= Fy; f[3 * j + 2] -= Fz;
+            U += lj_phi(r2, eps[t], sigma[t]) - lj_phi(rc2, eps[t], sigma[t]);
+        }
+    }
+    return U;
+}
+
+double orc_lj_typed_list(int64_t n, const double *pos, const double *box, int32_t nt,
+                         const int32_t *types, const double *eps, const double *sigma, double rc,
+                         const int64_t *offsets, const int32_t *ids, double *f, double *e_atom) {
+    double rc2 = rc * rc, U = 0.0;
+    #pragma omp parallel for schedule(dynamic, 256) reduction(+ : U)
+    for (int64_t i = 0; i < n; ++i) {
+        double fx = 0.0, fy = 0.0, fz = 0.0, ei = 0.0;
+        for (int64_t k = offsets[i]; k < offsets[i + 1]; ++k) {
+            int64_t j = ids[k];
+            double dx, dy, dz;
+            double r2 = pair_r2(pos, box, i, j, &dx, &dy, &dz);
+            if (!(r2 < rc2)) continue;
+            int t = types[i] * nt + types[j];
+            double fs = lj_fscalar(r2, eps[t], sigma[t]);
+            fx -= fs * dx; fy -= fs * dy; fz -= fs * dz;
+            ei += 0.5 * (lj_phi(r2, eps[t], sigma[t]) - lj_phi(rc2, eps[t], sigma[t]));
         }
         f[3 * i + 0] = fx; f[3 * i + 1] = fy; f[3 * i + 2] = fz;
         if (e_atom) e_atom[i] = ei;
@@ -639,7 +694,18 @@ int orc_forces_sample(const orc_params *p, int64_t n, const double *pos, const d
         if (cnt > CAP) { bad = 1; free(nb); free(nb2); continue; }
         qsort(nb, (size_t)cnt, sizeof(int64_t), cmp_i64);  /* ascending j, as the list routines */
         double fx = 0.0, fy = 0.0, fz = 0.0, ei = 0.0;
-        if (p->potential == 0) {
+        if (p->potential == 0 && p->ntypes > 0) {
+            double rc2 = p->rc * p->rc;
+            for (int64_t q = 0; q < cnt; ++q) {
+                double dx, dy, dz;
+                double r2 = pair_r2(pos, box, i, nb[q], &dx, &dy, &dz);
+                int t = p->types[i] * p->ntypes + p->types[nb[q]];
+                double fs = lj_fscalar(r2, p->t_eps[t], p->t_sigma[t]);
+                fx -= fs * dx; fy -= fs * dy; fz -= fs * dz;
+                ei += 0.5 * (lj_phi(r2, p->t_eps[t], p->t_sigma[t]) -
+                             lj_phi(rc2, p->t_eps[t], p->t_sigma[t]));
+            }
+        } else if (p->potential == 0) {
             double shift = lj_phi(p->rc * p->rc, p->eps, p->sigma);
             for (int64_t q = 0; q < cnt; ++q) {
                 double dx, dy, dz;
@@ -776,6 +842,9 @@ static int build_list(int64_t n, const double *pos, const double *box, double r_
 
 static double forces(const orc_params *p, int64_t n, const double *pos, const double *box,
                      const orc_list *L, double *f) {
+    if (p->potential == 0 && p->ntypes > 0)
+        return orc_lj_typed_list(n, pos, box, p->ntypes, p->types, p->t_eps, p->t_sigma, p->rc,
+                                 L->offsets, L->ids, f, NULL);
     if (p->potential == 0)
         return orc_lj_list(n, pos, box, p->eps, p->sigma, p->rc, L->offsets, L->ids, f, NULL);
     if (p->potential == 2)
@@ -784,10 +853,21 @@ static double forces(const orc_params *p, int64_t n, const double *pos, const do
                        L->offsets, L->ids, f, NULL, NULL, NULL);
 }
 
-static double kinetic(int64_t n, const double *vel, double mass) {
+/* mass of atom i: its species' mass for a multi-element system */
+static double atom_mass(const orc_params *p, int64_t i) {
+    return p->ntypes > 0 ? p->t_mass[p->types[i]] : p->mass;
+}
+
+static double kinetic(const orc_params *p, int64_t n, const double *vel) {
+    if (p->ntypes == 0) {
+        double s = 0.0;
+        for (int64_t k = 0; k < 3 * n; ++k) s += vel[k] * vel[k];
+        return 0.5 * p->mass * s;
+    }
     double s = 0.0;
-    for (int64_t k = 0; k < 3 * n; ++k) s += vel[k] * vel[k];
-    return 0.5 * mass * s;
+    for (int64_t i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d) s += 0.5 * atom_mass(p, i) * vel[3 * i + d] * vel[3 * i + d];
+    return s;
 }
 
 /* Runs nsteps velocity-Verlet steps in place on pos/vel (n x 3).  energies
@@ -813,16 +893,17 @@ int64_t orc_md_run(const orc_params *p, int64_t n, double *pos, double *vel, con
     int64_t since = 0;
     double U = forces(p, n, pos, box, &L, f);
     if (energies) {
-        double K = kinetic(n, vel, p->mass);
+        double K = kinetic(p, n, vel);
         energies[0] = K; energies[1] = U; energies[2] = K + U;
     }
-    double h = 0.5 * p->dt / p->mass;
     for (int64_t s = 1; s <= nsteps; ++s) {
-        for (int64_t i = 0; i < n; ++i)
+        for (int64_t i = 0; i < n; ++i) {
+            double h = 0.5 * p->dt / atom_mass(p, i);
             for (int d = 0; d < 3; ++d) {
                 vel[3 * i + d] += h * f[3 * i + d];
                 pos[3 * i + d] = wrap(pos[3 * i + d] + p->dt * vel[3 * i + d], box[d]);
             }
+        }
         since += 1;
         int rebuild = 0;
         if (p->rebuild_every > 0) {
@@ -845,9 +926,12 @@ int64_t orc_md_run(const orc_params *p, int64_t n, double *pos, double *vel, con
             since = 0;
         }
         U = forces(p, n, pos, box, &L, f);
-        for (int64_t k = 0; k < 3 * n; ++k) vel[k] += h * f[k];
+        for (int64_t i = 0; i < n; ++i) {
+            double h = 0.5 * p->dt / atom_mass(p, i);
+            for (int d = 0; d < 3; ++d) vel[3 * i + d] += h * f[3 * i + d];
+        }
         if (energies) {
-            double K = kinetic(n, vel, p->mass);
+            double K = kinetic(p, n, vel);
             energies[3 * s + 0] = K; energies[3 * s + 1] = U; energies[3 * s + 2] = K + U;
         }
     }

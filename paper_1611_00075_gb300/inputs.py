@@ -14,6 +14,8 @@ are not available, so these stand in for them:
 * ``sc_fcc``      -- many-body fcc metal at its lattice constant
 * ``eam_bcc``     -- bcc metal under a piecewise embedded-atom potential
   (stands in for Fe126)
+* ``lj_alloy``, ``lj_layer`` -- a Cu-Au-like binary LJ crystal, random or in
+  slabs (stand in for the Alloy and Layer systems)
 * ``lj_ensemble`` -- a batch of independent replicas of uneven size
 
 Random numbers come from splitmix64 (Steele, Lea & Flood 2014): output k of a
@@ -247,6 +249,65 @@ def eam_bcc(nc: int = 126, a0: float = 1.0, seed: int = SEED_BASE + 6, **over) -
     vel = maxwell_boltzmann(pos.shape[0], p["T"], p["mass"], seed)
     box = np.full(3, nc * a0)
     return System("eam_bcc_%d" % nc, pos, vel, box, dict(potential="eam", **p))
+
+
+# A synthetic Cu-Au-like binary Lennard-Jones system standing in for the
+# paper's Alloy (Cu75Au25) and Layer (Cu and Au slabs) configurations, whose
+# Cleri-Rosato parameters are not available here.  Species 0 (Cu-like):
+# eps = sigma = mass = 1; species 1 (Au-like): eps 1.12, sigma 1.128, mass
+# 3.10 -- the Au/Cu ratios of published Lennard-Jones fits for the two fcc
+# metals and of their atomic masses; unlike pairs by Lorentz-Berthelot
+# mixing.  fcc lattice constant 1.625, the minimum of the unrelaxed random
+# 25 % alloy's lattice energy; T* = 0.063 (300 K over the Cu-like eps,
+# 0.409 eV).  The unrelaxed unlike neighbours are compressed (Au-like pairs at
+# 1.01 sigma), which stiffens the dynamics: dt = 0.002 keeps the float64
+# energy within 1e-5 over 400 steps (0.005 drifts by 5e-5).
+LJ_CUAU = dict(eps=(1.0, 1.12), sigma=(1.0, 1.128), mass=(1.0, 3.10), a0=1.625,
+               rc=2.5, skin=0.3, dt=0.002, T=0.063)
+
+
+def mixing_rules(eps, sigma):
+    """nt x nt pair parameters: sqrt(eps_a eps_b) and (sigma_a + sigma_b) / 2."""
+    e = np.sqrt(np.outer(eps, eps))
+    s = 0.5 * (np.add.outer(sigma, sigma))
+    return e, s
+
+
+def _typed_system(name, pos, types, box, p, seed):
+    mass = np.asarray(p["mass"])[types]
+    # Maxwell-Boltzmann per species mass: unit Gaussians scaled by 1/sqrt(m),
+    # then the common shift and rescale to exactly T (momentum-weighted)
+    g = gaussian(seed, 3 * len(pos)).reshape(-1, 3) * np.sqrt(p["T"] / mass)[:, None]
+    g -= (mass[:, None] * g).sum(axis=0) / mass.sum()
+    ke = 0.5 * float(np.sum(mass[:, None] * g * g))
+    g *= math.sqrt(0.5 * (3 * len(pos) - 3) * p["T"] / ke)
+    t_eps, t_sigma = mixing_rules(p["eps"], p["sigma"])
+    params = dict(potential="lj", rc=p["rc"], skin=p["skin"], dt=p["dt"], T=p["T"],
+                  types=np.ascontiguousarray(types, np.int32), t_eps=t_eps, t_sigma=t_sigma,
+                  t_mass=np.asarray(p["mass"], np.float64), eps=1.0, sigma=1.0, mass=1.0)
+    return System(name, np.ascontiguousarray(pos), np.ascontiguousarray(g), box, params)
+
+
+def lj_alloy(nc: int = 105, frac: float = 0.25, seed: int = SEED_BASE + 7, **over) -> System:
+    """Random substitutional alloy: fcc sites of nc^3 cells, each Au-like with
+    probability frac (105^3 cells: 4,630,500 atoms, the paper's Alloy size)."""
+    p = dict(LJ_CUAU)
+    p.update(over)
+    pos = fcc_lattice(nc, p["a0"])
+    types = (uniform(seed, len(pos)) < frac).astype(np.int32)
+    return _typed_system("lj_alloy_%d" % nc, pos, types, np.full(3, nc * p["a0"]), p, seed + 1)
+
+
+def lj_layer(nc: int = 99, slab: int = 9, seed: int = SEED_BASE + 8, **over) -> System:
+    """Slabs of slab fcc cells along z, alternately Cu-like and Au-like
+    (99^3 cells: 3,881,196 atoms, near the paper's Layer size)."""
+    p = dict(LJ_CUAU)
+    p.update(over)
+    pos = fcc_lattice(nc, p["a0"])
+    nz = np.repeat(np.arange(nc), 4)  # the fcc order is (ix, iy, iz, basis)
+    iz = np.tile(nz, nc * nc)
+    types = ((iz // slab) % 2).astype(np.int32)
+    return _typed_system("lj_layer_%d" % nc, pos, types, np.full(3, nc * p["a0"]), p, seed + 1)
 
 
 def lj_ensemble(count: int = 64, nmin: int = 1000, nmax: int = 200000,
