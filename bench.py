@@ -70,7 +70,7 @@ def parse_args(argv):
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="porous",
-                    choices=["porous", "fcc", "sc", "eam", "ensemble"])
+                    choices=["porous", "fcc", "sc", "eam", "alloy", "layer", "ensemble"])
     ap.add_argument("--compare-steps", type=int, default=100,
                     help="steps timed for each other scheduler (0 = skip the comparison)")
     ap.add_argument("--scheduler", default="mlp",
@@ -136,6 +136,18 @@ def make_workload(name: str, nc: int = 0):
                 "(2,000 untimed mixed-precision steps, velocities rescaled every 50 steps to "
                 "T*=2.4 for 1,000 steps, then to T*=1.2), T*=1.2, rc=2.5, skin=0.3, dt=0.005, "
                 "half-skin rebuilds" % (k, s.n))
+    elif name in ("alloy", "layer"):
+        if name == "alloy":
+            k = nc or 105
+            s = inputs.lj_alloy(nc=k)
+            what = "random alloy, 25 % Au-like (the paper's Alloy size)"
+        else:
+            k = nc or 99
+            s = inputs.lj_layer(nc=k)
+            what = "slabs of 9 fcc cells, alternately Cu-like and Au-like (near the Layer size)"
+        desc = ("Cu-Au-like binary Lennard-Jones fcc %d^3 cells = %d atoms, %s; eps 1 / 1.12, "
+                "sigma 1 / 1.128 (Lorentz-Berthelot), mass 1 / 3.10, a0=1.625, rc=2.5, skin=0.3, "
+                "T*=0.063, dt=0.002" % (k, s.n, what))
     elif name == "eam":
         k = nc or 126
         s = inputs.eam_bcc(nc=k)
@@ -167,6 +179,8 @@ def md_kwargs(s):
         kw.update(eam={k: p[k] for k in ("phi_r", "phi_a", "psi_r", "psi_a", "F_sqrt",
                                          "F_quad")})
         del kw["eps"], kw["sigma"]
+    if "types" in p:
+        kw.update(species=(p["types"], p["t_eps"], p["t_sigma"], p["t_mass"]))
     return kw
 
 
@@ -257,7 +271,7 @@ def run_gpu(args, rank, world, local):
             args.scheduler = "grid"  # measured faster than the dynamic queue for batches
         args.fp64_steps = 0  # batches run the mixed path; per-replica fp64 is not the comparison
     kw = md_kwargs(s)
-    if kw["potential"] != "lj" and args.scheduler != "grid":
+    if (kw["potential"] != "lj" or "species" in kw) and args.scheduler != "grid":
         args.scheduler = "grid"  # the persistent schedulers drive the Lennard-Jones kernel
     sched = {"grid": md.MD_SCHED_GRID, "paircount": md.MD_SCHED_PAIRCOUNT,
              "mlp": md.MD_SCHED_MLP, "dynamic": md.MD_SCHED_DYNAMIC}[args.scheduler]
@@ -337,7 +351,7 @@ def run_gpu(args, rank, world, local):
                         "atom_steps_per_s": mixed.n * args.compare_steps / (e0.elapsed_time(e1) * 1e-3),
                         "steps": args.compare_steps}
             batch_from_s0(sched)
-        elif kw["potential"] == "lj":
+        elif kw["potential"] == "lj" and "species" not in kw:
             # the learned part first: per-cell clock64 timings of this state,
             # then the network trained on the GPU
             if args.scheduler == "mlp" or args.compare_steps > 0:
@@ -422,7 +436,7 @@ def run_gpu(args, rank, world, local):
         # persistent schedulers serve Lennard-Jones; Sutton-Chen runs a grid)
         fp64 = None
         if args.fp64_steps > 0:
-            sched64 = "paircount" if kw["potential"] == "lj" else "grid"
+            sched64 = "paircount" if (kw["potential"] == "lj" and "species" not in kw) else "grid"
             plain = md.System(s.pos, s.vel, s.box, precision="fp64", stream=stream,
                               scheduler=md.MD_SCHED_PAIRCOUNT if sched64 == "paircount"
                               else md.MD_SCHED_GRID, **kw)
@@ -521,7 +535,8 @@ def run_gpu(args, rank, world, local):
             "frac": (ach_gbs / hbm_peak) if hbm_bound else (ach_flops / fp32_peak),
             "traffic": traffic,
             "traffic_note": traffic_note,
-            "kernel": ("lj_mixed_persist<FM_FUSED_FULL> (%s)" % args.scheduler if args.scheduler != "grid"
+            "kernel": ("lj_typed_kernel<FM_FUSED_FULL>" if "species" in kw else
+                       "lj_mixed_persist<FM_FUSED_FULL> (%s)" % args.scheduler if args.scheduler != "grid"
                        else "lj_mixed_kernel<FM_FUSED_FULL>") if kw["potential"] == "lj" else
                       ("eam_force_mixed" if kw["potential"] == "eam" else "sc_force_mixed"),
             "multi_box": ensemble,
@@ -610,6 +625,10 @@ def oracle_sample_system(args, orc):
         return reps[k], "ensemble replica %d (the largest with <= 150,000 atoms)" % k
     if args.workload == "eam":
         return inputs.eam_bcc(nc=40), "piecewise-EAM bcc 40^3 cells"
+    if args.workload == "alloy":
+        return inputs.lj_alloy(nc=40), "Cu-Au-like random alloy 40^3 fcc cells"
+    if args.workload == "layer":
+        return inputs.lj_layer(nc=36), "Cu-Au-like slabs 36^3 fcc cells"
     return inputs.sc_fcc(nc=48), "Sutton-Chen fcc 48^3 cells"
 
 
@@ -618,6 +637,10 @@ def oracle_params(orc, p: dict):
         t = orc.make_eam(p["phi_r"], p["phi_a"], p["psi_r"], p["psi_a"], p["F_sqrt"], p["F_quad"])
         return orc.make_params(potential=orc.POT_EAM, rc=p["rc"], skin=p["skin"], dt=p["dt"],
                                mass=p["mass"], eam=t)
+    if p["potential"] == "lj" and "types" in p:
+        return orc.make_params(potential=orc.POT_LJ, rc=p["rc"], skin=p["skin"], dt=p["dt"],
+                               types=p["types"], t_eps=p["t_eps"], t_sigma=p["t_sigma"],
+                               t_mass=p["t_mass"])
     if p["potential"] == "lj":
         return orc.make_params(potential=orc.POT_LJ, eps=p["eps"], sigma=p["sigma"], rc=p["rc"],
                                skin=p["skin"], dt=p["dt"], mass=p["mass"])

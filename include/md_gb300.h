@@ -135,6 +135,34 @@ md_status md_create_eam(md_system **out, const md_params *p, const md_eam *eam_h
                         const double *box3_host, const double *pos_dev, const double *vel_dev,
                         void *cuda_stream);
 
+/* Multi-element Lennard-Jones, the GPU counterpart of the paper's Cu-Au
+ * Alloy and Layer systems (Sec. 3.1), whose SIMD loop reloads each pair's
+ * parameters with masks (Sec. 2.2): ntypes species (1..MD_MAX_TYPES); the
+ * pair (i, j) uses eps[t_i * ntypes + t_j] and sigma[...] (symmetric
+ * matrices) with its energy shifted to zero at r_c, and atom i has mass
+ * mass[t_i].  The md_params fields eps, sigma and mass are not used. */
+#define MD_MAX_TYPES 4
+typedef struct {
+    int32_t ntypes;
+    int32_t reserved;
+    double eps[MD_MAX_TYPES * MD_MAX_TYPES];
+    double sigma[MD_MAX_TYPES * MD_MAX_TYPES];
+    double mass[MD_MAX_TYPES];
+} md_lj_types;
+
+/* md_create for a multi-element Lennard-Jones system: p->potential must be
+ * MD_POT_LJ; types_host (copied) holds the species parameters and type_dev
+ * (device, n int32 in original order, 0 <= t < ntypes) each atom's species.
+ * Full lists under MD_SCHED_GRID, fp64 or mixed precision.  The species
+ * travels with the atom through binning (two spare bits above the original
+ * id in its float32 position word), so the pair loop reads j's species from
+ * the position it loads anyway and selects the pair's parameters from the
+ * row of i's species held in registers.  MD_ERR_INVALID for bad species,
+ * asymmetric or non-positive parameters. */
+md_status md_create_typed(md_system **out, const md_params *p, const md_lj_types *types_host,
+                          const int32_t *type_dev, int64_t n, const double *box3_host,
+                          const double *pos_dev, const double *vel_dev, void *cuda_stream);
+
 /* A batch of n_replicas independent systems advanced together: replica r
  * has n_each_host[r] atoms in the box box3_each_host[3r .. 3r+2]; pos_dev /
  * vel_dev hold all replicas' atoms one replica after the other (n = sum of

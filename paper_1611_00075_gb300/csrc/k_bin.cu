@@ -174,7 +174,8 @@ __global__ void gather_kernel(int n, const Grid *__restrict__ grids,
                               float4 *__restrict__ xq, float4 *__restrict__ xq_build,
                               double4 *__restrict__ xabs, double *__restrict__ v,
                               int32_t *__restrict__ orig, int32_t *__restrict__ cell,
-                              uint16_t *__restrict__ rep, DevStatus *ds, bool gated) {
+                              uint16_t *__restrict__ rep, const int32_t *__restrict__ type_orig,
+                              DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) ds->abs_fresh = 1;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
@@ -190,7 +191,10 @@ __global__ void gather_kernel(int n, const Grid *__restrict__ grids,
         const double3 C = cell_centre_of(cl % g.nx, (cl / g.nx) % g.ny, cl / (g.nx * g.ny), g);
         const double rx = a.x - C.x, ry = a.y - C.y, rz = a.z - C.z;
         xr[k] = make_double4(rx, ry, rz, 0.0);
-        const float4 q = make_float4((float)rx, (float)ry, (float)rz, __int_as_float(o));
+        // the float32 word carries the original id and, for a multi-element
+        // system, the species above it
+        const uint32_t w = (uint32_t)o | (type_orig ? (uint32_t)type_orig[o] << kIndexBits : 0u);
+        const float4 q = make_float4((float)rx, (float)ry, (float)rz, __uint_as_float(w));
         xq[k] = q;
         xq_build[k] = q;
         xabs[k] = make_double4(a.x, a.y, a.z, 0.0);
@@ -240,7 +244,8 @@ cudaError_t launch_bin(md_system *h, bool gated) {
                                                                      h->key, h->src, h->ds, gated);
     gather_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->grids, h->src, h->tmp_abs, h->tmp_v,
                                                   h->xr64[cur], h->xq[cur], h->xq_build, h->xabs,
-                                                  h->v, h->orig, h->cell, h->rep, h->ds, gated);
+                                                  h->v, h->orig, h->cell, h->rep, h->type_orig,
+                                                  h->ds, gated);
     return cudaGetLastError();
 }
 

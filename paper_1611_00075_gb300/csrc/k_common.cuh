@@ -59,7 +59,9 @@ template <int MODE>
 __device__ __forceinline__ void vv_epilogue(const ForceArgs &a, int i, double Fx, double Fy,
                                             double Fz, float qw) {
     const size_t n = (size_t)a.n;
-    const double hk = (MODE == FM_FUSED_FULL) ? a.fc.dt * a.fc.inv_m : 0.5 * a.fc.dt * a.fc.inv_m;
+    double im = a.fc.inv_m;
+    if (a.fc.ntypes > 0) im = pick4(a.fc.t_inv_m, species_of(__float_as_uint(qw)));
+    const double hk = (MODE == FM_FUSED_FULL) ? a.fc.dt * im : 0.5 * a.fc.dt * im;
     double vx = a.v[i] + hk * Fx;
     double vy = a.v[n + i] + hk * Fy;
     double vz = a.v[2 * n + i] + hk * Fz;

@@ -13,11 +13,13 @@ namespace mdg {
 
 namespace {
 
-__global__ void kick_drift_kernel(int n, double hk, double dt, float half_skin2,
+// hk_t: the half kick dt / 2m of each species of a multi-element system
+// (ntypes > 0), read from the species bits of the position word.
+__global__ void kick_drift_kernel(int n, double hk0, double dt, float half_skin2,
                                   int rebuild_every, double4 *__restrict__ xr,
                                   float4 *__restrict__ xq, const float4 *__restrict__ xq_build,
                                   double *__restrict__ v, const double *__restrict__ f,
-                                  DevStatus *ds) {
+                                  DevStatus *ds, int ntypes, double4 hk_t) {
     if (ds->status != 0) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ds->abs_fresh = 0;
@@ -28,6 +30,12 @@ __global__ void kick_drift_kernel(int n, double hk, double dt, float half_skin2,
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const size_t N = (size_t)n;
+    float4 q = xq[i];
+    double hk = hk0;
+    if (ntypes > 0) {
+        const int t = species_of(__float_as_uint(q.w));
+        hk = t < 2 ? (t == 0 ? hk_t.x : hk_t.y) : (t == 2 ? hk_t.z : hk_t.w);
+    }
     double vx = v[i] + hk * f[i];
     double vy = v[N + i] + hk * f[N + i];
     double vz = v[2 * N + i] + hk * f[2 * N + i];
@@ -39,7 +47,6 @@ __global__ void kick_drift_kernel(int n, double hk, double dt, float half_skin2,
     r.y += dt * vy;
     r.z += dt * vz;
     xr[i] = r;
-    float4 q = xq[i];
     q.x = (float)r.x;
     q.y = (float)r.y;
     q.z = (float)r.z;
@@ -59,7 +66,8 @@ __global__ void load_state_kernel(int n, const Grid *__restrict__ grids,
                                   float4 *__restrict__ xq, double4 *__restrict__ xabs,
                                   double *__restrict__ v, int32_t *__restrict__ orig,
                                   int32_t *__restrict__ cell, const int64_t *__restrict__ atom_off,
-                                  int R, uint16_t *__restrict__ rep, DevStatus *ds) {
+                                  int R, uint16_t *__restrict__ rep, DevStatus *ds,
+                                  const int32_t *__restrict__ type_orig) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
         ds->abs_fresh = 1;
@@ -86,7 +94,8 @@ __global__ void load_state_kernel(int n, const Grid *__restrict__ grids,
                                        wrap_coord(pos[3 * (size_t)i + 2], g.L[2]), 0.0);
         xr[i] = a;
         xabs[i] = a;
-        xq[i] = make_float4((float)a.x, (float)a.y, (float)a.z, __int_as_float(i));
+        const uint32_t w = (uint32_t)i | (type_orig ? (uint32_t)type_orig[i] << kIndexBits : 0u);
+        xq[i] = make_float4((float)a.x, (float)a.y, (float)a.z, __uint_as_float(w));
         orig[i] = i;
         cell[i] = -1;
     }
@@ -191,13 +200,19 @@ __global__ void partial_pe_kernel(int n, const double *__restrict__ e, double *p
 }
 
 __global__ void partial_ke_kernel(int n, double half_m, const double *__restrict__ v,
-                                  double *partials) {
+                                  double *partials, const float4 *__restrict__ xq_typed,
+                                  double4 half_m_t) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const size_t N = (size_t)n;
     double x = 0.0;
     if (i < n) {
+        double hm = half_m;
+        if (xq_typed) {  // multi-element: the species' mass
+            const int t = species_of(__float_as_uint(xq_typed[i].w));
+            hm = t < 2 ? (t == 0 ? half_m_t.x : half_m_t.y) : (t == 2 ? half_m_t.z : half_m_t.w);
+        }
         double a = v[i], b = v[N + i], c = v[2 * N + i];
-        x = half_m * (a * a + b * b + c * c);
+        x = hm * (a * a + b * b + c * c);
     }
     double t = block_sum(x);
     if (threadIdx.x == 0) partials[blockIdx.x] = t;
@@ -240,9 +255,12 @@ __global__ void replica_energy_kernel(const Grid *__restrict__ grids,
 
 cudaError_t launch_kick_drift(md_system *h) {
     int n = (int)h->n;
+    const double *im = h->fc.t_inv_m;
+    const double hd = 0.5 * h->p.dt;
     kick_drift_kernel<<<nblocks(n), kBlock, 0, h->stream>>>(
         n, 0.5 * h->p.dt / h->p.mass, h->p.dt, h->fc.half_skin2f, h->p.rebuild_every,
-        h->xr64[h->cur], h->xq[h->cur], h->xq_build, h->v, h->f, h->ds);
+        h->xr64[h->cur], h->xq[h->cur], h->xq_build, h->v, h->f, h->ds, h->fc.ntypes,
+        make_double4(hd * im[0], hd * im[1], hd * im[2], hd * im[3]));
     return cudaGetLastError();
 }
 
@@ -251,7 +269,7 @@ cudaError_t launch_load_state(md_system *h, const double *pos, const double *vel
     if (pos) {
         load_state_kernel<<<nblocks(n), kBlock, 0, h->stream>>>(
             n, h->grids, pos, vel, h->xr64[h->cur], h->xq[h->cur], h->xabs, h->v, h->orig, h->cell,
-            h->atom_off, h->R, h->rep, h->ds);
+            h->atom_off, h->R, h->rep, h->ds, h->type_orig);
     } else if (vel) {
         load_vel_kernel<<<nblocks(n), kBlock, 0, h->stream>>>(n, vel, h->orig, h->v);
     }
@@ -294,7 +312,10 @@ cudaError_t launch_reduce_pe(md_system *h) {
 
 cudaError_t launch_reduce_ke(md_system *h) {
     int n = (int)h->n, nb = nblocks(n);
-    partial_ke_kernel<<<nb, kBlock, 0, h->stream>>>(n, 0.5 * h->p.mass, h->v, h->partials);
+    const double *m = h->types_mass;
+    partial_ke_kernel<<<nb, kBlock, 0, h->stream>>>(
+        n, 0.5 * h->p.mass, h->v, h->partials, h->fc.ntypes > 0 ? h->xq[h->cur] : nullptr,
+        make_double4(0.5 * m[0], 0.5 * m[1], 0.5 * m[2], 0.5 * m[3]));
     final_sum_kernel<<<1, kBlock, 0, h->stream>>>(nb, h->partials, h->red_out + 1);
     return cudaGetLastError();
 }

@@ -371,6 +371,209 @@ __global__ void __launch_bounds__(kBlock) lj_fp64_kernel(ForceArgs a, int store_
     if (i < a.n) lj_fp64_atom<MODE, ENERGY>(a, sh, i, store_f);
 }
 
+// ---- multi-element Lennard-Jones (Sec. 2.2 pair loop, Sec. 3.1 Cu-Au) ------
+//
+// The paper's SIMD loop reloads the parameters of each pair with masks.  Here
+// the lane keeps the row of its own species (NT values of each parameter) in
+// registers and picks the pair's entry with the species of j, which sits in
+// the position word it loads anyway: selects instead of loads.
+
+template <int NT>
+__device__ __forceinline__ float pick_row(const float *row, int t) {
+    if (NT == 1) return row[0];
+    if (NT == 2) return t ? row[1] : row[0];
+    if (NT == 3) return t == 0 ? row[0] : (t == 1 ? row[1] : row[2]);
+    return t < 2 ? (t == 0 ? row[0] : row[1]) : (t == 2 ? row[2] : row[3]);
+}
+template <int NT>
+__device__ __forceinline__ double pick_row(const double *row, int t) {
+    if (NT == 1) return row[0];
+    if (NT == 2) return t ? row[1] : row[0];
+    if (NT == 3) return t == 0 ? row[0] : (t == 1 ? row[1] : row[2]);
+    return t < 2 ? (t == 0 ? row[0] : row[1]) : (t == 2 ? row[2] : row[3]);
+}
+// row ti of an NT x NT table, into registers (constant indices only)
+template <int NT, class T>
+__device__ __forceinline__ void load_row(const T *tab, int ti, T *row) {
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+        T v = tab[k];
+#pragma unroll
+        for (int r = 1; r < NT; ++r) v = (ti == r) ? tab[r * NT + k] : v;
+        row[k] = v;
+    }
+}
+
+template <int MODE, bool ENERGY, int NT>
+__device__ __forceinline__ void lj_typed_mixed_atom(const ForceArgs &a, const TypeTab &tt,
+                                                    const ShiftTab *sh, int i, int store_f) {
+    const float4 qi = a.xq[i];
+    const int ti = species_of(__float_as_uint(qi.w));
+    float e48[NT], e4[NT], s2[NT], shf[NT];
+    load_row<NT>(tt.e48, ti, e48);
+    load_row<NT>(tt.e4, ti, e4);
+    load_row<NT>(tt.s2, ti, s2);
+    load_row<NT>(tt.sh, ti, shf);
+    const int nq = (min(a.ncount[i], a.cap) + 3) >> 2;
+    const uint4 *lq = reinterpret_cast<const uint4 *>(a.nlist + list_group(i, a.cap)) + (i & 31);
+    const float rc2 = a.fc.rc2f;
+    double Fx = 0.0, Fy = 0.0, Fz = 0.0, E = 0.0;
+    unsigned npair = 0;
+    float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+    auto pair = [&](uint32_t ent) {
+        const float4 qj = __ldg(a.xq + (ent & kIndexMask));
+        const uint32_t st = ent >> kIndexBits;
+        const float ex = (qj.x - qi.x) + sh->x[st];
+        const float ey = (qj.y - qi.y) + sh->y[st];
+        const float ez = (qj.z - qi.z) + sh->z[st];
+        const float r2 = ex * ex + ey * ey + ez * ez;
+        if (r2 < rc2) {
+            const int tj = species_of(__float_as_uint(qj.w));
+            const float r2i = __fdividef(1.0f, r2);
+            float s6 = pick_row<NT>(s2, tj) * r2i;
+            s6 = s6 * s6 * s6;
+            const float fs = pick_row<NT>(e48, tj) * r2i * s6 * (s6 - 0.5f);
+            fx -= fs * ex;
+            fy -= fs * ey;
+            fz -= fs * ez;
+            if (ENERGY) {
+                e += pick_row<NT>(e4, tj) * s6 * (s6 - 1.0f) - pick_row<NT>(shf, tj);
+                ++npair;
+            }
+        }
+    };
+    uint4 nxt = nq > 0 ? __ldcs(lq) : make_uint4(0u, 0u, 0u, 0u);
+    for (int q0 = 0; q0 < nq; q0 += kChunkQ) {
+        const int q1 = min(q0 + kChunkQ, nq);
+        for (int q = q0; q < q1; ++q) {
+            const uint4 e4q = nxt;
+            if (q + 1 < nq) nxt = __ldcs(lq + (size_t)(q + 1) * 32);
+            pair(e4q.x);
+            pair(e4q.y);
+            pair(e4q.z);
+            pair(e4q.w);
+        }
+        Fx += (double)fx;
+        Fy += (double)fy;
+        Fz += (double)fz;
+        fx = fy = fz = 0.f;
+        if (ENERGY) {
+            E += (double)e;
+            e = 0.f;
+        }
+    }
+    const size_t n = (size_t)a.n;
+    if (MODE == FM_STORE || store_f) {
+        a.f[i] = Fx;
+        a.f[n + i] = Fy;
+        a.f[2 * n + i] = Fz;
+    }
+    if (ENERGY) {
+        a.e_atom[i] = 0.5 * E;
+        count_pairs(a.ds, npair);
+    }
+    if (MODE != FM_STORE) vv_epilogue<MODE>(a, i, Fx, Fy, Fz, qi.w);
+}
+
+template <int MODE, bool ENERGY, int NT>
+__device__ __forceinline__ void lj_typed_fp64_atom(const ForceArgs &a, const TypeTab &tt,
+                                                   const double3 *sh, int i, int store_f) {
+    const double4 ri = a.xr[i];
+    const float4 qi = a.xq[i];
+    const int ti = species_of(__float_as_uint(qi.w));
+    double e48[NT], e4[NT], s2[NT], shd[NT];
+    load_row<NT>(tt.e48d, ti, e48);
+    load_row<NT>(tt.e4d, ti, e4);
+    load_row<NT>(tt.s2d, ti, s2);
+    load_row<NT>(tt.shd, ti, shd);
+    const int cnt = min(a.ncount[i], a.cap);
+    const double rc2 = a.fc.rc2;
+    double fx = 0.0, fy = 0.0, fz = 0.0, e = 0.0;
+    unsigned npair = 0;
+    for (int k = 0; k < cnt; ++k) {
+        const uint32_t ent = __ldg(a.nlist + list_idx(i, k, a.cap));
+        const int j = (int)(ent & kIndexMask);
+        const double4 rj = a.xr[j];
+        const double3 sd = sh[ent >> kIndexBits];
+        const double ex = (rj.x - ri.x) + sd.x;
+        const double ey = (rj.y - ri.y) + sd.y;
+        const double ez = (rj.z - ri.z) + sd.z;
+        const double r2 = ex * ex + ey * ey + ez * ez;
+        if (r2 < rc2) {
+            const int tj = species_of(__float_as_uint(__ldg(&a.xq[j].w)));
+            const double r2i = 1.0 / r2;
+            double s6 = pick_row<NT>(s2, tj) * r2i;
+            s6 = s6 * s6 * s6;
+            const double fs = pick_row<NT>(e48, tj) * r2i * s6 * (s6 - 0.5);
+            fx -= fs * ex;
+            fy -= fs * ey;
+            fz -= fs * ez;
+            if (ENERGY) {
+                e += pick_row<NT>(e4, tj) * s6 * (s6 - 1.0) - pick_row<NT>(shd, tj);
+                ++npair;
+            }
+        }
+    }
+    const size_t n = (size_t)a.n;
+    if (MODE == FM_STORE || store_f) {
+        a.f[i] = fx;
+        a.f[n + i] = fy;
+        a.f[2 * n + i] = fz;
+    }
+    if (ENERGY) {
+        a.e_atom[i] = 0.5 * e;
+        count_pairs(a.ds, npair);
+    }
+    if (MODE != FM_STORE) vv_epilogue<MODE>(a, i, fx, fy, fz, qi.w);
+}
+
+template <int MODE, bool ENERGY, int NT, bool F64>
+__global__ void __launch_bounds__(128) lj_typed_kernel(ForceArgs a, TypeTab tt, int store_f) {
+    __shared__ ShiftTab sh;
+    __shared__ double3 sh64[F64 ? kStencil : 1];
+    if (F64) load_shifts_f64(a.g, sh64);
+    else load_shifts_f32(a.g, &sh);
+    __syncthreads();
+    if (a.ds->status != 0) return;
+    step_bookkeeping<MODE>(a);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    if (F64) lj_typed_fp64_atom<MODE, ENERGY, NT>(a, tt, sh64, i, store_f);
+    else lj_typed_mixed_atom<MODE, ENERGY, NT>(a, tt, &sh, i, store_f);
+}
+
+template <int NT, bool F64>
+cudaError_t launch_lj_typed_nt(md_system *h, const ForceArgs &a, int mode, bool energy, int sf) {
+    const int nb = nblocks(a.n, 128);
+    cudaStream_t s = h->stream;
+    const TypeTab &tt = h->types;
+    switch (mode) {
+        case FM_STORE:
+            if (energy) lj_typed_kernel<FM_STORE, true, NT, F64><<<nb, 128, 0, s>>>(a, tt, sf);
+            else lj_typed_kernel<FM_STORE, false, NT, F64><<<nb, 128, 0, s>>>(a, tt, sf);
+            break;
+        case FM_FUSED_FULL:
+            if (energy) lj_typed_kernel<FM_FUSED_FULL, true, NT, F64><<<nb, 128, 0, s>>>(a, tt, sf);
+            else lj_typed_kernel<FM_FUSED_FULL, false, NT, F64><<<nb, 128, 0, s>>>(a, tt, sf);
+            break;
+        default:
+            if (energy) lj_typed_kernel<FM_FUSED_HALF, true, NT, F64><<<nb, 128, 0, s>>>(a, tt, sf);
+            else lj_typed_kernel<FM_FUSED_HALF, false, NT, F64><<<nb, 128, 0, s>>>(a, tt, sf);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+template <bool F64>
+cudaError_t launch_lj_typed_p(md_system *h, const ForceArgs &a, int mode, bool energy, int sf) {
+    switch (h->fc.ntypes) {
+        case 1: return launch_lj_typed_nt<1, F64>(h, a, mode, energy, sf);
+        case 2: return launch_lj_typed_nt<2, F64>(h, a, mode, energy, sf);
+        case 3: return launch_lj_typed_nt<3, F64>(h, a, mode, energy, sf);
+        default: return launch_lj_typed_nt<4, F64>(h, a, mode, energy, sf);
+    }
+}
+
 ForceArgs make_force_args(md_system *h) {
     ForceArgs a;
     a.n = (int)h->n;
@@ -405,6 +608,10 @@ cudaError_t launch_lj(md_system *h, int mode, bool energy, bool store_f) {
     const int nb = nblocks(a.n);
     const int sf = store_f ? 1 : 0;
     cudaStream_t s = h->stream;
+    if (h->fc.ntypes > 0) {
+        return h->p.precision == MD_MIXED ? launch_lj_typed_p<false>(h, a, mode, energy, sf)
+                                          : launch_lj_typed_p<true>(h, a, mode, energy, sf);
+    }
 #define MDG_LJ(K, M, E) K<M, E><<<nb, kBlock, 0, s>>>(a, sf)
     if (h->R > 1) {
         // several boxes: mixed precision only (checked at creation)

@@ -92,7 +92,7 @@ void free_all(md_system *h) {
     F(h->cell_start); F(h->cell_count); F(h->new_cell); F(h->slot); F(h->src); F(h->key);
     F(h->scan_bsum); F(h->tmp_abs); F(h->tmp_v); F(h->nlist); F(h->ncount);
     F(h->rho); F(h->dF32); F(h->dF64); F(h->xqf); F(h->partials); F(h->red_out); F(h->ds);
-    F(h->exp_tmp);
+    F(h->exp_tmp); F(h->type_orig);
     F(h->part_bounds); F(h->cell_cost); F(h->part_scratch); F(h->cell_X); F(h->cell_pred);
     F(h->cell_cycles); F(h->cta_cycles); F(h->samp_flag); F(h->samp_bsum); F(h->samp_X);
     F(h->samp_y); F(h->mlp_P); F(h->mlp_G); F(h->mlp_m); F(h->mlp_v); F(h->mlp_scratch);
@@ -518,9 +518,52 @@ static md_status eam_table(const md_params *p, const md_eam *e, EamTab *t, std::
     return MD_OK;
 }
 
+// Species tables of a multi-element Lennard-Jones system, checked and
+// converted for the kernels (species of every atom checked on the host).
+static md_status type_tables(const md_params *p, const md_lj_types *t, const int32_t *type_dev,
+                             int64_t n, TypeTab *tab, std::vector<int32_t> *types,
+                             std::string *why) {
+    auto bad = [&](const std::string &m) { *why = m; return MD_ERR_INVALID; };
+    if (!t || !type_dev) return bad("null species table or species array");
+    if (p->potential != MD_POT_LJ) return bad("species tables are for Lennard-Jones");
+    const int nt = t->ntypes;
+    if (nt < 1 || nt > kMaxTypes) return bad("ntypes must be in [1, 4]");
+    *tab = TypeTab{};
+    const double rc2 = p->rc * p->rc;
+    for (int a = 0; a < nt; ++a) {
+        if (!(t->mass[a] > 0) || !std::isfinite(t->mass[a])) return bad("masses must be > 0");
+        for (int b = 0; b < nt; ++b) {
+            const double e = t->eps[a * nt + b], sg = t->sigma[a * nt + b];
+            if (!(e > 0) || !(sg > 0) || !std::isfinite(e + sg))
+                return bad("eps and sigma must be > 0");
+            if (e != t->eps[b * nt + a] || sg != t->sigma[b * nt + a])
+                return bad("eps and sigma must be symmetric");
+            const double s2 = sg * sg, sr6 = std::pow(s2 / rc2, 3);
+            const int k = a * nt + b;
+            tab->e48d[k] = 48 * e;
+            tab->e4d[k] = 4 * e;
+            tab->s2d[k] = s2;
+            tab->shd[k] = 4 * e * (sr6 * sr6 - sr6);
+            tab->e48[k] = (float)tab->e48d[k];
+            tab->e4[k] = (float)tab->e4d[k];
+            tab->s2[k] = (float)s2;
+            tab->sh[k] = (float)tab->shd[k];
+        }
+    }
+    types->resize((size_t)n);
+    if (cudaMemcpy(types->data(), type_dev, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return bad("could not read the species array");
+    for (int32_t v : *types)
+        if (v < 0 || v >= nt) return bad("a species lies outside [0, ntypes)");
+    return MD_OK;
+}
+
 static md_status create_impl(md_system **out, const md_params *p, int R, const int64_t *n_each,
                              const double *boxes, const double *pos_dev, const double *vel_dev,
-                             void *cuda_stream, const char *who, const md_eam *eam = nullptr) {
+                             void *cuda_stream, const char *who, const md_eam *eam = nullptr,
+                             const md_lj_types *ltypes = nullptr,
+                             const int32_t *type_dev = nullptr) {
     md_system *h = nullptr;
     const std::string W(who);
     if (!out || !p || !boxes || !pos_dev || !n_each || R < 1)
@@ -546,6 +589,15 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
     } else if (eam) {
         return fail(nullptr, MD_ERR_INVALID, W + ": an EAM table needs MD_POT_EAM");
     }
+    TypeTab type_t{};
+    std::vector<int32_t> types_h;
+    if (ltypes) {
+        if (type_tables(p, ltypes, type_dev, n, &type_t, &types_h, &why) != MD_OK)
+            return fail(nullptr, MD_ERR_INVALID, W + ": " + why);
+        if (R != 1 || p->force_variant != MD_FORCE_FULL || p->scheduler != MD_SCHED_GRID)
+            return fail(nullptr, MD_ERR_INVALID,
+                        W + ": multi-element systems run full lists under MD_SCHED_GRID");
+    }
     if (p->force_variant != MD_FORCE_FULL && p->potential != MD_POT_LJ)
         return fail(nullptr, MD_ERR_INVALID, W + ": half lists are built for Lennard-Jones only");
     if (p->force_variant != MD_FORCE_FULL && p->precision != MD_MIXED)
@@ -560,6 +612,7 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
     if (!h) return fail(nullptr, MD_ERR_OOM, W + ": host allocation failed");
     h->p = *p;
     h->eam = eam_t;
+    h->types = type_t;
     h->n = n;
     h->R = R;
     h->stream = (cudaStream_t)cuda_stream;
@@ -607,6 +660,12 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
     fc.sc_af = (float)p->sigma; fc.sc_epsf = (float)p->eps; fc.sc_ecf = (float)(p->eps * p->c);
     fc.sc_n = (int)p->n_exp; fc.sc_m = (int)p->m_exp;
     fc.dt = p->dt; fc.inv_m = 1.0 / p->mass;
+    fc.ntypes = ltypes ? ltypes->ntypes : 0;
+    for (int t = 0; t < kMaxTypes; ++t) {
+        const double m = (ltypes && t < ltypes->ntypes) ? ltypes->mass[t] : p->mass;
+        fc.t_inv_m[t] = 1.0 / m;
+        h->types_mass[t] = m;
+    }
     fc.half_skin2f = (float)(0.25 * p->skin * p->skin);
 
     const size_t N = (size_t)n, C = (size_t)cells_total;
@@ -636,6 +695,12 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
     h->nblocks_n = nblocks(n);
     A(dalloc(&h->partials, (size_t)h->nblocks_n + 1)); A(dalloc(&h->red_out, 4));
     A(dalloc(&h->ds, 1));
+    if (ltypes) {
+        A(dalloc(&h->type_orig, N));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(h->type_orig, types_h.data(), N * sizeof(int32_t),
+                           cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->ds_host, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&h->red_host, 4 * sizeof(double));
     if (e != cudaSuccess) {
@@ -712,6 +777,15 @@ md_status md_create_eam(md_system **out, const md_params *p, const md_eam *eam_h
                        eam_host);
 }
 
+md_status md_create_typed(md_system **out, const md_params *p, const md_lj_types *types_host,
+                          const int32_t *type_dev, int64_t n, const double *box3_host,
+                          const double *pos_dev, const double *vel_dev, void *cuda_stream) {
+    if (!types_host || !type_dev)
+        return fail(nullptr, MD_ERR_INVALID, "md_create_typed: null species table or array");
+    return create_impl(out, p, 1, &n, box3_host, pos_dev, vel_dev, cuda_stream,
+                       "md_create_typed", nullptr, types_host, type_dev);
+}
+
 md_status md_create_batch(md_system **out, const md_params *p, int32_t n_replicas,
                           const int64_t *n_each_host, const double *box3_each_host,
                           const double *pos_dev, const double *vel_dev, void *cuda_stream) {
@@ -721,6 +795,7 @@ md_status md_create_batch(md_system **out, const md_params *p, int32_t n_replica
 
 md_status md_energy_batch(md_system *h, double *ke_host, double *pe_host) {
     if (!h) return fail(nullptr, MD_ERR_INVALID, "md_energy_batch: null handle");
+    if (h->fc.ntypes > 0) return md_energy(h, ke_host, pe_host);  // one box, species masses
     MD_CK(cudaMemsetAsync(&h->ds->pairs_cut, 0, sizeof(unsigned long long), h->stream));
     md_status st = forces_now(h, true);
     if (st != MD_OK) return st;
@@ -953,9 +1028,11 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
     if (force_variant < MD_FORCE_FULL || force_variant > MD_FORCE_HALF_ATOMIC ||
         scheduler < MD_SCHED_GRID || scheduler > MD_SCHED_DYNAMIC)
         return fail(h, MD_ERR_INVALID, "md_set_variant: unknown variant or scheduler");
-    if (h->p.potential == MD_POT_EAM && (force_variant != MD_FORCE_FULL || scheduler != MD_SCHED_GRID))
+    if ((h->p.potential == MD_POT_EAM || h->fc.ntypes > 0) &&
+        (force_variant != MD_FORCE_FULL || scheduler != MD_SCHED_GRID))
         return fail(h, MD_ERR_INVALID,
-                    "md_set_variant: the embedded-atom potential runs full lists under MD_SCHED_GRID");
+                    "md_set_variant: embedded-atom and multi-element systems run full lists "
+                    "under MD_SCHED_GRID");
     if (force_variant != MD_FORCE_FULL && h->p.potential == MD_POT_SC)
         return fail(h, MD_ERR_INVALID, "md_set_variant: half lists are built for Lennard-Jones only");
     if (force_variant != MD_FORCE_FULL && h->p.precision != MD_MIXED)
@@ -1031,7 +1108,7 @@ md_status cta_imbalance(md_system *h, float *out) {
 md_status md_cost_model(md_system *h, int32_t op, float *loss_out) {
     if (!h) return fail(nullptr, MD_ERR_INVALID, "md_cost_model: null handle");
     if (h->p.potential != MD_POT_LJ || h->p.precision != MD_MIXED ||
-        h->p.force_variant != MD_FORCE_FULL || h->R > 1)
+        h->p.force_variant != MD_FORCE_FULL || h->R > 1 || h->fc.ntypes > 0)
         return fail(h, MD_ERR_INVALID,
                     "md_cost_model: the cost model drives the persistent mixed-precision "
                     "Lennard-Jones full-list force kernel of a single box");

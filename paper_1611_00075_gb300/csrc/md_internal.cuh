@@ -137,6 +137,25 @@ struct ForceConsts {
     // integrator
     double dt, inv_m;
     float half_skin2f;
+    // multi-element Lennard-Jones: species count (0 = one species) and the
+    // inverse mass of each species; an atom's species sits in bits 27-28 of
+    // its float32 position's w word, above the original id
+    int ntypes;
+    double t_inv_m[4];
+};
+
+constexpr int kMaxTypes = 4;
+// species of a position word: bits 27-28 above the original id
+__host__ __device__ __forceinline__ int species_of(uint32_t w) { return (int)(w >> 27) & 3; }
+__device__ __forceinline__ double pick4(const double *v, int t) {
+    return t < 2 ? (t == 0 ? v[0] : v[1]) : (t == 2 ? v[2] : v[3]);
+}
+
+// Pair parameters of a multi-element Lennard-Jones system, [t_i * nt + t_j]:
+// 48 eps, 4 eps, sigma^2 and the energy shift at r_c, in float32 and float64.
+struct TypeTab {
+    float e48[16], e4[16], s2[16], sh[16];
+    double e48d[16], e4d[16], s2d[16], shd[16];
 };
 
 // Piecewise embedded-atom tables (MD_POT_EAM), passed to the kernels by value
@@ -179,6 +198,9 @@ struct md_system {
     double *rep_ke = nullptr, *rep_pe = nullptr;  // per-replica sums (device)
     mdg::ForceConsts fc{};
     mdg::EamTab eam{};  // MD_POT_EAM only
+    mdg::TypeTab types{};        // multi-element Lennard-Jones only
+    int32_t *type_orig = nullptr;  // species of each atom, original order (typed only)
+    double types_mass[4] = {0, 0, 0, 0};  // mass of each species (typed only)
     double r_list = 0.0;
     float list_lo = 0.f, list_hi = 0.f;  // fp32 prefilter band around r_list^2
     double rl2 = 0.0;

@@ -60,6 +60,29 @@ class md_eam(C.Structure):
                 ("F_sqrt", C.c_double), ("F_quad", C.c_double)]
 
 
+MD_MAX_TYPES = 4
+
+
+class md_lj_types(C.Structure):
+    _fields_ = [("ntypes", C.c_int32), ("reserved", C.c_int32),
+                ("eps", C.c_double * (MD_MAX_TYPES * MD_MAX_TYPES)),
+                ("sigma", C.c_double * (MD_MAX_TYPES * MD_MAX_TYPES)),
+                ("mass", C.c_double * MD_MAX_TYPES)]
+
+
+def make_lj_types(t_eps, t_sigma, t_mass) -> md_lj_types:
+    """Species table from nt x nt eps and sigma and nt masses (nested lists or arrays)."""
+    t = md_lj_types()
+    nt = len(t_mass)
+    t.ntypes = nt
+    for a in range(nt):
+        t.mass[a] = float(t_mass[a])
+        for b in range(nt):
+            t.eps[a * nt + b] = float(t_eps[a][b])
+            t.sigma[a * nt + b] = float(t_sigma[a][b])
+    return t
+
+
 def make_eam(phi_r, phi_a, psi_r, psi_a, F_sqrt, F_quad) -> md_eam:
     t = md_eam()
     t.n_phi, t.n_psi = len(phi_r), len(psi_r)
@@ -87,6 +110,8 @@ def lib() -> C.CDLL:
         "md_create": [C.POINTER(vp), C.POINTER(md_params), i64, vp, vp, vp, vp],
         "md_create_eam": [C.POINTER(vp), C.POINTER(md_params), C.POINTER(md_eam), i64, vp, vp,
                           vp, vp],
+        "md_create_typed": [C.POINTER(vp), C.POINTER(md_params), C.POINTER(md_lj_types), vp,
+                            i64, vp, vp, vp, vp],
         "md_bin_cells": [vp], "md_build_neighbors": [vp], "md_forces": [vp],
         "md_step": [vp, i64], "md_energy": [vp, vp, vp],
         "md_get_state": [vp, vp, vp, vp], "md_set_state": [vp, vp, vp],
@@ -170,6 +195,20 @@ def md_create_eam(params: md_params, eam: md_eam, pos: torch.Tensor, vel: torch.
     st = lib().md_create_eam(C.byref(h), C.byref(params), C.byref(eam), n,
                              C.cast(box_arr, C.c_void_p), _ptr(pos), _ptr(vel), _stream(stream))
     _check(st, None, "md_create_eam")
+    return h.value
+
+
+def md_create_typed(params: md_params, types: md_lj_types, type_dev: torch.Tensor,
+                    pos: torch.Tensor, vel: torch.Tensor | None, box, stream=None) -> int:
+    n = pos.shape[0]
+    assert pos.dtype == torch.float64 and pos.shape == (n, 3)
+    assert type_dev.dtype == torch.int32 and type_dev.numel() == n
+    box_arr = (C.c_double * 3)(*[float(b) for b in box])
+    h = C.c_void_p()
+    st = lib().md_create_typed(C.byref(h), C.byref(params), C.byref(types), _ptr(type_dev), n,
+                               C.cast(box_arr, C.c_void_p), _ptr(pos), _ptr(vel),
+                               _stream(stream))
+    _check(st, None, "md_create_typed")
     return h.value
 
 
@@ -336,9 +375,11 @@ class System:
     """Owns one md_system handle.  pos/vel: (n, 3) float64 tensors (any device;
     copied to the GPU), box: 3 floats, params: md_params or keyword dict."""
 
-    def __init__(self, pos, vel, box, params=None, stream=None, eam=None, **kw):
+    def __init__(self, pos, vel, box, params=None, stream=None, eam=None, species=None, **kw):
         """eam: an md_eam table (or a dict of make_eam's arguments) for the
-        embedded-atom potential (md_create_eam)."""
+        embedded-atom potential (md_create_eam).  species: (types, t_eps,
+        t_sigma, t_mass) of a multi-element Lennard-Jones system
+        (md_create_typed)."""
         self.h = None
         if eam is not None:
             kw.setdefault("potential", "eam")
@@ -358,6 +399,11 @@ class System:
         self.box = [float(b) for b in box]
         if eam is not None:
             self.h = md_create_eam(params, eam, p, v, self.box, stream)
+        elif species is not None:
+            types, t_eps, t_sigma, t_mass = species
+            td = torch.as_tensor(types, dtype=torch.int32).to(dev).contiguous()
+            self.h = md_create_typed(params, make_lj_types(t_eps, t_sigma, t_mass), td, p, v,
+                                     self.box, stream)
         else:
             self.h = md_create(params, p, v, self.box, stream)
 

@@ -165,6 +165,26 @@ def test_eam_fe126_4m(md, orc):
     check_forces(orc, prm, f, pos, s.box, idx, ooff, oids, p["rc"], 2e-4, 1e-5)
 
 
+def test_alloy_4_6m(md, orc):
+    """The Cu-Au-like random alloy on 105^3 fcc cells (4,630,500 atoms, the
+    paper's Alloy size), mixed path with species parameters and masses."""
+    s = inputs.lj_alloy(nc=105)
+    p = s.params
+    sp = (p["types"], p["t_eps"], p["t_sigma"], p["t_mass"])
+    prm = orc.make_params(potential=orc.POT_LJ, rc=p["rc"], skin=p["skin"], dt=p["dt"],
+                          types=p["types"], t_eps=p["t_eps"], t_sigma=p["t_sigma"],
+                          t_mass=p["t_mass"])
+    with md.System(s.pos, s.vel, s.box, precision="mixed", species=sp, rc=p["rc"],
+                   skin=p["skin"], dt=p["dt"]) as a:
+        assert a.n == 4630500
+        a.step(10)
+        pos = perturbed(s.pos, s.box, 0.04, inputs.SEED_BASE + 315)
+        f = load(md, a, pos, s.vel)
+        idx = sample_ids(a.n, 300, inputs.SEED_BASE + 307)
+        ooff, oids = check_rows(orc, a, pos, s.box, p["rc"] + p["skin"], idx)
+    check_forces(orc, prm, f, pos, s.box, idx, ooff, oids, p["rc"], 2e-4, 1e-5)
+
+
 def test_ensemble_64_replicas(md, orc):
     """The 64-replica ensemble (2,428,400 atoms) as one batch: sampled atoms
     of each of eight replicas against the oracle on that replica's box."""
