@@ -408,6 +408,18 @@ def run_gpu(args, rank, world, local):
                 variants["full"] = {"atom_steps_per_s": sched_info["grid"]["atom_steps_per_s"],
                                     "force_ms_per_launch": sched_info["grid"]["force_ms_per_launch"]}
                 sched_info["force_variants"] = variants
+                # the inner/outer split of Sec. 2.1 (virtual domains, boundary
+                # positions exchanged on a second stream) against the fused pass
+                split = {"fused": variants["full"]}
+                for dd in ((2, 2, 2), (4, 4, 4)):
+                    from_s0(md.MD_FORCE_FULL, md.MD_SCHED_GRID)
+                    md.md_set_decomposition(mixed.h, *dd)
+                    msx, stx = timed(mixed, args.compare_steps)
+                    split["%dx%dx%d" % dd] = {
+                        "atom_steps_per_s": n_of(mixed) * args.compare_steps / (msx * 1e-3),
+                        "force_ms_per_launch": stx["ms"]["force"] / max(1, stx["count"]["force"])}
+                    md.md_set_decomposition(mixed.h, 1, 1, 1)
+                sched_info["inner_outer_split"] = split
             from_s0(md.MD_FORCE_FULL, sched)
         else:
             md.md_set_variant(mixed.h, md.MD_FORCE_FULL, sched)

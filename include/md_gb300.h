@@ -290,6 +290,24 @@ md_status md_cost_model(md_system *h, int32_t op, float *loss_out);
  * Synchronizes. */
 md_status md_set_timing(md_system *h, int32_t on);
 
+/* The inner/outer split of the force pass that lets the paper's domain
+ * decomposition communicate while it computes (Sec. 2.1, the seven-step
+ * pair-force algorithm), on one GPU: the cell grid is cut into px x py x pz
+ * virtual domains (blocks of cells, floor(c p / n) along each dimension).
+ * Each force pass then (1) packs the float32 positions of atoms whose cell
+ * touches a domain face into one send buffer, (2-3) copies it into a receive
+ * buffer on a second stream -- the stand-in for the transfer between
+ * domains --, (4) computes every atom's intra-domain forces meanwhile
+ * (interior atoms finish their step there), (5) waits for the copy and
+ * (6) adds the inter-domain forces of the boundary atoms, their foreign
+ * neighbours read from the receive buffer.  Forces equal the fused pass's up
+ * to the order of float32 partial sums.  (1, 1, 1) switches it off.  For the
+ * mixed-precision one-species Lennard-Jones full list of one box under
+ * MD_SCHED_GRID; MD_ERR_INVALID otherwise or for more domains than cells.
+ * Captured step graphs are dropped; the split steps are captured again, both
+ * streams joined by events. */
+md_status md_set_decomposition(md_system *h, int32_t px, int32_t py, int32_t pz);
+
 /* Shape of the static partition used by MD_SCHED_PAIRCOUNT and MD_SCHED_MLP
  * (the load-balance question of Sec. 1 and Sec. 2.1 for inhomogeneous
  * systems): rounds = equal-cost ranges per persistent CTA (1..8; 0 = sized

@@ -55,12 +55,14 @@ __device__ __forceinline__ void load_shifts_f32(const Grid &g, ShiftTab *sh) {
 ForceArgs make_force_args(md_system *h);
 
 // Shared epilogue: kick (and drift) of atom i with its float64 force.
-template <int MODE>
+// SPECIES: a multi-element system, whose atom takes its species' mass (a
+// compile-time switch: a run-time test here cost the persistent kernel 6 %).
+template <int MODE, bool SPECIES = false>
 __device__ __forceinline__ void vv_epilogue(const ForceArgs &a, int i, double Fx, double Fy,
                                             double Fz, float qw) {
     const size_t n = (size_t)a.n;
     double im = a.fc.inv_m;
-    if (a.fc.ntypes > 0) im = pick4(a.fc.t_inv_m, species_of(__float_as_uint(qw)));
+    if (SPECIES) im = pick4(a.fc.t_inv_m, species_of(__float_as_uint(qw)));
     const double hk = (MODE == FM_FUSED_FULL) ? a.fc.dt * im : 0.5 * a.fc.dt * im;
     double vx = a.v[i] + hk * Fx;
     double vy = a.v[n + i] + hk * Fy;

@@ -472,7 +472,7 @@ __device__ __forceinline__ void lj_typed_mixed_atom(const ForceArgs &a, const Ty
         a.e_atom[i] = 0.5 * E;
         count_pairs(a.ds, npair);
     }
-    if (MODE != FM_STORE) vv_epilogue<MODE>(a, i, Fx, Fy, Fz, qi.w);
+    if (MODE != FM_STORE) vv_epilogue<MODE, true>(a, i, Fx, Fy, Fz, qi.w);
 }
 
 template <int MODE, bool ENERGY, int NT>
@@ -524,7 +524,7 @@ __device__ __forceinline__ void lj_typed_fp64_atom(const ForceArgs &a, const Typ
         a.e_atom[i] = 0.5 * e;
         count_pairs(a.ds, npair);
     }
-    if (MODE != FM_STORE) vv_epilogue<MODE>(a, i, fx, fy, fz, qi.w);
+    if (MODE != FM_STORE) vv_epilogue<MODE, true>(a, i, fx, fy, fz, qi.w);
 }
 
 template <int MODE, bool ENERGY, int NT, bool F64>

@@ -93,6 +93,11 @@ void free_all(md_system *h) {
     F(h->scan_bsum); F(h->tmp_abs); F(h->tmp_v); F(h->nlist); F(h->ncount);
     F(h->rho); F(h->dF32); F(h->dF64); F(h->xqf); F(h->partials); F(h->red_out); F(h->ds);
     F(h->exp_tmp); F(h->type_orig);
+    F(h->ov_cell_outer); F(h->ov_flag); F(h->ov_pos); F(h->ov_bsum); F(h->ov_gidx);
+    F(h->ov_bidx); F(h->ov_nb); F(h->ov_send); F(h->ov_recv);
+    if (h->ov_stream) cudaStreamDestroy(h->ov_stream);
+    for (cudaEvent_t ev : h->ov_ev)
+        if (ev) cudaEventDestroy(ev);
     F(h->part_bounds); F(h->cell_cost); F(h->part_scratch); F(h->cell_X); F(h->cell_pred);
     F(h->cell_cycles); F(h->cta_cycles); F(h->samp_flag); F(h->samp_bsum); F(h->samp_X);
     F(h->samp_y); F(h->mlp_P); F(h->mlp_G); F(h->mlp_m); F(h->mlp_v); F(h->mlp_scratch);
@@ -235,6 +240,10 @@ md_status enqueue_rebuild(md_system *h, bool gated) {
     MD_CK(launch_bin(h, gated));
     MD_CK(launch_build_list(h, true, gated));
     h->launches += kBinLaunches + 3;  // binning, list reset and build, finish
+    if (h->ov_on) {
+        MD_CK(launch_overlap_index(h, gated));
+        h->launches += 5;
+    }
     md_status st = enqueue_sched_prep(h, gated);
     if (st != MD_OK) return st;
     MD_CK(launch_finish_rebuild(h, gated));
@@ -268,6 +277,7 @@ md_status rebuild_now(md_system *h, bool size_from_count) {
         if (st != MD_OK) return st;
         MD_CK(alloc_list(h, cap_for(h->ds_host->max_count)));
     }
+    if (h->ov_on) MD_CK(launch_overlap_index(h, false));
     md_status st = enqueue_sched_prep(h, false);
     if (st != MD_OK) return st;
     MD_CK(launch_finish_rebuild(h, false));
@@ -285,6 +295,9 @@ md_status enqueue_forces(md_system *h, int mode, bool energy, bool store_f) {
         MD_CK(launch_eam_density(h));
         MD_CK(launch_eam_force(h, mode, energy, store_f));
         h->launches += 2;
+    } else if (h->ov_on) {
+        MD_CK(launch_overlap_forces(h, mode, energy, store_f));
+        h->launches += 4;
     } else if (h->p.force_variant != MD_FORCE_FULL) {
         int nl = 0;
         MD_CK(launch_lj_half(h, mode, energy, &nl));
@@ -893,6 +906,7 @@ md_status md_step(md_system *h, int64_t nsteps) {
             return fail(h, MD_ERR_LIST_OVERFLOW, "md_step: neighbour count exceeds max_neighbors");
         MD_CK(alloc_list(h, cap_for(h->ds_host->max_count)));
         MD_CK(launch_build_list(h, true, false));
+        if (h->ov_on) MD_CK(launch_overlap_index(h, false));
         st = enqueue_sched_prep(h, false);
         if (st != MD_OK) return st;
         MD_CK(launch_finish_rebuild(h, false));
@@ -1028,11 +1042,11 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
     if (force_variant < MD_FORCE_FULL || force_variant > MD_FORCE_HALF_ATOMIC ||
         scheduler < MD_SCHED_GRID || scheduler > MD_SCHED_DYNAMIC)
         return fail(h, MD_ERR_INVALID, "md_set_variant: unknown variant or scheduler");
-    if ((h->p.potential == MD_POT_EAM || h->fc.ntypes > 0) &&
+    if ((h->p.potential == MD_POT_EAM || h->fc.ntypes > 0 || h->ov_on) &&
         (force_variant != MD_FORCE_FULL || scheduler != MD_SCHED_GRID))
         return fail(h, MD_ERR_INVALID,
-                    "md_set_variant: embedded-atom and multi-element systems run full lists "
-                    "under MD_SCHED_GRID");
+                    "md_set_variant: embedded-atom, multi-element and split (inner/outer) "
+                    "systems run full lists under MD_SCHED_GRID");
     if (force_variant != MD_FORCE_FULL && h->p.potential == MD_POT_SC)
         return fail(h, MD_ERR_INVALID, "md_set_variant: half lists are built for Lennard-Jones only");
     if (force_variant != MD_FORCE_FULL && h->p.precision != MD_MIXED)
@@ -1064,6 +1078,67 @@ md_status md_set_schedule(md_system *h, int32_t rounds, int32_t tail_percent) {
     h->sched_rounds = rounds > 0 ? rounds : sched_rounds(h->n, h->sched_ctas);
     if (!h->list_valid) return rebuild_now(h, false);
     return enqueue_sched_prep(h, false);
+}
+
+md_status md_set_decomposition(md_system *h, int32_t px, int32_t py, int32_t pz) {
+    if (!h) return fail(nullptr, MD_ERR_INVALID, "md_set_decomposition: null handle");
+    const int p3[3] = {px, py, pz};
+    const int nd[3] = {h->g.nx, h->g.ny, h->g.nz};
+    for (int d = 0; d < 3; ++d)
+        if (p3[d] < 1 || p3[d] > nd[d])
+            return fail(h, MD_ERR_INVALID,
+                        "md_set_decomposition: 1 <= domains <= cells along every dimension");
+    const bool on = px * py * pz > 1;
+    if (on && (h->R > 1 || h->p.potential != MD_POT_LJ || h->p.precision != MD_MIXED ||
+               h->p.force_variant != MD_FORCE_FULL || h->p.scheduler != MD_SCHED_GRID ||
+               h->fc.ntypes > 0))
+        return fail(h, MD_ERR_INVALID,
+                    "md_set_decomposition: the inner/outer split runs the mixed-precision "
+                    "one-species Lennard-Jones full list of one box under MD_SCHED_GRID");
+    drop_graphs(h);  // the captured steps launch the other force path
+    h->ov_on = false;
+    h->dd[0] = px; h->dd[1] = py; h->dd[2] = pz;
+    if (!on) return MD_OK;
+    const size_t N = (size_t)h->n, C = (size_t)h->g.ncells;
+    if (!h->ov_cell_outer) {
+        cudaError_t e = cudaSuccess;
+        auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+        A(dalloc(&h->ov_cell_outer, C)); A(dalloc(&h->ov_flag, N)); A(dalloc(&h->ov_pos, N + 1));
+        A(dalloc(&h->ov_bsum, N / (kBlock * 8) + 4)); A(dalloc(&h->ov_gidx, N));
+        A(dalloc(&h->ov_bidx, N)); A(dalloc(&h->ov_nb, 1)); A(dalloc(&h->ov_send, N));
+        A(dalloc(&h->ov_recv, N));
+        A(cudaStreamCreateWithFlags(&h->ov_stream, cudaStreamNonBlocking));
+        for (cudaEvent_t &ev : h->ov_ev) A(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        if (e != cudaSuccess)
+            return fail(h, e == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA,
+                        std::string("md_set_decomposition: ") + cudaGetErrorString(e));
+    }
+    // per cell: the stencil cells that lie in another domain (domain of cell c
+    // along a dimension of n cells cut into p domains: floor(c p / n))
+    std::vector<uint32_t> outer(C);
+    auto dom = [](int c, int n, int p) { return (int)((int64_t)c * p / n); };
+    for (int cz = 0; cz < nd[2]; ++cz)
+        for (int cy = 0; cy < nd[1]; ++cy)
+            for (int cx = 0; cx < nd[0]; ++cx) {
+                uint32_t m = 0;
+                const int c3[3] = {cx, cy, cz};
+                for (int s = 0; s < kStencil; ++s) {
+                    const int o3[3] = {s % 3 - 1, (s / 3) % 3 - 1, s / 9 - 1};
+                    bool across = false;
+                    for (int d = 0; d < 3; ++d) {
+                        const int nb = ((c3[d] + o3[d]) % nd[d] + nd[d]) % nd[d];
+                        across |= dom(nb, nd[d], p3[d]) != dom(c3[d], nd[d], p3[d]);
+                    }
+                    if (across) m |= 1u << s;
+                }
+                outer[((size_t)cz * nd[1] + cy) * nd[0] + cx] = m;
+            }
+    MD_CK(cudaMemcpyAsync(h->ov_cell_outer, outer.data(), C * sizeof(uint32_t),
+                          cudaMemcpyHostToDevice, h->stream));
+    h->ov_on = true;
+    if (h->list_valid) MD_CK(launch_overlap_index(h, false));
+    MD_CK(cudaStreamSynchronize(h->stream));  // the host table above goes out of scope
+    return MD_OK;
 }
 
 md_status md_get_cell_costs(md_system *h, float *cycles_dev, int64_t *predicted_dev,

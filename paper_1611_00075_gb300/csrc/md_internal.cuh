@@ -266,6 +266,18 @@ struct md_system {
     int64_t mlp_t = 0;                  // Adam step count
     bool partition_valid = false;
 
+    // inner/outer split of the force pass (md_set_decomposition)
+    bool ov_on = false;
+    int dd[3] = {1, 1, 1};               // virtual domains per dimension
+    uint32_t *ov_cell_outer = nullptr;   // per cell: stencil cells in another domain (27 bits)
+    int32_t *ov_flag = nullptr, *ov_pos = nullptr, *ov_bsum = nullptr;  // boundary flags, scan
+    int32_t *ov_gidx = nullptr;          // sorted slot -> buffer slot (-1: interior atom)
+    int32_t *ov_bidx = nullptr;          // buffer slot -> sorted slot
+    int32_t *ov_nb = nullptr;            // boundary atom count (device)
+    float4 *ov_send = nullptr, *ov_recv = nullptr;  // the exchange's buffers
+    cudaStream_t ov_stream = nullptr;    // the exchange's stream
+    cudaEvent_t ov_ev[2] = {nullptr, nullptr};
+
     mdg::DevStatus *ds = nullptr;       // device
     mdg::DevStatus *ds_host = nullptr;  // pinned mirror
     double *red_host = nullptr;         // pinned
@@ -322,6 +334,10 @@ cudaError_t launch_lj_persist(md_system *h, int mode, bool store_f, bool dynamic
 int persist_ctas_per_sm(bool f64);
 cudaError_t launch_sc_density(md_system *h);
 cudaError_t launch_sc_force(md_system *h, int mode, bool energy, bool store_f);
+// inner/outer split (k_overlap.cu): boundary index after a rebuild (5 kernels),
+// then per force pass assemble, exchange, inner and outer passes (4 kernels)
+cudaError_t launch_overlap_index(md_system *h, bool gated);
+cudaError_t launch_overlap_forces(md_system *h, int mode, bool energy, bool store_f);
 cudaError_t launch_eam_density(md_system *h);  // k_eam.cu
 cudaError_t launch_eam_force(md_system *h, int mode, bool energy, bool store_f);
 

@@ -121,6 +121,7 @@ def lib() -> C.CDLL:
         "md_cost_model": [vp, i32, vp], "md_stats": [vp, C.c_char_p, C.c_size_t],
         "md_set_timing": [vp, i32], "md_color_cells": [vp, vp, vp],
         "md_set_schedule": [vp, i32, i32],
+        "md_set_decomposition": [vp, i32, i32, i32],
         "md_get_cell_costs": [vp, vp, vp, vp],
         "md_create_batch": [C.POINTER(vp), C.POINTER(md_params), i32, vp, vp, vp, vp, vp],
         "md_energy_batch": [vp, vp, vp],
@@ -290,6 +291,10 @@ def md_set_variant(h, force_variant: int, scheduler: int):
 
 def md_set_schedule(h, rounds: int, tail_percent: int):
     _check(lib().md_set_schedule(h, int(rounds), int(tail_percent)), h, "md_set_schedule")
+
+
+def md_set_decomposition(h, px: int, py: int, pz: int):
+    _check(lib().md_set_decomposition(h, int(px), int(py), int(pz)), h, "md_set_decomposition")
 
 
 def md_cost_model(h, op: int) -> float:
