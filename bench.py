@@ -398,13 +398,17 @@ def run_gpu(args, rank, world, local):
                 # the Newton's-third-law variants (half lists) against the full list
                 variants = {}
                 for name, code in (("half_color", md.MD_FORCE_HALF_COLOR),
-                                   ("half_atomic", md.MD_FORCE_HALF_ATOMIC)):
+                                   ("half_atomic", md.MD_FORCE_HALF_ATOMIC),
+                                   ("cluster_pairs", md.MD_FORCE_CLUSTER)):
                     from_s0(code, md.MD_SCHED_GRID)
                     msx, stx = timed(mixed, args.compare_steps)
                     variants[name] = {
                         "atom_steps_per_s": n_of(mixed) * args.compare_steps / (msx * 1e-3),
                         "force_ms_per_launch": stx["ms"]["force"] / max(1, stx["count"]["force"]),
                         "rebuild_ms_per_step": stx["ms"]["rebuild"] / args.compare_steps}
+                    if code == md.MD_FORCE_CLUSTER:
+                        variants[name]["cluster_pairs"] = stx["cluster_pairs"]
+                        variants[name]["pair_slots_per_atom"] = 32.0 * stx["cluster_pairs"] / n_of(mixed)
                 variants["full"] = {"atom_steps_per_s": sched_info["grid"]["atom_steps_per_s"],
                                     "force_ms_per_launch": sched_info["grid"]["force_ms_per_launch"]}
                 sched_info["force_variants"] = variants

@@ -54,8 +54,15 @@ typedef enum {
 
 enum { MD_POT_LJ = 0, MD_POT_SC = 1, MD_POT_EAM = 2 };
 enum { MD_FP64 = 0, MD_MIXED = 1 };
-/* Newton's-third-law strategy (Sec. 1 race problem, Sec. 2.2 pair loop). */
-enum { MD_FORCE_FULL = 0, MD_FORCE_HALF_COLOR = 1, MD_FORCE_HALF_ATOMIC = 2 };
+/* Newton's-third-law strategy (Sec. 1 race problem, Sec. 2.2 pair loop), and
+ * the cluster-pair layout the paper compares its SIMD scheme with (Sec. 4.1):
+ * MD_FORCE_CLUSTER evaluates the full pair set from a list of (i-cluster of up
+ * to 8 atoms, j-cluster of up to 4 atoms) pairs whose bounding boxes come
+ * within r_list, one warp per i-cluster; the per-atom list is still built
+ * (for md_get_neighbors).  Mixed-precision one-species Lennard-Jones of one
+ * box under MD_SCHED_GRID, n < 2^25. */
+enum { MD_FORCE_FULL = 0, MD_FORCE_HALF_COLOR = 1, MD_FORCE_HALF_ATOMIC = 2,
+       MD_FORCE_CLUSTER = 3 };
 /* How force work is spread over the SMs.  The static schedulers cut the
  * cells into equal-cost ranges per persistent CTA and leave the last fifth
  * of the cost as a tail that CTAs claim tile by tile when their ranges are

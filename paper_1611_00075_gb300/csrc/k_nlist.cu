@@ -317,7 +317,7 @@ cudaError_t launch_build_list(md_system *h, bool write, bool gated) {
     cudaStream_t s = h->stream;
     int cur = h->cur;
     const bool prefilter = (h->p.precision == MD_MIXED);
-    const bool half = (h->p.force_variant != MD_FORCE_FULL);
+    const bool half = half_variant(h->p.force_variant);
     reset_max_count_kernel<<<1, 1, 0, s>>>(h->ds, gated);
 #define MDG_LIST(PF, WR, HF)                                                                    \
     build_list_kernel<PF, WR, HF><<<gs_blocks(n) * (kBlock / kListBlock), kListBlock, 0, s>>>(                                \

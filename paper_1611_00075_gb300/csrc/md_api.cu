@@ -56,7 +56,7 @@ md_status check_params(const md_params *p, int64_t n, const double *box, std::st
     if (p->potential != MD_POT_LJ && p->potential != MD_POT_SC && p->potential != MD_POT_EAM)
         return bad("unknown potential");
     if (p->precision != MD_FP64 && p->precision != MD_MIXED) return bad("unknown precision");
-    if (p->force_variant < MD_FORCE_FULL || p->force_variant > MD_FORCE_HALF_ATOMIC)
+    if (p->force_variant < MD_FORCE_FULL || p->force_variant > MD_FORCE_CLUSTER)
         return bad("unknown force_variant");
     if (p->scheduler < MD_SCHED_GRID || p->scheduler > MD_SCHED_DYNAMIC)
         return bad("unknown scheduler");
@@ -93,6 +93,8 @@ void free_all(md_system *h) {
     F(h->scan_bsum); F(h->tmp_abs); F(h->tmp_v); F(h->nlist); F(h->ncount);
     F(h->rho); F(h->dF32); F(h->dF64); F(h->xqf); F(h->partials); F(h->red_out); F(h->ds);
     F(h->exp_tmp); F(h->type_orig);
+    F(h->cl_icnt); F(h->cl_jcnt); F(h->cl_ioff); F(h->cl_joff); F(h->cl_bsum); F(h->cl_icl);
+    F(h->cl_icell); F(h->cl_jbox); F(h->cl_ntot); F(h->cl_list); F(h->cl_row);
     F(h->ov_cell_outer); F(h->ov_flag); F(h->ov_pos); F(h->ov_bsum); F(h->ov_gidx);
     F(h->ov_bidx); F(h->ov_nb); F(h->ov_send); F(h->ov_recv);
     if (h->ov_stream) cudaStreamDestroy(h->ov_stream);
@@ -110,13 +112,41 @@ void free_all(md_system *h) {
 
 void drop_graphs(md_system *h);
 
+// Cluster tables and a cluster list of cl_cap entries per i-cluster, sized
+// from the largest cell occupancy seen (a quarter of headroom).
+cudaError_t alloc_cluster(md_system *h, int max_cell) {
+    const size_t C = (size_t)h->g.ncells;
+    const int64_t rows = cluster_rows(h->n, h->g.ncells);
+    const int64_t jrows = h->n / 4 + h->g.ncells + 1;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    if (!h->cl_icnt) {
+        A(dalloc(&h->cl_icnt, C)); A(dalloc(&h->cl_jcnt, C)); A(dalloc(&h->cl_ioff, C + 1));
+        A(dalloc(&h->cl_joff, C + 1)); A(dalloc(&h->cl_bsum, C / (kBlock * 8) + 4));
+        A(dalloc(&h->cl_icl, (size_t)rows)); A(dalloc(&h->cl_icell, (size_t)rows));
+        A(dalloc(&h->cl_jbox, 2 * (size_t)jrows)); A(dalloc(&h->cl_ntot, 2));
+        A(dalloc(&h->cl_row, (size_t)rows));
+    }
+    const int cap = cluster_cap(max_cell + max_cell / 4 + 4);
+    if (e == cudaSuccess && (cap > h->cl_cap || !h->cl_list)) {
+        if (h->cl_list) cudaFree(h->cl_list);
+        h->cl_list = nullptr;
+        h->cl_cap = cap;
+        A(dalloc(&h->cl_list, (size_t)rows * cap));
+    }
+    return e;
+}
+
 cudaError_t alloc_list(md_system *h, int cap) {
     drop_graphs(h);  // captured steps hold the old list pointer and capacity
     if (h->nlist) cudaFree(h->nlist);
     h->nlist = nullptr;
     h->cap = cap;
     h->nlist_entries = (size_t)((h->n + 31) / 32) * 32 * (size_t)cap;
-    return dalloc(&h->nlist, h->nlist_entries);
+    cudaError_t e = dalloc(&h->nlist, h->nlist_entries);
+    if (e == cudaSuccess && h->p.force_variant == MD_FORCE_CLUSTER)
+        e = alloc_cluster(h, h->ds_host ? h->ds_host->max_cell : 32);
+    return e;
 }
 
 int cap_for(int max_count) {
@@ -244,6 +274,10 @@ md_status enqueue_rebuild(md_system *h, bool gated) {
         MD_CK(launch_overlap_index(h, gated));
         h->launches += 5;
     }
+    if (h->p.force_variant == MD_FORCE_CLUSTER) {
+        MD_CK(launch_cluster_build(h, gated));
+        h->launches += 9;
+    }
     md_status st = enqueue_sched_prep(h, gated);
     if (st != MD_OK) return st;
     MD_CK(launch_finish_rebuild(h, gated));
@@ -278,6 +312,16 @@ md_status rebuild_now(md_system *h, bool size_from_count) {
         MD_CK(alloc_list(h, cap_for(h->ds_host->max_count)));
     }
     if (h->ov_on) MD_CK(launch_overlap_index(h, false));
+    if (h->p.force_variant == MD_FORCE_CLUSTER) {
+        md_status st = read_status(h);  // the binning's largest cell sizes the cluster list
+        if (st != MD_OK) return st;
+        MD_CK(alloc_cluster(h, h->ds_host->max_cell));
+        MD_CK(launch_cluster_build(h, false));
+        st = read_status(h);
+        if (st != MD_OK) return st;
+        if (h->ds_host->status != 0)
+            return fail(h, (md_status)h->ds_host->status, "device error during cluster build");
+    }
     md_status st = enqueue_sched_prep(h, false);
     if (st != MD_OK) return st;
     MD_CK(launch_finish_rebuild(h, false));
@@ -298,6 +342,9 @@ md_status enqueue_forces(md_system *h, int mode, bool energy, bool store_f) {
     } else if (h->ov_on) {
         MD_CK(launch_overlap_forces(h, mode, energy, store_f));
         h->launches += 4;
+    } else if (h->p.force_variant == MD_FORCE_CLUSTER) {
+        MD_CK(launch_cluster_forces(h, mode, energy, store_f));
+        h->launches += 1;
     } else if (h->p.force_variant != MD_FORCE_FULL) {
         int nl = 0;
         MD_CK(launch_lj_half(h, mode, energy, &nl));
@@ -611,6 +658,11 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
             return fail(nullptr, MD_ERR_INVALID,
                         W + ": multi-element systems run full lists under MD_SCHED_GRID");
     }
+    if (p->force_variant == MD_FORCE_CLUSTER &&
+        (R != 1 || p->scheduler != MD_SCHED_GRID || ltypes || n >= ((int64_t)1 << 25)))
+        return fail(nullptr, MD_ERR_INVALID,
+                    W + ": the cluster-pair list runs one one-species box under MD_SCHED_GRID, "
+                        "n < 2^25");
     if (p->force_variant != MD_FORCE_FULL && p->potential != MD_POT_LJ)
         return fail(nullptr, MD_ERR_INVALID, W + ": half lists are built for Lennard-Jones only");
     if (p->force_variant != MD_FORCE_FULL && p->precision != MD_MIXED)
@@ -907,6 +959,7 @@ md_status md_step(md_system *h, int64_t nsteps) {
         MD_CK(alloc_list(h, cap_for(h->ds_host->max_count)));
         MD_CK(launch_build_list(h, true, false));
         if (h->ov_on) MD_CK(launch_overlap_index(h, false));
+        if (h->p.force_variant == MD_FORCE_CLUSTER) MD_CK(launch_cluster_build(h, false));
         st = enqueue_sched_prep(h, false);
         if (st != MD_OK) return st;
         MD_CK(launch_finish_rebuild(h, false));
@@ -980,7 +1033,7 @@ md_status md_get_neighbors(md_system *h, int32_t half, int64_t *offsets_dev, int
                            int64_t cap, int64_t *total_host) {
     if (!h) return fail(nullptr, MD_ERR_INVALID, "md_get_neighbors: null handle");
     if (!offsets_dev || cap < 0) return fail(h, MD_ERR_INVALID, "md_get_neighbors: bad argument");
-    if (!half && h->p.force_variant != MD_FORCE_FULL)
+    if (!half && half_variant(h->p.force_variant))
         return fail(h, MD_ERR_INVALID, "md_get_neighbors: the list is a half list");
     if (!h->list_valid) {
         md_status st = rebuild_now(h, false);
@@ -1039,7 +1092,7 @@ md_status md_get_atom_energy(md_system *h, double *e_dev) {
 
 md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler) {
     if (!h) return fail(nullptr, MD_ERR_INVALID, "md_set_variant: null handle");
-    if (force_variant < MD_FORCE_FULL || force_variant > MD_FORCE_HALF_ATOMIC ||
+    if (force_variant < MD_FORCE_FULL || force_variant > MD_FORCE_CLUSTER ||
         scheduler < MD_SCHED_GRID || scheduler > MD_SCHED_DYNAMIC)
         return fail(h, MD_ERR_INVALID, "md_set_variant: unknown variant or scheduler");
     if ((h->p.potential == MD_POT_EAM || h->fc.ntypes > 0 || h->ov_on) &&
@@ -1055,7 +1108,14 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
                      (scheduler != MD_SCHED_GRID && scheduler != MD_SCHED_DYNAMIC)))
         return fail(h, MD_ERR_INVALID,
                     "md_set_variant: batches run full lists under MD_SCHED_GRID or MD_SCHED_DYNAMIC");
-    const bool relist = (force_variant != MD_FORCE_FULL) != (h->p.force_variant != MD_FORCE_FULL);
+    if (force_variant == MD_FORCE_CLUSTER &&
+        (scheduler != MD_SCHED_GRID || h->n >= ((int64_t)1 << 25)))
+        return fail(h, MD_ERR_INVALID,
+                    "md_set_variant: the cluster-pair list runs under MD_SCHED_GRID, n < 2^25");
+    // a change between half and full pair sets relists; entering the cluster
+    // layout builds its tables and list
+    const bool relist = half_variant(force_variant) != half_variant(h->p.force_variant) ||
+                        (force_variant == MD_FORCE_CLUSTER && h->p.force_variant != MD_FORCE_CLUSTER);
     drop_graphs(h);  // the captured steps launch the old variant's kernels
     h->p.force_variant = force_variant;
     h->p.scheduler = scheduler;
@@ -1278,14 +1338,15 @@ md_status md_stats(md_system *h, char *buf_host, size_t cap) {
                   "{\"n\": %lld, \"ncell\": [%d, %d, %d], \"cap\": %d, \"builds\": %d, "
                   "\"steps\": %lld, \"max_count\": %d, \"max_cell\": %d, \"status\": %d, "
                   "\"precision\": %d, \"force_variant\": %d, \"scheduler\": %d, "
-                  "\"list_entries\": %llu, \"pairs_cut\": %llu, \"launches\": %lld, "
+                  "\"list_entries\": %llu, \"pairs_cut\": %llu, \"cluster_pairs\": %llu, "
+                  "\"launches\": %lld, "
                   "\"ms\": {\"rebuild\": %.6f, \"force\": %.6f, \"integrate\": %.6f, "
                   "\"other\": %.6f}, \"count\": {\"rebuild\": %lld, \"force\": %lld, "
                   "\"integrate\": %lld, \"other\": %lld}}",
                   (long long)h->n, h->g.nx, h->g.ny, h->g.nz, h->cap, d.builds,
                   (long long)h->steps_total, d.max_count, d.max_cell, d.status, h->p.precision,
                   h->p.force_variant, h->p.scheduler, d.list_entries, d.pairs_cut,
-                  h->launches + d.cond_runs * h->body_launches,
+                  d.cluster_pairs, h->launches + d.cond_runs * h->body_launches,
                   h->ms_kind[0], h->ms_kind[1], h->ms_kind[2], h->ms_kind[3], h->n_kind[0],
                   h->n_kind[1], h->n_kind[2], h->n_kind[3]);
     return MD_OK;

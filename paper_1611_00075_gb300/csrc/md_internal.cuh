@@ -59,6 +59,10 @@ __host__ __device__ __forceinline__ int color_cell_1d(int k, int t, int n) {
     return k < 3 ? k + 3 * t : (n / 3) * 3 + (k - 3);
 }
 
+// half lists (Newton's third law: each pair once) as opposed to the full pair
+// set of the per-atom or the cluster-pair list
+inline bool half_variant(int fv) { return fv == MD_FORCE_HALF_COLOR || fv == MD_FORCE_HALF_ATOMIC; }
+
 // Device status word.  Every kernel of a step returns at entry when `status`
 // is non-zero, so an error stops the rest of the enqueued work and the host
 // finds the state exactly where it stopped.
@@ -78,6 +82,7 @@ struct DevStatus {
     int tile_counter;                 // dynamic scheduler: next unclaimed tile
     unsigned int done_ctas;           // dynamic scheduler: CTAs finished this launch
     long long cond_runs;              // rebuild chains run by a graph's IF node
+    unsigned long long cluster_pairs; // (i-cluster, j-cluster) entries of the last cluster list
 };
 
 // What the persistent force kernel needs besides ForceArgs.
@@ -266,6 +271,18 @@ struct md_system {
     int64_t mlp_t = 0;                  // Adam step count
     bool partition_valid = false;
 
+    // cluster-pair list (MD_FORCE_CLUSTER)
+    int32_t *cl_icnt = nullptr, *cl_jcnt = nullptr;  // clusters per cell
+    int32_t *cl_ioff = nullptr, *cl_joff = nullptr;  // their scans (ncells + 1)
+    int32_t *cl_bsum = nullptr;
+    uint32_t *cl_icl = nullptr;   // i-cluster: first atom | (size - 1) << 27
+    int32_t *cl_icell = nullptr;  // i-cluster: cell
+    float4 *cl_jbox = nullptr;    // j-cluster: box lo (w: first atom), hi (w: size)
+    int32_t *cl_ntot = nullptr;   // [0] i-clusters, [1] j-clusters (device)
+    uint32_t *cl_list = nullptr;  // rows of cl_cap entries per i-cluster
+    int32_t *cl_row = nullptr;    // row lengths
+    int cl_cap = 0;
+
     // inner/outer split of the force pass (md_set_decomposition)
     bool ov_on = false;
     int dd[3] = {1, 1, 1};               // virtual domains per dimension
@@ -334,6 +351,12 @@ cudaError_t launch_lj_persist(md_system *h, int mode, bool store_f, bool dynamic
 int persist_ctas_per_sm(bool f64);
 cudaError_t launch_sc_density(md_system *h);
 cudaError_t launch_sc_force(md_system *h, int mode, bool energy, bool store_f);
+// cluster-pair list (k_cluster.cu): tables and list after a rebuild (10 kernels),
+// one force kernel
+int cluster_cap(int max_cell);
+int64_t cluster_rows(int64_t n, int ncells);
+cudaError_t launch_cluster_build(md_system *h, bool gated);
+cudaError_t launch_cluster_forces(md_system *h, int mode, bool energy, bool store_f);
 // inner/outer split (k_overlap.cu): boundary index after a rebuild (5 kernels),
 // then per force pass assemble, exchange, inner and outer passes (4 kernels)
 cudaError_t launch_overlap_index(md_system *h, bool gated);
