@@ -665,25 +665,55 @@ def oracle_params(orc, p: dict):
                            dt=p["dt"], mass=p["mass"])
 
 
-def cpu_baseline_leg(args, gpu=None, steps=None):
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                name = line.split(":", 1)[1].strip()
+                if name and not name.isdigit():
+                    return name
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_baseline_leg(args, gpu=None, steps=None, repeats=5):
     """Times the CPU oracle (as it stands) on a bounded sample on all host
-    cores, and measures the GPU snapshot's force error against it."""
+    cores -- `repeats` runs of `steps` steps after a list build, reported as
+    the mean with the standard deviation over the runs (the paper's timing
+    protocol, Sec. 3.3) -- and measures the GPU snapshot's force error
+    against it."""
     import oracle as orc
     orc.build()
     cores = os.cpu_count() or 1
     orc.set_threads(cores)
     s, what = oracle_sample_system(args, orc)
     prm = oracle_params(orc, s.params)
-    k = steps if steps is not None else 5
-    t0 = time.perf_counter()
-    orc.forces_once(prm, s.pos, s.box)
-    t1 = time.perf_counter()
-    orc.md_run(prm, s.pos, s.vel, s.box, k, want_energies=False)
-    t2 = time.perf_counter()
-    per_step = max(1e-9, ((t2 - t1) - (t1 - t0)) / k)  # first list build excluded
-    out = {"value": s.n / per_step, "unit": "atom-steps/s", "cores": cores, "kind": "oracle",
-           "sample": "%s, %d atoms, %d velocity-Verlet steps after the first list build "
-                     "(fp64 C oracle, OpenMP over atoms)" % (what, s.n, k)}
+    k = steps if steps is not None else 10
+    rates = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        orc.forces_once(prm, s.pos, s.box)
+        t1 = time.perf_counter()
+        orc.md_run(prm, s.pos, s.vel, s.box, k, want_energies=False)
+        t2 = time.perf_counter()
+        per_step = max(1e-9, ((t2 - t1) - (t1 - t0)) / k)  # the first list build excluded
+        rates.append(s.n / per_step)
+    out = {"value": statistics.mean(rates), "std": statistics.stdev(rates) if repeats > 1 else 0.0,
+           "repeats": repeats, "unit": "atom-steps/s", "cores": cores, "cpu": cpu_model(),
+           "kind": "oracle",
+           "sample": "%s, %d atoms, %d runs of %d velocity-Verlet steps after a list build "
+                     "(fp64 C oracle, OpenMP over atoms); mean and standard deviation over "
+                     "the runs" % (what, s.n, repeats, k)}
     if gpu is not None:
         rng_idx = (inputs.splitmix64(inputs.SEED_BASE + 99, 4096) % gpu["n_check"]).astype(np.int64)
         idx = np.unique(rng_idx)
@@ -722,12 +752,13 @@ def run_reference(args, rank, world):
     value = s.n * args.steps / sec
     _, desc = make_workload_desc(args)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "atom-steps/s",
+            "cpu": cpu_model(),
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": sec * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc},
             "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": cores,
-                             "kind": "oracle",
+                             "cpu": cpu_model(), "kind": "oracle",
                              "sample": "%s, %d atoms, %d velocity-Verlet steps after the first "
                                        "list build (fp64 C oracle, OpenMP over atoms)"
                                        % (what, s.n, args.steps)},
