@@ -45,8 +45,9 @@ FORCE_SOURCES = ("paper_1611_00075_gb300/csrc/k_lj.cu", "paper_1611_00075_gb300/
                  "paper_1611_00075_gb300/csrc/md_internal.cuh")
 PROFILED_TRAFFIC = {
     # kernel: (sources sha1[:16], DRAM bytes per atom, capture)
-    "lj_mixed_persist": ("f46a337b68db4f07", 449.0,
-                         "ncu --set full, porous 80^3 cells (1,223,941 atoms), one launch"),
+    "lj_mixed_persist": ("bfa90097e980e658", 482.6,
+                         "ncu --set full, porous 80^3 cells (1,223,941 atoms) equilibrated as the "
+                         "bench's input, one FM_FUSED_FULL launch of the timed range"),
 }
 
 
@@ -81,6 +82,8 @@ def parse_args(argv):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nc", type=int, default=0,
                     help="fcc cells per side (0 = the workload's own size; smaller for profiling)")
+    ap.add_argument("--no-equilibrate", dest="equilibrate", action="store_false",
+                    help="porous: time from the generated state instead of the equilibrated one")
     return ap.parse_args(argv)
 
 
@@ -324,6 +327,19 @@ def run_gpu(args, rank, world, local):
                               box=s.box, params=s.params)
             sched_info["melt"] = {"seconds": time.perf_counter() - t0, "steps": sum(
                 k for _, k in inputs.MELT_SCHEDULE), "schedule": inputs.MELT_SCHEDULE}
+        elif args.workload == "porous" and args.equilibrate:
+            # the porous solid relaxes its surfaces and heats at first: every
+            # leg below starts from it at its steady rebuild rate
+            t0 = time.perf_counter()
+            gpu_melt(md, mixed, kw["mass"], dev, inputs.POROUS_EQUIL_SCHEDULE)
+            p_m, v_m, _ = mixed.state()
+            s = inputs.System(name=s.name + "_equilibrated", pos=p_m.cpu().numpy(),
+                              vel=v_m.cpu().numpy(), box=s.box, params=s.params)
+            sched_info["equilibration"] = {
+                "seconds": time.perf_counter() - t0,
+                "steps": sum(k for _, k in inputs.POROUS_EQUIL_SCHEDULE),
+                "schedule": inputs.POROUS_EQUIL_SCHEDULE,
+                "rescale_every": inputs.MELT_RESCALE_EVERY}
         md.md_step(mixed.h, args.warmup)
         if ensemble:
             s0 = mixed.state()[:2]
@@ -399,7 +415,8 @@ def run_gpu(args, rank, world, local):
                 variants = {}
                 for name, code in (("half_color", md.MD_FORCE_HALF_COLOR),
                                    ("half_atomic", md.MD_FORCE_HALF_ATOMIC),
-                                   ("cluster_pairs", md.MD_FORCE_CLUSTER)):
+                                   ("cluster_pairs", md.MD_FORCE_CLUSTER),
+                                   ("paired", md.MD_FORCE_PAIRED)):
                     from_s0(code, md.MD_SCHED_GRID)
                     msx, stx = timed(mixed, args.compare_steps)
                     variants[name] = {
@@ -409,6 +426,9 @@ def run_gpu(args, rank, world, local):
                     if code == md.MD_FORCE_CLUSTER:
                         variants[name]["cluster_pairs"] = stx["cluster_pairs"]
                         variants[name]["pair_slots_per_atom"] = 32.0 * stx["cluster_pairs"] / n_of(mixed)
+                    if code == md.MD_FORCE_PAIRED:
+                        variants[name]["slot_entries_per_atom"] = stx["slot_entries"] / n_of(mixed)
+                        variants[name]["list_entries_per_atom"] = stx["list_entries"] / n_of(mixed)
                 variants["full"] = {"atom_steps_per_s": sched_info["grid"]["atom_steps_per_s"],
                                     "force_ms_per_launch": sched_info["grid"]["force_ms_per_launch"]}
                 sched_info["force_variants"] = variants
@@ -574,23 +594,35 @@ def run_gpu(args, rank, world, local):
                 sched_info=sched_info)
 
 
-def gpu_melt(md, sysobj, mass, device):
-    """Melts the system in place on the GPU (untimed input preparation):
-    inputs.MELT_SCHEDULE with the velocities rescaled to each stage's
-    temperature every inputs.MELT_RESCALE_EVERY steps and once at the end."""
+def start_state(info):
+    """How the timed state was prepared (untimed), for the JSON line."""
+    for key, what in (("melt", "melted"), ("equilibration", "equilibrated")):
+        if key in info:
+            stages = ", ".join("%d steps at T*=%g" % (k, T) for T, k in info[key]["schedule"])
+            return ("%s on the GPU before timing (untimed): %s, velocities rescaled every %d steps"
+                    % (what, stages, inputs.MELT_RESCALE_EVERY))
+    return "as generated"
+
+
+def gpu_melt(md, sysobj, mass, device, schedule=None):
+    """Melts (or equilibrates) the system in place on the GPU, untimed input
+    preparation: the schedule (inputs.MELT_SCHEDULE by default) with the
+    velocities rescaled to each stage's temperature every
+    inputs.MELT_RESCALE_EVERY steps and once at the end."""
     import torch
     every = inputs.MELT_RESCALE_EVERY
+    schedule = schedule or inputs.MELT_SCHEDULE
 
     def rescale(T):
         v = sysobj.state()[1].cpu().numpy()
         v = torch.from_numpy(inputs.rescale_velocities(v, T, mass)).to(device)
         md.md_set_state(sysobj.h, None, v)
 
-    for T, nsteps in inputs.MELT_SCHEDULE:
+    for T, nsteps in schedule:
         for _ in range(nsteps // every):
             rescale(T)
             md.md_step(sysobj.h, every)
-    rescale(inputs.MELT_SCHEDULE[-1][0])
+    rescale(schedule[-1][0])
     torch.cuda.synchronize()
 
 
@@ -790,7 +822,8 @@ def main():
                    "force_variant": "full list", "scheduler": args.scheduler,
                    "l2": "inputs larger than L2 (%.1f GB resident state + list)"
                          % ((g["n"] * 300 + g["st_e"]["list_entries"] * 4) / 1e9),
-                   "list_builds_in_timed_steps": g["builds_timed"]},
+                   "list_builds_in_timed_steps": g["builds_timed"],
+                   "start_state": start_state(g["sched_info"])},
         "fp64_baseline": g["fp64"],
         "speedup_vs_fp64": (g["value"] / g["fp64"]["value"]) if g["fp64"] else None,
         "roofline": g["roof"],

@@ -60,9 +60,17 @@ enum { MD_FP64 = 0, MD_MIXED = 1 };
  * to 8 atoms, j-cluster of up to 4 atoms) pairs whose bounding boxes come
  * within r_list, one warp per i-cluster; the per-atom list is still built
  * (for md_get_neighbors).  Mixed-precision one-species Lennard-Jones of one
- * box under MD_SCHED_GRID, n < 2^25. */
+ * box under MD_SCHED_GRID, n < 2^25.
+ * MD_FORCE_PAIRED clusters the home side only, by two (Sec. 4.1's point that
+ * grouping atoms saves neighbour loads): each thread owns two consecutive
+ * atoms of one cell and walks the union of their lists, so that one gathered
+ * neighbour position serves two pair evaluations.  The full pair set, the
+ * same forces as MD_FORCE_FULL up to float32 rounding; the per-atom list is
+ * still built (for md_get_neighbors).  Mixed-precision one-species
+ * Lennard-Jones of one box under MD_SCHED_GRID.  Both are measured
+ * alternatives: on GB300 the per-atom full list is faster. */
 enum { MD_FORCE_FULL = 0, MD_FORCE_HALF_COLOR = 1, MD_FORCE_HALF_ATOMIC = 2,
-       MD_FORCE_CLUSTER = 3 };
+       MD_FORCE_CLUSTER = 3, MD_FORCE_PAIRED = 4 };
 /* How force work is spread over the SMs.  The static schedulers cut the
  * cells into equal-cost ranges per persistent CTA and leave the last fifth
  * of the cost as a tail that CTAs claim tile by tile when their ranges are

@@ -1,0 +1,352 @@
+// k_pair.cu -- two home atoms per thread (MD_FORCE_PAIRED).
+//
+// Sec. 4.1 contrasts the paper's per-atom SIMD pair loop with clustering:
+// grouping atoms lets one neighbour load serve several pair evaluations,
+// which avoids the gather cost that dominates light potentials.  Full 8 x 4
+// cluster pairs waste most of their slots at r_c = 2.5 sigma (their bounding
+// boxes are as large as the cut-off sphere); this layout clusters only the
+// home side, and only by two: the atoms of each cell, in their sorted order,
+// are taken two at a time into slots (a cell of odd occupancy ends with a
+// one-atom slot).  A slot's list is the union of its two atoms' lists, so one
+// gather of a neighbour position feeds two pair evaluations: the union of two
+// r_list spheres about one atom spacing apart holds about 1.3 times the
+// entries of one, for twice the pairs.
+//
+// Slot s holds sorted atoms i0 = slot_atom[s] & 0x7fffffff and, unless bit 31
+// is set, i1 = i0 + 1 (the same cell).  Its list uses the per-atom layout
+// (groups of 32 slots, quads of entries; entry = (stencil << 27) | j, j never
+// i0 or i1) and is padded to whole quads with entries that point at a far
+// away dummy position stored after the last atom (index n).  The list is a
+// superset of both atoms' lists: it accepts j when the float32 distance to
+// either atom is below r_list^2 (1 + 2^-14), which covers every pair within
+// r_list -- and so, by the half-skin rule, every pair within r_c until the
+// next rebuild.  The force pass evaluates the slot's own pair once
+// (f_i0 += F, f_i1 -= F), then both atoms against each list entry, with the
+// mixed-precision arithmetic of the per-atom kernel (float32 pair terms,
+// float32 chunk sums added in float64) and its velocity-Verlet epilogue.
+#include "k_common.cuh"
+#include "k_scan.cuh"
+
+namespace mdg {
+
+namespace {
+
+constexpr uint32_t kSingle = 0x80000000u;   // slot_atom: a one-atom slot
+constexpr uint32_t kHomeStencil = 13;       // stencil cell (0, 0, 0)
+constexpr int kPairBlock = 128;
+
+__device__ __forceinline__ bool chain_off(const DevStatus *ds, bool gated) {
+    return ds->status != 0 || (gated && ds->rebuild == 0);
+}
+
+__device__ __forceinline__ int row_off(int k) { return k + (k >> 2) * 124; }
+
+// slots per cell: ceil(atoms / 2)
+__global__ void slot_count_kernel(int ncells, const int32_t *__restrict__ start,
+                                  int32_t *__restrict__ cnt, const DevStatus *ds, bool gated) {
+    if (chain_off(ds, gated)) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x)
+        cnt[c] = (start[c + 1] - start[c] + 1) >> 1;
+}
+
+// the first atom of every slot, flagged when the slot holds one atom
+__global__ void slot_fill_kernel(int n, const int32_t *__restrict__ cell,
+                                 const int32_t *__restrict__ start,
+                                 const int32_t *__restrict__ slot_start,
+                                 uint32_t *__restrict__ slot_atom, const DevStatus *ds,
+                                 bool gated) {
+    if (chain_off(ds, gated)) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int c = cell[i];
+        const int k = i - start[c];
+        if (k & 1) continue;
+        const uint32_t single = (i + 1 >= start[c + 1]) ? kSingle : 0u;
+        slot_atom[slot_start[c] + (k >> 1)] = (uint32_t)i | single;
+    }
+}
+
+// The union list of each slot: the 27 cells around the slot's cell, in
+// stencil order, each candidate tested against both atoms in float32.
+template <bool WRITE>
+__global__ void __launch_bounds__(kPairBlock)
+pair_list_kernel(int n, Grid g, float hi, const float4 *__restrict__ xq,
+                 const int32_t *__restrict__ cell, const int32_t *__restrict__ start,
+                 const int32_t *__restrict__ slot_start, const uint32_t *__restrict__ slot_atom,
+                 uint32_t *__restrict__ list, int32_t *__restrict__ count, int cap, DevStatus *ds,
+                 bool gated) {
+    if (chain_off(ds, gated)) return;
+    const int nslots = slot_start[g.ncells];
+    unsigned long long tot = 0;
+    int overflow = 0, maxc = 0;
+    const float wx = (float)g.w[0], wy = (float)g.w[1], wz = (float)g.w[2];
+    const uint32_t pad = (kHomeStencil << kIndexBits) | (uint32_t)n;
+    // grid-stride over whole warps, so every lane reaches the reductions below
+    const int stride = gridDim.x * blockDim.x;
+    const int send = ((nslots + 31) & ~31);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < send; s += stride) {
+        if (s < nslots) {
+            const uint32_t sa = slot_atom[s];
+            const int i0 = (int)(sa & ~kSingle);
+            const int i1 = (sa & kSingle) ? i0 : i0 + 1;
+            const float4 q0 = xq[i0], q1 = xq[i1];
+            const int c = cell[i0];
+            const int cx = c % g.nx, cy = (c / g.nx) % g.ny, cz = c / (g.nx * g.ny);
+            uint32_t *row = list + list_group(s, cap) + ((s & 31) << 2);
+            int cnt = 0;
+            for (int dz = -1; dz <= 1; ++dz) {
+                const int zz = (cz + dz + g.nz) % g.nz;
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int yy = (cy + dy + g.ny) % g.ny;
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int xx = (cx + dx + g.nx) % g.nx;
+                        const int cn = (zz * g.ny + yy) * g.nx + xx;
+                        const uint32_t sbits =
+                            (uint32_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)) << kIndexBits;
+                        // home positions moved against the cell shift
+                        const float ax = q0.x - (float)dx * wx, ay = q0.y - (float)dy * wy,
+                                    az = q0.z - (float)dz * wz;
+                        const float bx = q1.x - (float)dx * wx, by = q1.y - (float)dy * wy,
+                                    bz = q1.z - (float)dz * wz;
+                        const int b = start[cn], e = start[cn + 1];
+#pragma unroll 4
+                        for (int j = b; j < e; ++j) {
+                            const float4 qj = xq[j];
+                            const float ex = qj.x - ax, ey = qj.y - ay, ez = qj.z - az;
+                            const float fx = qj.x - bx, fy = qj.y - by, fz = qj.z - bz;
+                            const float r0 = ex * ex + ey * ey + ez * ez;
+                            const float r1 = fx * fx + fy * fy + fz * fz;
+                            const bool acc = (fminf(r0, r1) < hi) & (j != i0) & (j != i1);
+                            if (WRITE && acc && cnt < cap) row[row_off(cnt)] = sbits | (uint32_t)j;
+                            cnt += acc ? 1 : 0;
+                        }
+                    }
+                }
+            }
+            if (WRITE && cnt <= cap)
+                for (int k = cnt; k & 3; ++k) row[row_off(k)] = pad;
+            if (WRITE) count[s] = cnt;
+            maxc = max(maxc, cnt);
+            tot += (unsigned long long)cnt;
+            overflow |= (cnt > cap);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+    maxc = (int)__reduce_max_sync(0xffffffffu, (unsigned)maxc);
+    if ((threadIdx.x & 31) == 0) {
+        if (tot) atomicAdd(&ds->pair_entries, tot);
+        if (maxc) atomicMax(&ds->pair_max, maxc);
+    }
+    if (WRITE && overflow) atomicCAS(&ds->status, 0, (int)MD_ERR_LIST_OVERFLOW);
+}
+
+__global__ void pair_reset_kernel(DevStatus *ds, bool gated) {
+    if (chain_off(ds, gated)) return;
+    ds->pair_max = 0;
+    ds->pair_entries = 0;
+}
+
+// the dummy neighbour of the padding entries, past the last atom of both
+// position buffers
+__global__ void pair_dummy_kernel(float4 *xq0, float4 *xq1, int n) {
+    const float4 far = make_float4(3.0e18f, 3.0e18f, 3.0e18f, 0.f);
+    xq0[n] = far;
+    xq1[n] = far;
+}
+
+struct PairArgs {
+    const int32_t *slot_start;   // ncells + 1 (slot_start[ncells] = slots)
+    const uint32_t *slot_atom;
+    const uint32_t *list;
+    const int32_t *count;
+    int cap, ncells;
+};
+
+// Lennard-Jones pair term in float32 for the pair vector e = x_j - x_i:
+// f_i -= fs * e; with ENERGY the shifted pair energy is added to `en`.
+template <bool ENERGY>
+__device__ __forceinline__ void lj_term(const ForceConsts &fc, float ex, float ey, float ez,
+                                        float r2, float &fx, float &fy, float &fz, float &en,
+                                        unsigned &np) {
+    const float r2i = __fdividef(1.0f, r2);
+    float s6 = fc.sig2f * r2i;
+    s6 = s6 * s6 * s6;
+    const float fs = fc.eps48f * r2i * s6 * (s6 - 0.5f);
+    fx -= fs * ex;
+    fy -= fs * ey;
+    fz -= fs * ez;
+    if (ENERGY) {
+        en += fc.eps4f * s6 * (s6 - 1.0f) - fc.shiftf;
+        ++np;
+    }
+}
+
+// Stores, energies and the velocity-Verlet epilogue of one atom of a slot.
+template <int MODE, bool ENERGY>
+__device__ __forceinline__ void pair_atom_out(const ForceArgs &a, int i, double Fx, double Fy,
+                                              double Fz, double E, unsigned np, float qw,
+                                              int store_f) {
+    const size_t n = (size_t)a.n;
+    if (MODE == FM_STORE || store_f) {
+        a.f[i] = Fx;
+        a.f[n + i] = Fy;
+        a.f[2 * n + i] = Fz;
+    }
+    if (ENERGY) {
+        a.e_atom[i] = 0.5 * E;
+        count_pairs(a.ds, np);
+    }
+    if (MODE != FM_STORE) vv_epilogue<MODE>(a, i, Fx, Fy, Fz, qw);
+}
+
+template <int MODE, bool ENERGY>
+__device__ __forceinline__ void lj_pair_slot(const ForceArgs &a, const PairArgs &p,
+                                             const ShiftTab *sh, int s, int store_f) {
+    const uint32_t sa = p.slot_atom[s];
+    const int i0 = (int)(sa & ~kSingle);
+    const bool two = !(sa & kSingle);
+    const float4 q0 = a.xq[i0];
+    // a one-atom slot puts its second atom at the dummy's distance
+    const float4 q1 = two ? a.xq[i0 + 1] : make_float4(3.0e18f, 3.0e18f, 3.0e18f, 0.f);
+    const float rc2 = a.fc.rc2f;
+    double F0x = 0.0, F0y = 0.0, F0z = 0.0, F1x = 0.0, F1y = 0.0, F1z = 0.0, E0 = 0.0, E1 = 0.0;
+    float f0x = 0.f, f0y = 0.f, f0z = 0.f, f1x = 0.f, f1y = 0.f, f1z = 0.f, e0 = 0.f, e1 = 0.f;
+    unsigned np0 = 0, np1 = 0;
+    {
+        // the slot's own pair, once: f_i0 -= fs e, f_i1 += fs e
+        const float ex = q1.x - q0.x, ey = q1.y - q0.y, ez = q1.z - q0.z;
+        const float r2 = ex * ex + ey * ey + ez * ez;
+        if (r2 < rc2) {
+            float gx = 0.f, gy = 0.f, gz = 0.f, en = 0.f;
+            unsigned k = 0;
+            lj_term<ENERGY>(a.fc, ex, ey, ez, r2, gx, gy, gz, en, k);
+            f0x = gx; f0y = gy; f0z = gz;
+            f1x = -gx; f1y = -gy; f1z = -gz;
+            if (ENERGY) {
+                e0 = e1 = en;
+                np0 = np1 = 1;
+            }
+        }
+    }
+    const int nq = (min(p.count[s], p.cap) + 3) >> 2;
+    const uint4 *lq = reinterpret_cast<const uint4 *>(p.list + list_group(s, p.cap)) + (s & 31);
+    // one gather and one stencil shift per entry, two pair evaluations
+    auto pair = [&](uint32_t ent) {
+        const float4 qj = __ldg(a.xq + (ent & kIndexMask));
+        const uint32_t st = ent >> kIndexBits;
+        const float tx = qj.x + sh->x[st], ty = qj.y + sh->y[st], tz = qj.z + sh->z[st];
+        const float ax = tx - q0.x, ay = ty - q0.y, az = tz - q0.z;
+        const float ra = ax * ax + ay * ay + az * az;
+        if (ra < rc2) lj_term<ENERGY>(a.fc, ax, ay, az, ra, f0x, f0y, f0z, e0, np0);
+        const float bx = tx - q1.x, by = ty - q1.y, bz = tz - q1.z;
+        const float rb = bx * bx + by * by + bz * bz;
+        if (rb < rc2) lj_term<ENERGY>(a.fc, bx, by, bz, rb, f1x, f1y, f1z, e1, np1);
+    };
+    uint4 nxt = nq > 0 ? __ldcs(lq) : make_uint4(0u, 0u, 0u, 0u);
+    for (int c0 = 0; c0 < nq; c0 += kChunkQ) {
+        const int c1 = min(c0 + kChunkQ, nq);
+        for (int q = c0; q < c1; ++q) {
+            const uint4 e4 = nxt;
+            if (q + 1 < nq) nxt = __ldcs(lq + (size_t)(q + 1) * 32);
+            pair(e4.x);
+            pair(e4.y);
+            pair(e4.z);
+            pair(e4.w);
+        }
+        F0x += (double)f0x; F0y += (double)f0y; F0z += (double)f0z;
+        F1x += (double)f1x; F1y += (double)f1y; F1z += (double)f1z;
+        f0x = f0y = f0z = f1x = f1y = f1z = 0.f;
+        if (ENERGY) {
+            E0 += (double)e0;
+            E1 += (double)e1;
+            e0 = e1 = 0.f;
+        }
+    }
+    // a slot without list entries still carries its own pair
+    F0x += (double)f0x; F0y += (double)f0y; F0z += (double)f0z;
+    F1x += (double)f1x; F1y += (double)f1y; F1z += (double)f1z;
+    if (ENERGY) {
+        E0 += (double)e0;
+        E1 += (double)e1;
+    }
+    pair_atom_out<MODE, ENERGY>(a, i0, F0x, F0y, F0z, E0, np0, q0.w, store_f);
+    if (two) pair_atom_out<MODE, ENERGY>(a, i0 + 1, F1x, F1y, F1z, E1, np1, q1.w, store_f);
+}
+
+// Measured on GB300 (porous LJ, 9.8 M atoms, one force launch): this scalar
+// form at 72 registers (7 CTAs per SM) 1.498 ms; the same with packed
+// float32 pair arithmetic (add/mul/fma.rn.f32x2, both atoms in one
+// instruction) 1.551 ms at 72 registers and 1.690 ms at 64; the per-atom
+// kernel 1.307 ms.  The slot lists hold 0.68 times the per-atom entries and
+// the kernel issues fewer instructions and L1 wavefronts, but with fewer
+// warps resident its gathers' latency is no longer hidden.
+template <int MODE, bool ENERGY>
+__global__ void __launch_bounds__(kPairBlock, 7) lj_pair_kernel(ForceArgs a, PairArgs p,
+                                                                int store_f) {
+    __shared__ ShiftTab sh;
+    load_shifts_f32(a.g, &sh);
+    __syncthreads();
+    if (a.ds->status != 0) return;
+    step_bookkeeping<MODE>(a);
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < p.slot_start[p.ncells]) lj_pair_slot<MODE, ENERGY>(a, p, &sh, s, store_f);
+}
+
+}  // namespace
+
+int64_t pair_slots_max(int64_t n, int ncells) { return (n + ncells) / 2 + 1; }
+
+cudaError_t launch_pair_dummy(md_system *h) {
+    pair_dummy_kernel<<<1, 1, 0, h->stream>>>(h->xq[0], h->xq[1], (int)h->n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_build(md_system *h, bool write, bool gated) {
+    const int n = (int)h->n, nc = h->g.ncells;
+    cudaStream_t s = h->stream;
+    slot_count_kernel<<<gs_blocks(nc), kBlock, 0, s>>>(nc, h->cell_start, h->ps_cnt, h->ds, gated);
+    cudaError_t e = launch_scan_i32(h->ps_cnt, h->ps_start, nc, h->ps_bsum, h->ds, gated, s);
+    if (e != cudaSuccess) return e;
+    slot_fill_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->cell, h->cell_start, h->ps_start,
+                                                     h->ps_atom, h->ds, gated);
+    pair_reset_kernel<<<1, 1, 0, s>>>(h->ds, gated);
+    const int64_t smax = pair_slots_max(h->n, nc);
+    const int blocks = (int)std::min<int64_t>((smax + kPairBlock - 1) / kPairBlock, 152 * 16);
+    if (write)
+        pair_list_kernel<true><<<blocks, kPairBlock, 0, s>>>(
+            n, h->g, h->list_hi, h->xq[h->cur], h->cell, h->cell_start, h->ps_start, h->ps_atom,
+            h->ps_list, h->ps_count, h->ps_cap, h->ds, gated);
+    else
+        pair_list_kernel<false><<<blocks, kPairBlock, 0, s>>>(
+            n, h->g, h->list_hi, h->xq[h->cur], h->cell, h->cell_start, h->ps_start, h->ps_atom,
+            h->ps_list, h->ps_count, h->ps_cap, h->ds, gated);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_forces(md_system *h, int mode, bool energy, bool store_f) {
+    ForceArgs a = make_force_args(h);
+    PairArgs p;
+    p.slot_start = h->ps_start;
+    p.slot_atom = h->ps_atom;
+    p.list = h->ps_list;
+    p.count = h->ps_count;
+    p.cap = h->ps_cap;
+    p.ncells = h->g.ncells;
+    const int sf = store_f ? 1 : 0;
+    const int64_t smax = pair_slots_max(h->n, h->g.ncells);
+    const int blocks = (int)((smax + kPairBlock - 1) / kPairBlock);
+    cudaStream_t s = h->stream;
+#define MDG_PAIR(M)                                                                   \
+    do {                                                                              \
+        if (energy) lj_pair_kernel<M, true><<<blocks, kPairBlock, 0, s>>>(a, p, sf);  \
+        else lj_pair_kernel<M, false><<<blocks, kPairBlock, 0, s>>>(a, p, sf);        \
+    } while (0)
+    switch (mode) {
+        case FM_STORE: MDG_PAIR(FM_STORE); break;
+        case FM_FUSED_FULL: MDG_PAIR(FM_FUSED_FULL); break;
+        default: MDG_PAIR(FM_FUSED_HALF); break;
+    }
+#undef MDG_PAIR
+    return cudaGetLastError();
+}
+
+}  // namespace mdg

@@ -56,7 +56,7 @@ md_status check_params(const md_params *p, int64_t n, const double *box, std::st
     if (p->potential != MD_POT_LJ && p->potential != MD_POT_SC && p->potential != MD_POT_EAM)
         return bad("unknown potential");
     if (p->precision != MD_FP64 && p->precision != MD_MIXED) return bad("unknown precision");
-    if (p->force_variant < MD_FORCE_FULL || p->force_variant > MD_FORCE_CLUSTER)
+    if (p->force_variant < MD_FORCE_FULL || p->force_variant > MD_FORCE_PAIRED)
         return bad("unknown force_variant");
     if (p->scheduler < MD_SCHED_GRID || p->scheduler > MD_SCHED_DYNAMIC)
         return bad("unknown scheduler");
@@ -95,6 +95,7 @@ void free_all(md_system *h) {
     F(h->exp_tmp); F(h->type_orig);
     F(h->cl_icnt); F(h->cl_jcnt); F(h->cl_ioff); F(h->cl_joff); F(h->cl_bsum); F(h->cl_icl);
     F(h->cl_icell); F(h->cl_jbox); F(h->cl_ntot); F(h->cl_list); F(h->cl_row);
+    F(h->ps_cnt); F(h->ps_start); F(h->ps_bsum); F(h->ps_atom); F(h->ps_list); F(h->ps_count);
     F(h->ov_cell_outer); F(h->ov_flag); F(h->ov_pos); F(h->ov_bsum); F(h->ov_gidx);
     F(h->ov_bidx); F(h->ov_nb); F(h->ov_send); F(h->ov_recv);
     if (h->ov_stream) cudaStreamDestroy(h->ov_stream);
@@ -135,6 +136,58 @@ cudaError_t alloc_cluster(md_system *h, int max_cell) {
         A(dalloc(&h->cl_list, (size_t)rows * cap));
     }
     return e;
+}
+
+// Slot tables, then a union list of ps_cap entries per slot; cap == 0 keeps
+// the list (tables only).
+cudaError_t alloc_pair(md_system *h, int cap) {
+    const size_t C = (size_t)h->g.ncells;
+    const int64_t smax = pair_slots_max(h->n, h->g.ncells);
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    if (!h->ps_cnt) {
+        A(dalloc(&h->ps_cnt, C)); A(dalloc(&h->ps_start, C + 1));
+        A(dalloc(&h->ps_bsum, C / (kBlock * 8) + 4)); A(dalloc(&h->ps_atom, (size_t)smax));
+        A(dalloc(&h->ps_count, (size_t)smax));
+    }
+    if (e == cudaSuccess && cap > 0 && (cap != h->ps_cap || !h->ps_list)) {
+        drop_graphs(h);  // captured steps hold the old list pointer and capacity
+        if (h->ps_list) cudaFree(h->ps_list);
+        h->ps_list = nullptr;
+        h->ps_cap = cap;
+        A(dalloc(&h->ps_list, (size_t)((smax + 31) / 32) * 32 * (size_t)cap));
+    }
+    return e;
+}
+
+int cap_for(int max_count);
+md_status read_status(md_system *h);
+md_status clear_status(md_system *h);
+
+// Slot tables and union lists for the current binning, sized from a count
+// pass when the list is new, regrown when a row overflows.
+md_status pair_rebuild_now(md_system *h) {
+    MD_CK(alloc_pair(h, 0));
+    if (!h->ps_list) {
+        MD_CK(launch_pair_build(h, false, false));
+        md_status st = read_status(h);
+        if (st != MD_OK) return st;
+        if (h->ds_host->status != 0)
+            return fail(h, (md_status)h->ds_host->status, "device error during slot list count");
+        MD_CK(alloc_pair(h, std::max(cap_for(h->ds_host->pair_max), 8)));
+    }
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        MD_CK(launch_pair_build(h, true, false));
+        md_status st = read_status(h);
+        if (st != MD_OK) return st;
+        if (h->ds_host->status == 0) return MD_OK;
+        if (h->ds_host->status != MD_ERR_LIST_OVERFLOW)
+            return fail(h, (md_status)h->ds_host->status, "device error during slot list build");
+        st = clear_status(h);
+        if (st != MD_OK) return st;
+        MD_CK(alloc_pair(h, cap_for(h->ds_host->pair_max)));
+    }
+    return fail(h, MD_ERR_LIST_OVERFLOW, "slot list overflow could not be repaired");
 }
 
 cudaError_t alloc_list(md_system *h, int cap) {
@@ -278,6 +331,10 @@ md_status enqueue_rebuild(md_system *h, bool gated) {
         MD_CK(launch_cluster_build(h, gated));
         h->launches += 9;
     }
+    if (h->p.force_variant == MD_FORCE_PAIRED) {
+        MD_CK(launch_pair_build(h, true, gated));
+        h->launches += 7;
+    }
     md_status st = enqueue_sched_prep(h, gated);
     if (st != MD_OK) return st;
     MD_CK(launch_finish_rebuild(h, gated));
@@ -322,6 +379,10 @@ md_status rebuild_now(md_system *h, bool size_from_count) {
         if (h->ds_host->status != 0)
             return fail(h, (md_status)h->ds_host->status, "device error during cluster build");
     }
+    if (h->p.force_variant == MD_FORCE_PAIRED) {
+        md_status st = pair_rebuild_now(h);
+        if (st != MD_OK) return st;
+    }
     md_status st = enqueue_sched_prep(h, false);
     if (st != MD_OK) return st;
     MD_CK(launch_finish_rebuild(h, false));
@@ -344,6 +405,9 @@ md_status enqueue_forces(md_system *h, int mode, bool energy, bool store_f) {
         h->launches += 4;
     } else if (h->p.force_variant == MD_FORCE_CLUSTER) {
         MD_CK(launch_cluster_forces(h, mode, energy, store_f));
+        h->launches += 1;
+    } else if (h->p.force_variant == MD_FORCE_PAIRED) {
+        MD_CK(launch_pair_forces(h, mode, energy, store_f));
         h->launches += 1;
     } else if (h->p.force_variant != MD_FORCE_FULL) {
         int nl = 0;
@@ -658,6 +722,10 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
             return fail(nullptr, MD_ERR_INVALID,
                         W + ": multi-element systems run full lists under MD_SCHED_GRID");
     }
+    if (p->force_variant == MD_FORCE_PAIRED &&
+        (R != 1 || p->scheduler != MD_SCHED_GRID || ltypes))
+        return fail(nullptr, MD_ERR_INVALID,
+                    W + ": two atoms per thread run one one-species box under MD_SCHED_GRID");
     if (p->force_variant == MD_FORCE_CLUSTER &&
         (R != 1 || p->scheduler != MD_SCHED_GRID || ltypes || n >= ((int64_t)1 << 25)))
         return fail(nullptr, MD_ERR_INVALID,
@@ -737,7 +805,8 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
     const size_t scan_len = std::max(N, C + 1) / (kBlock * 8) + 4;
     cudaError_t e = cudaSuccess;
     auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-    for (int b = 0; b < 2; ++b) { A(dalloc(&h->xr64[b], N)); A(dalloc(&h->xq[b], N)); }
+    // xq holds one more entry: the far dummy position of the slot lists' padding
+    for (int b = 0; b < 2; ++b) { A(dalloc(&h->xr64[b], N)); A(dalloc(&h->xq[b], N + 1)); }
     A(dalloc(&h->xq_build, N)); A(dalloc(&h->xabs, N)); A(dalloc(&h->v, 3 * N));
     A(dalloc(&h->f, 3 * N)); A(dalloc(&h->e_atom, N)); A(dalloc(&h->orig, N));
     A(dalloc(&h->cell, N)); A(dalloc(&h->cell_start, C + 1)); A(dalloc(&h->cell_count, C));
@@ -813,6 +882,7 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
     step(cudaMemsetAsync(h->f, 0, 3 * N * sizeof(double), h->stream), "memset f");
     step(cudaMemsetAsync(h->e_atom, 0, N * sizeof(double), h->stream), "memset e");
     if (!vel_dev) step(cudaMemsetAsync(h->v, 0, 3 * N * sizeof(double), h->stream), "memset v");
+    step(launch_pair_dummy(h), "dummy position");
     step(launch_load_state(h, pos_dev, vel_dev), "load_state");
     // host arrays above stay alive until the copies finish
     if (st == MD_OK) step(cudaStreamSynchronize(h->stream), "synchronize");
@@ -960,6 +1030,10 @@ md_status md_step(md_system *h, int64_t nsteps) {
         MD_CK(launch_build_list(h, true, false));
         if (h->ov_on) MD_CK(launch_overlap_index(h, false));
         if (h->p.force_variant == MD_FORCE_CLUSTER) MD_CK(launch_cluster_build(h, false));
+        if (h->p.force_variant == MD_FORCE_PAIRED) {
+            st = pair_rebuild_now(h);
+            if (st != MD_OK) return st;
+        }
         st = enqueue_sched_prep(h, false);
         if (st != MD_OK) return st;
         MD_CK(launch_finish_rebuild(h, false));
@@ -1092,7 +1166,7 @@ md_status md_get_atom_energy(md_system *h, double *e_dev) {
 
 md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler) {
     if (!h) return fail(nullptr, MD_ERR_INVALID, "md_set_variant: null handle");
-    if (force_variant < MD_FORCE_FULL || force_variant > MD_FORCE_CLUSTER ||
+    if (force_variant < MD_FORCE_FULL || force_variant > MD_FORCE_PAIRED ||
         scheduler < MD_SCHED_GRID || scheduler > MD_SCHED_DYNAMIC)
         return fail(h, MD_ERR_INVALID, "md_set_variant: unknown variant or scheduler");
     if ((h->p.potential == MD_POT_EAM || h->fc.ntypes > 0 || h->ov_on) &&
@@ -1112,10 +1186,13 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
         (scheduler != MD_SCHED_GRID || h->n >= ((int64_t)1 << 25)))
         return fail(h, MD_ERR_INVALID,
                     "md_set_variant: the cluster-pair list runs under MD_SCHED_GRID, n < 2^25");
+    if (force_variant == MD_FORCE_PAIRED && scheduler != MD_SCHED_GRID)
+        return fail(h, MD_ERR_INVALID, "md_set_variant: two atoms per thread run under MD_SCHED_GRID");
     // a change between half and full pair sets relists; entering the cluster
-    // layout builds its tables and list
+    // or the two-atom layout builds its tables and list
     const bool relist = half_variant(force_variant) != half_variant(h->p.force_variant) ||
-                        (force_variant == MD_FORCE_CLUSTER && h->p.force_variant != MD_FORCE_CLUSTER);
+                        (force_variant == MD_FORCE_CLUSTER && h->p.force_variant != MD_FORCE_CLUSTER) ||
+                        (force_variant == MD_FORCE_PAIRED && h->p.force_variant != MD_FORCE_PAIRED);
     drop_graphs(h);  // the captured steps launch the old variant's kernels
     h->p.force_variant = force_variant;
     h->p.scheduler = scheduler;
@@ -1339,14 +1416,15 @@ md_status md_stats(md_system *h, char *buf_host, size_t cap) {
                   "\"steps\": %lld, \"max_count\": %d, \"max_cell\": %d, \"status\": %d, "
                   "\"precision\": %d, \"force_variant\": %d, \"scheduler\": %d, "
                   "\"list_entries\": %llu, \"pairs_cut\": %llu, \"cluster_pairs\": %llu, "
-                  "\"launches\": %lld, "
+                  "\"slot_entries\": %llu, \"slot_max\": %d, \"launches\": %lld, "
                   "\"ms\": {\"rebuild\": %.6f, \"force\": %.6f, \"integrate\": %.6f, "
                   "\"other\": %.6f}, \"count\": {\"rebuild\": %lld, \"force\": %lld, "
                   "\"integrate\": %lld, \"other\": %lld}}",
                   (long long)h->n, h->g.nx, h->g.ny, h->g.nz, h->cap, d.builds,
                   (long long)h->steps_total, d.max_count, d.max_cell, d.status, h->p.precision,
                   h->p.force_variant, h->p.scheduler, d.list_entries, d.pairs_cut,
-                  d.cluster_pairs, h->launches + d.cond_runs * h->body_launches,
+                  d.cluster_pairs, d.pair_entries, d.pair_max,
+                  h->launches + d.cond_runs * h->body_launches,
                   h->ms_kind[0], h->ms_kind[1], h->ms_kind[2], h->ms_kind[3], h->n_kind[0],
                   h->n_kind[1], h->n_kind[2], h->n_kind[3]);
     return MD_OK;

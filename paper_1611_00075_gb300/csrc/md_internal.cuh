@@ -83,6 +83,9 @@ struct DevStatus {
     unsigned int done_ctas;           // dynamic scheduler: CTAs finished this launch
     long long cond_runs;              // rebuild chains run by a graph's IF node
     unsigned long long cluster_pairs; // (i-cluster, j-cluster) entries of the last cluster list
+    unsigned long long pair_entries;  // entries of the last two-atom slot list
+    int pair_max;                     // its longest row
+    int pad1;
 };
 
 // What the persistent force kernel needs besides ForceArgs.
@@ -110,10 +113,12 @@ struct Grid {
     const double *ctab; // cell centres (c + 0.5) w: nx for x, then ny for y, then nz for z
 };
 
-// Periodic wrap into [0, L): x - L*floor(x/L), which for |x| < 2L is the
-// single x += L or x -= L; the second test catches x + L rounding up to L.
+// Periodic wrap into [0, L): x - L*floor(x/L), then one correction each
+// way -- the rounded quotient can leave x a period off (a tiny negative x,
+// or x just below a multiple of L), and x + L can round up to L itself.
 __device__ __forceinline__ double wrap_coord(double x, double L) {
     if (x < 0.0 || x >= L) x -= L * floor(x / L);
+    if (x < 0.0) x += L;
     if (x >= L) x -= L;
     return x;
 }
@@ -283,6 +288,15 @@ struct md_system {
     int32_t *cl_row = nullptr;    // row lengths
     int cl_cap = 0;
 
+    // two home atoms per thread (MD_FORCE_PAIRED)
+    int32_t *ps_cnt = nullptr;     // slots per cell
+    int32_t *ps_start = nullptr;   // their scan (ncells + 1)
+    int32_t *ps_bsum = nullptr;
+    uint32_t *ps_atom = nullptr;   // slot: first atom | 2^31 for a one-atom slot
+    uint32_t *ps_list = nullptr;   // union lists, per-atom layout over slots
+    int32_t *ps_count = nullptr;   // their lengths
+    int ps_cap = 0;
+
     // inner/outer split of the force pass (md_set_decomposition)
     bool ov_on = false;
     int dd[3] = {1, 1, 1};               // virtual domains per dimension
@@ -361,6 +375,13 @@ cudaError_t launch_cluster_forces(md_system *h, int mode, bool energy, bool stor
 // then per force pass assemble, exchange, inner and outer passes (4 kernels)
 cudaError_t launch_overlap_index(md_system *h, bool gated);
 cudaError_t launch_overlap_forces(md_system *h, int mode, bool energy, bool store_f);
+// two atoms per thread (k_pair.cu): slot tables and union lists after a
+// rebuild (7 kernels), one force kernel; the padding entries point at a
+// dummy position at index n of both position buffers
+int64_t pair_slots_max(int64_t n, int ncells);
+cudaError_t launch_pair_dummy(md_system *h);
+cudaError_t launch_pair_build(md_system *h, bool write, bool gated);
+cudaError_t launch_pair_forces(md_system *h, int mode, bool energy, bool store_f);
 cudaError_t launch_eam_density(md_system *h);  // k_eam.cu
 cudaError_t launch_eam_force(md_system *h, int mode, bool energy, bool store_f);
 

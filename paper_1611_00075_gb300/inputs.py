@@ -114,6 +114,13 @@ def rescale_velocities(v, T: float, mass: float = 1.0) -> np.ndarray:
 MELT_SCHEDULE = ((2.4, 1000), (1.2, 1000))  # (T*, steps) per stage: 2,000 steps
 MELT_RESCALE_EVERY = 50
 
+# Equilibration of the porous solid before it is measured, in the same form:
+# the crystal with carved voids relaxes its surfaces and heats (run without
+# rescaling from T* 0.3 it settles near T* 0.4 within about 600 steps, its
+# rebuild rate rising from 9 to 12 per 100 steps); held at T* 0.3 by the
+# rescaling for 1,000 steps it reaches its steady rebuild rate.
+POROUS_EQUIL_SCHEDULE = ((0.3, 1000),)
+
 
 def tile(s: "System", k: int) -> "System":
     """k x k x k periodic copies of a cubic system (atoms of copy (a, b, c),

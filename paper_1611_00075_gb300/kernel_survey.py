@@ -3,8 +3,8 @@
 
     python -m paper_1611_00075_gb300.kernel_survey [part]
 
-part is one of lj, half_atomic, half_color, cluster, split, mlp, persist,
-eam, typed, sc (default: all).  The systems are about 1.2 M atoms each, so
+part is one of lj, half_atomic, half_color, cluster, paired, split, mlp,
+persist, eam, typed, sc (default: all).  The systems are about 1.2 M atoms each, so
 their state and lists exceed the 129 MB L2:
 - lj .. persist: porous Lennard-Jones, 80^3 fcc cells (1,223,941 atoms), one
   system that switches force variant and scheduler between parts;
@@ -21,8 +21,8 @@ import torch
 
 from . import inputs, md
 
-PARTS = ("lj", "half_atomic", "half_color", "cluster", "split", "mlp", "persist", "eam",
-         "typed", "sc")
+PARTS = ("lj", "half_atomic", "half_color", "cluster", "paired", "split", "mlp", "persist",
+         "eam", "typed", "sc")
 
 
 def main(only: str = "all") -> None:
@@ -43,7 +43,7 @@ def main(only: str = "all") -> None:
     def wanted(*names):
         return only == "all" or only in names
 
-    if wanted("lj", "half_atomic", "half_color", "cluster", "split", "mlp", "persist"):
+    if wanted("lj", "half_atomic", "half_color", "cluster", "paired", "split", "mlp", "persist"):
         s = inputs.lj_porous(nc=80)
         with md.System(s.pos, s.vel, s.box, precision="mixed") as m:
             md.md_step(m.h, 5)
@@ -51,7 +51,8 @@ def main(only: str = "all") -> None:
             run("lj", lambda: (md.md_step(m.h, 3), md.md_build_neighbors(m.h)))
             for name, code in (("half_atomic", md.MD_FORCE_HALF_ATOMIC),
                                ("half_color", md.MD_FORCE_HALF_COLOR),
-                               ("cluster", md.MD_FORCE_CLUSTER)):
+                               ("cluster", md.MD_FORCE_CLUSTER),
+                               ("paired", md.MD_FORCE_PAIRED)):
                 md.md_set_variant(m.h, code, md.MD_SCHED_GRID)
                 run(name, lambda: md.md_step(m.h, 2))
             md.md_set_variant(m.h, md.MD_FORCE_FULL, md.MD_SCHED_GRID)

@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "MD_OK", -1: "MD_ERR_INVALID", -2: "MD_ERR_OOM", -3: "MD_ERR_
 MD_POT_LJ, MD_POT_SC, MD_POT_EAM = 0, 1, 2
 MD_EAM_MAX_KNOTS = 16
 MD_FP64, MD_MIXED = 0, 1
-MD_FORCE_FULL, MD_FORCE_HALF_COLOR, MD_FORCE_HALF_ATOMIC, MD_FORCE_CLUSTER = 0, 1, 2, 3
+MD_FORCE_FULL, MD_FORCE_HALF_COLOR, MD_FORCE_HALF_ATOMIC, MD_FORCE_CLUSTER, MD_FORCE_PAIRED = 0, 1, 2, 3, 4
 MD_SCHED_GRID, MD_SCHED_PAIRCOUNT, MD_SCHED_MLP, MD_SCHED_DYNAMIC = 0, 1, 2, 3
 MD_COST_TRAIN, MD_COST_PREDICT, MD_COST_RESET, MD_COST_SAMPLE, MD_COST_PROFILE = 0, 1, 2, 3, 4
 MLP_NPARAMS = 1217

@@ -82,6 +82,37 @@ def test_single_atom_free_flight(md, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_wrap_at_the_box_faces_is_exact(md, orc, precision):
+    """Lattice atoms on the x = 0, y = 0 and z = 0 faces handed in as -0.0,
+    -1e-18 (x + L rounds to L itself) and L: each wraps to exactly the
+    generator's 0.0, so the state equals the generator's positions bit for
+    bit and the oracle, given those positions only, bins and lists them the
+    same way."""
+    s = inputs.lj_fcc(nc=6, T=0.72)
+    L = np.asarray(s.box)
+    pos0 = np.array(s.pos)
+    moved = pos0.copy()
+    for d in range(3):
+        at0 = np.flatnonzero(pos0[:, d] == 0.0)
+        assert len(at0) >= 9
+        moved[at0[0::3], d] = -0.0
+        moved[at0[1::3], d] = -1e-18
+        moved[at0[2::3], d] = L[d]
+    with md.System(moved, s.vel, s.box, precision=precision) as a:
+        p = a.state()[0].cpu().numpy()
+        nc, cell_of, start = a.cells()
+        off, ids = a.neighbors()
+    assert np.all((p >= 0.0) & (p < L))
+    assert np.array_equal(p, pos0)
+    onc, ocell, ostart, _ = orc.bin_cells(pos0, L, 2.8)
+    np.testing.assert_array_equal(cell_of.cpu().numpy(), ocell)
+    np.testing.assert_array_equal(start.cpu().numpy(), ostart)
+    ooff, oids = orc.neighbors_cells(pos0, L, 2.8)
+    np.testing.assert_array_equal(off.cpu().numpy(), ooff)
+    np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_positions_outside_the_box_are_wrapped(md, orc, precision):
     """Inputs shifted by -2..2 box lengths per component: the system holds the
     wrapped positions, and cells, lists and forces are those of the oracle on

@@ -1,0 +1,167 @@
+"""Two home atoms per thread (MD_FORCE_PAIRED: the atoms of a cell taken two
+at a time, one union list per pair, Sec. 4.1's grouping applied to the home
+side): forces and energies against the oracle with the mixed-path bars on
+dense, porous, disordered and dilute systems (cells of odd and of one-atom
+occupancy), 100 steps of config 1 against the oracle's trajectory, graph
+replay, the per-atom list kept for export, and the argument checks."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1611_00075_gb300 import inputs
+
+from cutoff_bounds import lj_straddle_bound
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def md():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1611_00075_gb300 import build
+    build.build()
+    from paper_1611_00075_gb300 import md as _md
+    torch.cuda.set_device(0)
+    _md.lib()
+    return _md
+
+
+def systems(name):
+    if name == "fcc4000":
+        s = inputs.lj_fcc(nc=10, T=0.72)
+        amp, seed = 0.05, 1991
+    elif name == "porous":
+        s = inputs.lj_porous(nc=14, fraction=0.4, rmin=2.0, rmax=5.0)
+        amp, seed = 0.05, 1992
+    elif name == "disordered":  # hot and disordered: cells of very different occupancy
+        s = inputs.lj_fcc(nc=8, T=1.2)
+        amp, seed = 0.12, 1993
+    else:  # dilute: about 5 atoms per cell, many cells with one or three
+        s = inputs.lj_fcc(nc=9, T=0.72)
+        keep = inputs.gaussian(1994, s.n) > 1.0
+        s = inputs.System(s.name + "_dilute", s.pos[keep], s.vel[keep], s.box, s.params)
+        amp, seed = 0.05, 1995
+    g = inputs.gaussian(seed, s.pos.size).reshape(-1, 3)
+    return s, np.mod(s.pos + amp * g, s.box)
+
+
+def near_cutoff(pos, box, off, ids, rc, delta):
+    rows = np.repeat(np.arange(len(pos)), np.diff(off))
+    d = pos[ids] - pos[rows]
+    d -= box * np.round(d / box)
+    r = np.sqrt(np.sum(d * d, axis=1))
+    bad = np.zeros(len(pos), bool)
+    bad[rows[np.abs(r - rc) < delta]] = True
+    return bad
+
+
+@pytest.mark.parametrize("name", ["fcc4000", "porous", "disordered", "dilute"])
+def test_paired_forces_and_energy_match_oracle(md, orc, name):
+    s, pos = systems(name)
+    off, ids = orc.neighbors_cells(pos, s.box, 2.8)
+    U0, f0 = orc.lj_list(pos, s.box, off, ids)
+    bad = near_cutoff(pos, s.box, off, ids, 2.5, 1e-5)
+    with md.System(pos, s.vel, s.box, precision="mixed",
+                   force_variant=md.MD_FORCE_PAIRED) as sy:
+        f = sy.state()[2].cpu().numpy()
+        ke, pe = sy.energy()
+        st = sy.stats()
+        goff, gids = sy.neighbors()
+        e_dev = torch.empty(s.n, dtype=torch.float64, device="cuda")
+        md.md_get_atom_energy(sy.h, e_dev)
+        e_atom = e_dev.cpu().numpy()
+        _, cell_of, start = sy.cells()
+    fn = np.linalg.norm(f0, axis=1)
+    rms = math.sqrt(np.mean(fn * fn))
+    err = np.linalg.norm(f - f0, axis=1)
+    tol = 2e-4 * fn + 1e-5 * max(1.0, rms)
+    assert np.all((err <= tol) | bad), int(((err > tol) & ~bad).sum())
+    slack = lj_straddle_bound(orc, pos, s.box, off, ids, 2.5, 1e-5)
+    assert abs(pe - U0) <= 2e-6 * abs(U0) + slack, (pe, U0)
+    assert abs(e_atom.sum() - pe) <= 1e-9 * abs(pe)
+    # the per-atom list is kept for export
+    np.testing.assert_array_equal(goff.cpu().numpy(), off)
+    np.testing.assert_array_equal(gids.cpu().numpy(), ids)
+    # every pair within r_c is counted from both of its atoms
+    rows = np.repeat(np.arange(s.n), np.diff(off))
+    d = pos[ids] - pos[rows]
+    d -= s.box * np.round(d / s.box)
+    r = np.sqrt(np.sum(d * d, axis=1))
+    in_rc = int((r < 2.5).sum())
+    assert abs(st["pairs_cut"] - in_rc) <= int((np.abs(r - 2.5) < 1e-5).sum())
+    # slots: ceil(occupancy / 2) per cell.  A slot's list holds the union of
+    # its atoms' lists without the two atoms themselves: at least half their
+    # sum less one, at most their sum (plus float32 band candidates)
+    occ = np.diff(start.cpu().numpy())
+    nslots = int(((occ + 1) // 2).sum())
+    assert off[-1] / 2 - nslots <= st["slot_entries"] <= off[-1] * 1.001 + 8
+    print("%s: %d atoms, %d slots, %d slot entries (%.2f per atom) against %d list entries"
+          % (name, s.n, nslots, st["slot_entries"],
+             st["slot_entries"] / s.n, off[-1]))
+
+
+def test_paired_steps_track_the_oracle(md, orc):
+    """100 steps of config 1 with two atoms per thread: total energy within
+    1e-6 relative of the oracle's trajectory after every tenth step; on a
+    side stream (graph replay) the run ends bit-equal to plain launches."""
+    s = inputs.lj_fcc(nc=10, T=0.72)
+    p = orc.make_params(potential=orc.POT_LJ, rc=2.5, skin=0.3, dt=0.005)
+    E0 = orc.md_run(p, s.pos, s.vel, s.box, 100)["energies"]
+    states = []
+    for stream in (None, torch.cuda.Stream()):
+        ctx = torch.cuda.stream(stream if stream is not None else torch.cuda.default_stream())
+        with ctx, md.System(s.pos, s.vel, s.box, precision="mixed", stream=stream,
+                            force_variant=md.MD_FORCE_PAIRED) as sy:
+            es = [sy.energy()]
+            for _ in range(10):
+                sy.step(10)
+                es.append(sy.energy())
+            states.append(sy.state())
+            builds = sy.stats()["builds"]
+        es = np.array(es)
+        rel = np.abs(es[:, 0] + es[:, 1] - E0[::10, 2]) / np.abs(E0[::10, 2])
+        print("paired: max relative total-energy error %.3g, %d builds" % (rel.max(), builds))
+        assert rel.max() < 1e-6, rel.max()
+        assert builds > 2
+    for x, y in zip(states[0], states[1]):
+        assert torch.equal(x, y)
+
+
+def test_paired_melt_nve_matches_oracle(md, orc):
+    """A melted 4,000-atom liquid (the oracle's melt of config 1's crystal),
+    100 steps with two atoms per thread: total energy within 1e-6 relative of
+    the oracle's trajectory at every step."""
+    from melt import oracle_melt
+    s = oracle_melt(orc, 10)
+    p = orc.make_params(potential=orc.POT_LJ, rc=2.5, skin=0.3, dt=0.005)
+    E0 = orc.md_run(p, s.pos, s.vel, s.box, 100)["energies"]
+    with md.System(s.pos, s.vel, s.box, precision="mixed",
+                   force_variant=md.MD_FORCE_PAIRED) as sy:
+        es = [sy.energy()]
+        for _ in range(100):
+            sy.step(1)
+            es.append(sy.energy())
+    es = np.array(es)
+    rel = np.abs(es[:, 0] + es[:, 1] - E0[:, 2]) / np.abs(E0[:, 2])
+    assert rel.max() < 1e-6, rel.max()
+
+
+def test_paired_variant_switch_and_checks(md, orc):
+    s, pos = systems("disordered")
+    with md.System(pos, s.vel, s.box, precision="mixed") as sy:
+        f_full = sy.state()[2].cpu().numpy()
+        md.md_set_variant(sy.h, md.MD_FORCE_PAIRED, md.MD_SCHED_GRID)
+        md.md_forces(sy.h)
+        f_p = sy.state()[2].cpu().numpy()
+        sy.step(20)
+        with pytest.raises(md.MDError):
+            md.md_set_variant(sy.h, md.MD_FORCE_PAIRED, md.MD_SCHED_PAIRCOUNT)
+        md.md_set_variant(sy.h, md.MD_FORCE_FULL, md.MD_SCHED_GRID)
+        sy.step(5)
+    assert np.max(np.abs(f_p - f_full)) < 1e-4 * max(1.0, np.abs(f_full).max())
+    with pytest.raises(md.MDError):
+        md.System(pos, s.vel, s.box, precision="fp64", force_variant=md.MD_FORCE_PAIRED)
