@@ -730,7 +730,14 @@ def cpu_baseline_leg(args, gpu=None, steps=None, repeats=5):
     orc.set_threads(cores)
     s, what = oracle_sample_system(args, orc)
     prm = oracle_params(orc, s.params)
-    k = steps if steps is not None else 10
+    k = steps
+    if k is None:
+        # about 2.5 s per run (a dozen seconds of CPU work in all): the step
+        # count from one force evaluation with its list build
+        t0 = time.perf_counter()
+        orc.forces_once(prm, s.pos, s.box)
+        est = time.perf_counter() - t0
+        k = int(min(200, max(10, round(2.5 / max(est, 1e-6)))))
     rates = []
     for _ in range(repeats):
         t0 = time.perf_counter()

@@ -63,3 +63,26 @@ def test_noalloc_at_its_exact_size_limit(md):
         md.md_partition_noalloc(c, nparts, got)
         torch.cuda.synchronize()
         assert torch.equal(got, ref), (seed, nparts)
+
+
+def test_noalloc_inside_a_captured_graph(md):
+    """After one call on the device, md_partition_noalloc is captured into a
+    CUDA graph on a side stream; replays with new costs copied into the
+    captured input give md_partition's bounds."""
+    ncells, nparts = 300000, 1001
+    c = costs(905, ncells)
+    got = torch.full((nparts + 1,), -1, dtype=torch.int64, device="cuda")
+    md.md_partition_noalloc(c, nparts, got)  # the first call on the device
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        md.md_partition_noalloc(c, nparts, got, stream=side)
+    for seed in (906, 907):
+        c.copy_(costs(seed, ncells))
+        got.fill_(-1)
+        g.replay()
+        ref = torch.empty(nparts + 1, dtype=torch.int64, device="cuda")
+        md.md_partition(c, nparts, ref)
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref), seed
