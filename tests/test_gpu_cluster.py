@@ -98,6 +98,7 @@ def test_cluster_steps_track_the_oracle(md, orc):
             states.append(sy.state())
         es = np.array(es)
         rel = np.abs(es[:, 0] + es[:, 1] - E0[::10, 2]) / np.abs(E0[::10, 2])
+        print("cluster pairs: max relative total-energy error %.3g" % rel.max())
         assert rel.max() < 1e-6, rel.max()
     for x, y in zip(states[0], states[1]):
         assert torch.equal(x, y)

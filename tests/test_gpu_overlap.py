@@ -77,6 +77,7 @@ def test_split_steps_track_the_oracle(md, orc, stream):
         state = sy.state()
     es = np.array(es)
     rel = np.abs(es[:, 0] + es[:, 1] - E0[::10, 2]) / np.abs(E0[::10, 2])
+    print("inner/outer split: max relative total-energy error %.3g" % rel.max())
     assert rel.max() < 1e-6, rel.max()
     if stream == "side":
         with md.System(s.pos, s.vel, s.box, precision="mixed") as sy:

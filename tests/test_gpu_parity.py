@@ -277,6 +277,7 @@ def test_nve_100_steps_fp64_config1(md, orc):
     es = np.array(es)
     tot = es[:, 0] + es[:, 1]
     rel = np.abs(tot - E0[:, 2]) / np.abs(E0[:, 2])
+    print("fp64 config 1: max relative total-energy error over 100 steps %.3g" % rel.max())
     assert np.max(rel) < 1e-6, np.max(rel)
 
 
