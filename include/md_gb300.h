@@ -275,9 +275,10 @@ md_status md_get_atom_energy(md_system *h, double *e_dev);
  * potential and precision) and rebuilds what the new choice needs (the list
  * when switching between full and half lists, the cell partition for the
  * static schedulers).  Half lists (Newton's third law, each pair once, owned
- * by the lower original id) are built for the mixed-precision Lennard-Jones
- * path; the persistent schedulers drive the full-list Lennard-Jones pass of
- * either precision, and every other combination runs one thread per atom. */
+ * by the lower original id) are built for one-species Lennard-Jones on
+ * either path; the cluster and two-atom layouts for its mixed path; the
+ * persistent schedulers drive the full-list Lennard-Jones pass of either
+ * precision, and every other combination runs one thread per atom. */
 md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler);
 
 /* Colour of every cell of an ncell_host[0] x [1] x [2] grid (each >= 3) as

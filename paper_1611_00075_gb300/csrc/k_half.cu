@@ -14,11 +14,13 @@
 //                targets j are distinct, so f_j is updated with plain loads
 //                and stores -- no atomics, like the paper's lock-free tasks.
 //
-// A half list holds pair (i, j) at the atom with the lower original id.  Pair
-// terms are float32 as in the full-list mixed kernel; every update of f and
-// of the per-atom energy (split half and half between the two atoms) is
-// float64.  The velocity-Verlet update runs afterwards in integrate_kernel,
-// because an atom's force is complete only when the whole pass has finished.
+// A half list holds pair (i, j) at the atom with the lower original id.  On
+// the mixed path the pair terms are float32 as in the full-list mixed kernel;
+// on the float64 path (F64) they are float64 from the float64 cell-relative
+// positions, as in the plain full-list kernel.  Every update of f and of the
+// per-atom energy (split half and half between the two atoms) is float64.
+// The velocity-Verlet update runs afterwards in integrate_kernel, because an
+// atom's force is complete only when the whole pass has finished.
 #include "k_common.cuh"
 
 namespace mdg {
@@ -33,6 +35,62 @@ __device__ __forceinline__ void shifts_f32(const Grid &g, float4 *sh) {
                             0.f);
     }
 }
+
+__device__ __forceinline__ void shifts_f64(const Grid &g, double3 *sh) {
+    if (threadIdx.x < kStencil) {
+        int s = threadIdx.x;
+        int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = s / 9 - 1;
+        sh[s] = make_double3(dx * g.w[0], dy * g.w[1], dz * g.w[2]);
+    }
+}
+
+// fp64 pair term for list entry `ent` of atom i at ri; returns false outside r_c.
+__device__ __forceinline__ bool lj_pair_f64(const ForceArgs &a, const double3 *sh,
+                                            const double4 &ri, uint32_t ent, double &Fx,
+                                            double &Fy, double &Fz, double &phi) {
+    const double4 rj = a.xr[ent & kIndexMask];
+    const double3 sd = sh[ent >> kIndexBits];
+    const double ex = (rj.x - ri.x) + sd.x;
+    const double ey = (rj.y - ri.y) + sd.y;
+    const double ez = (rj.z - ri.z) + sd.z;
+    const double r2 = ex * ex + ey * ey + ez * ez;
+    if (!(r2 < a.fc.rc2)) return false;
+    const double r2i = 1.0 / r2;
+    double s6 = a.fc.sig2 * r2i;
+    s6 = s6 * s6 * s6;
+    const double fs = a.fc.eps48 * r2i * s6 * (s6 - 0.5);
+    Fx = -fs * ex;  // force on i: fs (r_i - r_j)
+    Fy = -fs * ey;
+    Fz = -fs * ez;
+    phi = a.fc.eps4 * s6 * (s6 - 1.0) - a.fc.shift;
+    return true;
+}
+
+// Shared-memory shift table and the pair term of one precision.
+template <bool F64>
+struct HalfPrec;
+template <>
+struct HalfPrec<false> {
+    using Acc = float;
+    using Pos = float4;
+    struct Tab { float4 s[kStencil]; };
+    static __device__ __forceinline__ void load(const Grid &g, Tab *t) { shifts_f32(g, t->s); }
+    static __device__ __forceinline__ Pos pos(const ForceArgs &a, int i) { return a.xq[i]; }
+    static __device__ __forceinline__ bool pair(const ForceArgs &a, const Tab *t, const Pos &p,
+                                                uint32_t ent, Acc &x, Acc &y, Acc &z, Acc &e);
+};
+template <>
+struct HalfPrec<true> {
+    using Acc = double;
+    using Pos = double4;
+    struct Tab { double3 s[kStencil]; };
+    static __device__ __forceinline__ void load(const Grid &g, Tab *t) { shifts_f64(g, t->s); }
+    static __device__ __forceinline__ Pos pos(const ForceArgs &a, int i) { return a.xr[i]; }
+    static __device__ __forceinline__ bool pair(const ForceArgs &a, const Tab *t, const Pos &p,
+                                                uint32_t ent, Acc &x, Acc &y, Acc &z, Acc &e) {
+        return lj_pair_f64(a, t->s, p, ent, x, y, z, e);
+    }
+};
 
 // fp32 pair term for list entry `ent` of atom i at qi; returns false outside r_c.
 __device__ __forceinline__ bool lj_pair_f32(const ForceArgs &a, const float4 *sh,
@@ -56,26 +114,34 @@ __device__ __forceinline__ bool lj_pair_f32(const ForceArgs &a, const float4 *sh
     return true;
 }
 
-template <bool ENERGY>
+__device__ __forceinline__ bool HalfPrec<false>::pair(const ForceArgs &a, const Tab *t,
+                                                      const Pos &p, uint32_t ent, Acc &x,
+                                                      Acc &y, Acc &z, Acc &e) {
+    return lj_pair_f32(a, t->s, p, ent, x, y, z, e);
+}
+
+template <bool ENERGY, bool F64>
 __global__ void __launch_bounds__(kBlock) lj_half_atomic_kernel(ForceArgs a) {
-    __shared__ float4 sh[kStencil];
-    shifts_f32(a.g, sh);
+    using P = HalfPrec<F64>;
+    using Acc = typename P::Acc;
+    __shared__ typename P::Tab sh;
+    P::load(a.g, &sh);
     __syncthreads();
     if (a.ds->status != 0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const size_t n = (size_t)a.n;
-    const float4 qi = a.xq[i];
+    const typename P::Pos qi = P::pos(a, i);
     const int cnt = min(a.ncount[i], a.cap);
     double Fx = 0.0, Fy = 0.0, Fz = 0.0, E = 0.0;
     unsigned npair = 0;
     for (int k0 = 0; k0 < cnt; k0 += 4 * kChunkQ) {
         const int k1 = min(k0 + 4 * kChunkQ, cnt);
-        float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+        Acc fx = 0, fy = 0, fz = 0, e = 0;
         for (int k = k0; k < k1; ++k) {
             const uint32_t ent = __ldg(a.nlist + list_idx(i, k, a.cap));
-            float px, py, pz, phi;
-            if (!lj_pair_f32(a, sh, qi, ent, px, py, pz, phi)) continue;
+            Acc px, py, pz, phi;
+            if (!P::pair(a, &sh, qi, ent, px, py, pz, phi)) continue;
             const size_t j = ent & kIndexMask;
             fx += px;
             fy += py;
@@ -84,7 +150,7 @@ __global__ void __launch_bounds__(kBlock) lj_half_atomic_kernel(ForceArgs a) {
             atomicAdd(a.f + n + j, -(double)py);
             atomicAdd(a.f + 2 * n + j, -(double)pz);
             if (ENERGY) {
-                e += 0.5f * phi;
+                e += Acc(0.5) * phi;
                 atomicAdd(a.e_atom + j, 0.5 * (double)phi);
                 ++npair;
             }
@@ -109,10 +175,12 @@ struct ColorArgs {
     int tx, ty, tz;     // cells of that colour per dimension
 };
 
-template <bool ENERGY>
+template <bool ENERGY, bool F64>
 __global__ void __launch_bounds__(kBlock) lj_half_color_kernel(ForceArgs a, ColorArgs ca) {
-    __shared__ float4 sh[kStencil];
-    shifts_f32(a.g, sh);
+    using P = HalfPrec<F64>;
+    using Acc = typename P::Acc;
+    __shared__ typename P::Tab sh;
+    P::load(a.g, &sh);
     __syncthreads();
     if (a.ds->status != 0) return;
     const int lane = threadIdx.x & 31;
@@ -125,13 +193,13 @@ __global__ void __launch_bounds__(kBlock) lj_half_color_kernel(ForceArgs a, Colo
     const size_t n = (size_t)a.n;
     unsigned npair = 0;
     for (int i = ca.cell_start[c]; i < ca.cell_start[c + 1]; ++i) {
-        const float4 qi = a.xq[i];
+        const typename P::Pos qi = P::pos(a, i);
         const int cnt = min(a.ncount[i], a.cap);
-        float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
+        Acc fx = 0, fy = 0, fz = 0, e = 0;
         for (int k = lane; k < cnt; k += 32) {
             const uint32_t ent = __ldg(a.nlist + list_idx(i, k, a.cap));
-            float px, py, pz, phi;
-            if (!lj_pair_f32(a, sh, qi, ent, px, py, pz, phi)) continue;
+            Acc px, py, pz, phi;
+            if (!P::pair(a, &sh, qi, ent, px, py, pz, phi)) continue;
             const size_t j = ent & kIndexMask;  // distinct across the lanes
             fx += px;
             fy += py;
@@ -140,7 +208,7 @@ __global__ void __launch_bounds__(kBlock) lj_half_color_kernel(ForceArgs a, Colo
             a.f[n + j] -= (double)py;
             a.f[2 * n + j] -= (double)pz;
             if (ENERGY) {
-                e += 0.5f * phi;
+                e += Acc(0.5) * phi;
                 a.e_atom[j] += 0.5 * (double)phi;
                 ++npair;
             }
@@ -184,9 +252,16 @@ cudaError_t launch_lj_half(md_system *h, int mode, bool energy, int *launches) {
     if (e == cudaSuccess && energy) e = cudaMemsetAsync(h->e_atom, 0, n * sizeof(double), s);
     if (e != cudaSuccess) return e;
     int nl = 0;
+    const bool f64 = (h->p.precision == MD_FP64);
     if (h->p.force_variant == MD_FORCE_HALF_ATOMIC) {
-        if (energy) lj_half_atomic_kernel<true><<<nblocks(h->n), kBlock, 0, s>>>(a);
-        else lj_half_atomic_kernel<false><<<nblocks(h->n), kBlock, 0, s>>>(a);
+        const int nb = nblocks(h->n);
+        if (f64) {
+            if (energy) lj_half_atomic_kernel<true, true><<<nb, kBlock, 0, s>>>(a);
+            else lj_half_atomic_kernel<false, true><<<nb, kBlock, 0, s>>>(a);
+        } else {
+            if (energy) lj_half_atomic_kernel<true, false><<<nb, kBlock, 0, s>>>(a);
+            else lj_half_atomic_kernel<false, false><<<nb, kBlock, 0, s>>>(a);
+        }
         ++nl;
     } else {
         const Grid &g = h->g;
@@ -201,8 +276,13 @@ cudaError_t launch_lj_half(md_system *h, int mode, bool energy, int *launches) {
                     ca.tz = color_count_1d(kz, g.nz);
                     const long long warps = (long long)ca.tx * ca.ty * ca.tz;
                     const int nb = (int)((warps * 32 + kBlock - 1) / kBlock);
-                    if (energy) lj_half_color_kernel<true><<<nb, kBlock, 0, s>>>(a, ca);
-                    else lj_half_color_kernel<false><<<nb, kBlock, 0, s>>>(a, ca);
+                    if (f64) {
+                        if (energy) lj_half_color_kernel<true, true><<<nb, kBlock, 0, s>>>(a, ca);
+                        else lj_half_color_kernel<false, true><<<nb, kBlock, 0, s>>>(a, ca);
+                    } else {
+                        if (energy) lj_half_color_kernel<true, false><<<nb, kBlock, 0, s>>>(a, ca);
+                        else lj_half_color_kernel<false, false><<<nb, kBlock, 0, s>>>(a, ca);
+                    }
                     ++nl;
                 }
     }

@@ -21,9 +21,12 @@
 // either atom is below r_list^2 (1 + 2^-14), which covers every pair within
 // r_list -- and so, by the half-skin rule, every pair within r_c until the
 // next rebuild.  The force pass evaluates the slot's own pair once
-// (f_i0 += F, f_i1 -= F), then both atoms against each list entry, with the
-// mixed-precision arithmetic of the per-atom kernel (float32 pair terms,
-// float32 chunk sums added in float64) and its velocity-Verlet epilogue.
+// (f_i0 += F, f_i1 -= F), then both atoms against each list entry in
+// float32, with the per-atom kernel's velocity-Verlet epilogue.  Each atom's
+// force is summed in float32 over the whole list (about 55 entries per atom
+// at rho* = 0.8442, so one chunk of the per-atom kernel's float32-then-
+// float64 sums) and converted once: without the float64 accumulators the
+// kernel fits 9 CTAs of 128 threads per SM.
 #include "k_common.cuh"
 #include "k_scan.cuh"
 
@@ -208,7 +211,6 @@ __device__ __forceinline__ void lj_pair_slot(const ForceArgs &a, const PairArgs 
     // a one-atom slot puts its second atom at the dummy's distance
     const float4 q1 = two ? a.xq[i0 + 1] : make_float4(3.0e18f, 3.0e18f, 3.0e18f, 0.f);
     const float rc2 = a.fc.rc2f;
-    double F0x = 0.0, F0y = 0.0, F0z = 0.0, F1x = 0.0, F1y = 0.0, F1z = 0.0, E0 = 0.0, E1 = 0.0;
     float f0x = 0.f, f0y = 0.f, f0z = 0.f, f1x = 0.f, f1y = 0.f, f1z = 0.f, e0 = 0.f, e1 = 0.f;
     unsigned np0 = 0, np1 = 0;
     {
@@ -242,45 +244,30 @@ __device__ __forceinline__ void lj_pair_slot(const ForceArgs &a, const PairArgs 
         if (rb < rc2) lj_term<ENERGY>(a.fc, bx, by, bz, rb, f1x, f1y, f1z, e1, np1);
     };
     uint4 nxt = nq > 0 ? __ldcs(lq) : make_uint4(0u, 0u, 0u, 0u);
-    for (int c0 = 0; c0 < nq; c0 += kChunkQ) {
-        const int c1 = min(c0 + kChunkQ, nq);
-        for (int q = c0; q < c1; ++q) {
-            const uint4 e4 = nxt;
-            if (q + 1 < nq) nxt = __ldcs(lq + (size_t)(q + 1) * 32);
-            pair(e4.x);
-            pair(e4.y);
-            pair(e4.z);
-            pair(e4.w);
-        }
-        F0x += (double)f0x; F0y += (double)f0y; F0z += (double)f0z;
-        F1x += (double)f1x; F1y += (double)f1y; F1z += (double)f1z;
-        f0x = f0y = f0z = f1x = f1y = f1z = 0.f;
-        if (ENERGY) {
-            E0 += (double)e0;
-            E1 += (double)e1;
-            e0 = e1 = 0.f;
-        }
+    for (int q = 0; q < nq; ++q) {
+        const uint4 e4 = nxt;
+        if (q + 1 < nq) nxt = __ldcs(lq + (size_t)(q + 1) * 32);
+        pair(e4.x);
+        pair(e4.y);
+        pair(e4.z);
+        pair(e4.w);
     }
-    // a slot without list entries still carries its own pair
-    F0x += (double)f0x; F0y += (double)f0y; F0z += (double)f0z;
-    F1x += (double)f1x; F1y += (double)f1y; F1z += (double)f1z;
-    if (ENERGY) {
-        E0 += (double)e0;
-        E1 += (double)e1;
-    }
+    const double F0x = f0x, F0y = f0y, F0z = f0z, F1x = f1x, F1y = f1y, F1z = f1z;
+    const double E0 = e0, E1 = e1;
     pair_atom_out<MODE, ENERGY>(a, i0, F0x, F0y, F0z, E0, np0, q0.w, store_f);
     if (two) pair_atom_out<MODE, ENERGY>(a, i0 + 1, F1x, F1y, F1z, E1, np1, q1.w, store_f);
 }
 
-// Measured on GB300 (porous LJ, 9.8 M atoms, one force launch): this scalar
-// form at 72 registers (7 CTAs per SM) 1.498 ms; the same with packed
-// float32 pair arithmetic (add/mul/fma.rn.f32x2, both atoms in one
-// instruction) 1.551 ms at 72 registers and 1.690 ms at 64; the per-atom
-// kernel 1.307 ms.  The slot lists hold 0.68 times the per-atom entries and
-// the kernel issues fewer instructions and L1 wavefronts, but with fewer
-// warps resident its gathers' latency is no longer hidden.
+// Measured on GB300 (porous LJ, 9.8 M atoms, one force launch, from the
+// generated state): this form at 56 registers (9 CTAs per SM) 1.387 ms; with
+// float64 chunk accumulators at 72 registers (7 CTAs) 1.498 ms, and with
+// packed float32 pair arithmetic (add/mul/fma.rn.f32x2, both atoms in one
+// instruction) on top 1.551 ms; the per-atom kernel 1.308 ms.  The slot
+// lists hold 0.68 times the per-atom entries and the kernel issues fewer
+// instructions and L1 wavefronts, but fewer of its lanes stay active (a
+// warp's 64 atoms span more cells, whose list lengths differ).
 template <int MODE, bool ENERGY>
-__global__ void __launch_bounds__(kPairBlock, 7) lj_pair_kernel(ForceArgs a, PairArgs p,
+__global__ void __launch_bounds__(kPairBlock, 9) lj_pair_kernel(ForceArgs a, PairArgs p,
                                                                 int store_f) {
     __shared__ ShiftTab sh;
     load_shifts_f32(a.g, &sh);

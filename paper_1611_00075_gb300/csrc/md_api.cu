@@ -733,8 +733,10 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
                         "n < 2^25");
     if (p->force_variant != MD_FORCE_FULL && p->potential != MD_POT_LJ)
         return fail(nullptr, MD_ERR_INVALID, W + ": half lists are built for Lennard-Jones only");
-    if (p->force_variant != MD_FORCE_FULL && p->precision != MD_MIXED)
-        return fail(nullptr, MD_ERR_INVALID, W + ": half lists are built for the mixed path");
+    if ((p->force_variant == MD_FORCE_CLUSTER || p->force_variant == MD_FORCE_PAIRED) &&
+        p->precision != MD_MIXED)
+        return fail(nullptr, MD_ERR_INVALID,
+                    W + ": the cluster and two-atom layouts are built for the mixed path");
     if (R > 1 && (p->potential != MD_POT_LJ || p->precision != MD_MIXED ||
                   p->force_variant != MD_FORCE_FULL ||
                   (p->scheduler != MD_SCHED_GRID && p->scheduler != MD_SCHED_DYNAMIC)))
@@ -1176,8 +1178,10 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
                     "systems run full lists under MD_SCHED_GRID");
     if (force_variant != MD_FORCE_FULL && h->p.potential == MD_POT_SC)
         return fail(h, MD_ERR_INVALID, "md_set_variant: half lists are built for Lennard-Jones only");
-    if (force_variant != MD_FORCE_FULL && h->p.precision != MD_MIXED)
-        return fail(h, MD_ERR_INVALID, "md_set_variant: half lists are built for the mixed path");
+    if ((force_variant == MD_FORCE_CLUSTER || force_variant == MD_FORCE_PAIRED) &&
+        h->p.precision != MD_MIXED)
+        return fail(h, MD_ERR_INVALID,
+                    "md_set_variant: the cluster and two-atom layouts are built for the mixed path");
     if (h->R > 1 && (force_variant != MD_FORCE_FULL ||
                      (scheduler != MD_SCHED_GRID && scheduler != MD_SCHED_DYNAMIC)))
         return fail(h, MD_ERR_INVALID,

@@ -206,9 +206,7 @@ def test_orthorhombic_box(md, orc, precision, variant):
     """Different cell counts and widths per dimension: cells and lists
     bit-exact, forces within the bars, and 60 steps with rebuilds against the
     oracle's total energy (1e-6 relative on the fp64 path, 1e-4 mixed).  The
-    half-list variants (mixed path only) colour a 3 x 4 x 6 grid."""
-    if variant != "full" and precision == "fp64":
-        pytest.skip("half lists are built for the mixed path")
+    half-list variants colour a 3 x 4 x 6 grid."""
     pos, vel, box = orthorhombic()
     code = {"full": md.MD_FORCE_FULL, "color": md.MD_FORCE_HALF_COLOR,
             "atomic": md.MD_FORCE_HALF_ATOMIC}[variant]

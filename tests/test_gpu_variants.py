@@ -39,9 +39,10 @@ def variant_code(md, name):
     return {"color": md.MD_FORCE_HALF_COLOR, "atomic": md.MD_FORCE_HALF_ATOMIC}[name]
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
 @pytest.mark.parametrize("variant", ["color", "atomic"])
 @pytest.mark.parametrize("sysname", ["fcc4000", "porous13"])
-def test_half_variants_match_oracle(md, orc, variant, sysname):
+def test_half_variants_match_oracle(md, orc, variant, sysname, precision):
     s, pos = systems()[sysname]
     off, ids = orc.neighbors_cells(pos, s.box, 2.8)
     U0, f0 = orc.lj_list(pos, s.box, off, ids)
@@ -50,8 +51,8 @@ def test_half_variants_match_oracle(md, orc, variant, sysname):
     d -= s.box * np.round(d / s.box)
     r = np.sqrt((d * d).sum(1))
     bad = np.zeros(len(pos), bool)
-    bad[rows[np.abs(r - 2.5) < 1e-5]] = True
-    with md.System(pos, s.vel, s.box, precision="mixed",
+    bad[rows[np.abs(r - 2.5) < (1e-5 if precision == "mixed" else 1e-12)]] = True
+    with md.System(pos, s.vel, s.box, precision=precision,
                    force_variant=variant_code(md, variant)) as sy:
         _, _, f = sy.state()
         ke, pe = sy.energy()
@@ -62,8 +63,12 @@ def test_half_variants_match_oracle(md, orc, variant, sysname):
     fn = np.linalg.norm(f0, axis=1)
     rms = math.sqrt(np.mean(fn * fn))
     err = np.linalg.norm(f - f0, axis=1)
-    assert np.all((err <= 2e-4 * fn + 1e-5 * max(1.0, rms)) | bad)
-    assert abs(pe - U0) <= 2e-6 * abs(U0)
+    if precision == "mixed":
+        assert np.all((err <= 2e-4 * fn + 1e-5 * max(1.0, rms)) | bad)
+        assert abs(pe - U0) <= 2e-6 * abs(U0)
+    else:
+        assert np.all((err <= 1e-5 * fn + 1e-9 * rms) | bad)
+        assert abs(pe - U0) <= 1e-10 * abs(U0)
     ho, hi = orc.neighbors_cells(pos, s.box, 2.8, half=True)
     np.testing.assert_array_equal(hoff.cpu().numpy(), ho)
     np.testing.assert_array_equal(hids.cpu().numpy(), hi)
@@ -131,3 +136,26 @@ def test_switch_variant_under_graph_replay(md, orc, variant):
     assert np.all((err <= 2e-4 * fn + 1e-5 * max(1.0, rms)) | bad)
     E = orc.md_run(prm, pos, s.vel, s.box, 60)["energies"][-1, 2]
     assert abs(ke + pe - E) < 1e-4 * abs(E), (ke + pe, E)
+
+
+@pytest.mark.parametrize("variant", ["color", "atomic"])
+def test_half_lists_fp64_nve_config1(md, orc, variant):
+    """The float64 half-list passes on config 1 (4,000-atom fcc, T* 0.72):
+    total energy after every tenth of 100 steps within 1e-6 relative of the
+    oracle's trajectory, with the list rebuilt on the way."""
+    s = inputs.lj_fcc(nc=10, T=0.72)
+    p = orc.make_params(potential=orc.POT_LJ, rc=2.5, skin=0.3, dt=0.005)
+    E0 = orc.md_run(p, s.pos, s.vel, s.box, 100)["energies"]
+    with md.System(s.pos, s.vel, s.box, precision="fp64",
+                   force_variant=variant_code(md, variant)) as sy:
+        es = [sy.energy()]
+        for _ in range(10):
+            sy.step(10)
+            es.append(sy.energy())
+        builds = sy.stats()["builds"]
+    es = np.array(es)
+    rel = np.abs(es[:, 0] + es[:, 1] - E0[::10, 2]) / np.abs(E0[::10, 2])
+    print("fp64 half list (%s): max relative total-energy error %.3g, %d builds"
+          % (variant, rel.max(), builds))
+    assert rel.max() < 1e-6, rel.max()
+    assert builds > 2
