@@ -209,3 +209,33 @@ def test_ensemble_64_replicas(md, orc):
                                           oids[ooff[k]:ooff[k + 1]])
         check_forces(orc, prm, np.ascontiguousarray(f[a0:a1]), p_r, box, idx, ooff, oids, 2.5,
                      2e-4, 1e-5)
+
+
+@pytest.mark.parametrize("variant", ["paired", "cluster", "split", "half_atomic"])
+def test_porous_9_8m_force_variants(md, orc, variant):
+    """The other force layouts at the headline size (9,828,959 porous atoms,
+    mixed path), as bench.py's comparison runs them: 10 steps (rebuilds and
+    graph replay), then generator positions loaded, and the sampled forces
+    against the oracle.  The list rows (kept per atom by every layout) are
+    checked too."""
+    s = inputs.lj_porous()
+    p = s.params
+    prm = orc.make_params(potential=orc.POT_LJ, rc=p["rc"], skin=p["skin"], dt=p["dt"])
+    code = {"paired": md.MD_FORCE_PAIRED, "cluster": md.MD_FORCE_CLUSTER,
+            "split": md.MD_FORCE_FULL, "half_atomic": md.MD_FORCE_HALF_ATOMIC}[variant]
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        with md.System(s.pos, s.vel, s.box, precision="mixed", stream=st, rc=p["rc"],
+                       skin=p["skin"], dt=p["dt"], force_variant=code) as a:
+            if variant == "split":
+                md.md_set_decomposition(a.h, 2, 2, 2)
+            a.step(10)
+            pos = perturbed(s.pos, s.box, 0.05, inputs.SEED_BASE + 313)
+            f = load(md, a, pos, s.vel)
+            idx = sample_ids(a.n, 400, inputs.SEED_BASE + 303)
+            if variant == "half_atomic":
+                # a half list exports the pairs it owns; the full rows come from the oracle
+                ooff, oids = orc.neighbors_sample(pos, s.box, p["rc"] + p["skin"], idx)
+            else:
+                ooff, oids = check_rows(orc, a, pos, s.box, p["rc"] + p["skin"], idx)
+    check_forces(orc, prm, f, pos, s.box, idx, ooff, oids, p["rc"], 2e-4, 1e-5)
