@@ -234,6 +234,31 @@ def test_orthorhombic_box(md, orc, precision, variant):
     assert abs(ke + pe - E) <= tol * abs(E), (ke + pe, E)
 
 
+@pytest.mark.parametrize("variant", ["paired", "cluster"])
+def test_orthorhombic_box_clustered_layouts(md, orc, variant):
+    """The two clustered layouts (mixed path only) on the 3 x 4 x 6-cell
+    orthorhombic box: exported rows bit-exact, forces within the mixed bars,
+    and 60 steps with rebuilds against the oracle's total energy."""
+    pos, vel, box = orthorhombic()
+    code = {"paired": md.MD_FORCE_PAIRED, "cluster": md.MD_FORCE_CLUSTER}[variant]
+    with md.System(pos, vel, box, precision="mixed", force_variant=code) as a:
+        off, ids = a.neighbors()
+        f = a.state()[2].cpu().numpy()
+        b0 = a.stats()["builds"]
+        a.step(60)
+        builds = a.stats()["builds"] - b0
+        ke, pe = a.energy()
+    ooff, oids = orc.neighbors_cells(pos, box, 2.8)
+    np.testing.assert_array_equal(off.cpu().numpy(), ooff)
+    np.testing.assert_array_equal(ids.cpu().numpy(), oids)
+    prm = orc.make_params(potential=orc.POT_LJ, rc=2.5, skin=0.3, dt=0.005)
+    _, f0 = orc.forces_once(prm, pos, box)
+    check_forces(f, f0, "mixed", near_cutoff(pos, box, ooff, oids, 2.5, 1e-5))
+    assert builds >= 1
+    E = orc.md_run(prm, pos, vel, box, 60)["energies"][-1, 2]
+    assert abs(ke + pe - E) <= 1e-4 * abs(E), (ke + pe, E)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_sutton_chen_orthorhombic_box(md, orc, precision):
     """Sutton-Chen on a 7 x 8 x 9 fcc block (3 x 3 x 4 cells): densities and
