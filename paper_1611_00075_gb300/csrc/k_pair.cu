@@ -22,7 +22,8 @@
 // r_list -- and so, by the half-skin rule, every pair within r_c until the
 // next rebuild.  The force pass evaluates the slot's own pair once
 // (f_i0 += F, f_i1 -= F), then both atoms against each list entry in
-// float32, with the per-atom kernel's velocity-Verlet epilogue.  Each atom's
+// float32 -- packed: one f32x2 instruction serves the two atoms -- with the
+// per-atom kernel's velocity-Verlet epilogue.  Each atom's
 // force is summed in float32 over the whole list (about 55 entries per atom
 // at rho* = 0.8442, so one chunk of the per-atom kernel's float32-then-
 // float64 sums) and converted once: without the float64 accumulators the
@@ -201,6 +202,33 @@ __device__ __forceinline__ void pair_atom_out(const ForceArgs &a, int i, double 
     if (MODE != FM_STORE) vv_epilogue<MODE>(a, i, Fx, Fy, Fz, qw);
 }
 
+// Packed float32 pairs (add/mul/fma.rn.f32x2, sm_100 and later): lane .x
+// carries the slot's first atom, .y its second, so each instruction of the
+// pair arithmetic serves both atoms.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
 template <int MODE, bool ENERGY>
 __device__ __forceinline__ void lj_pair_slot(const ForceArgs &a, const PairArgs &p,
                                              const ShiftTab *sh, int s, int store_f) {
@@ -211,37 +239,57 @@ __device__ __forceinline__ void lj_pair_slot(const ForceArgs &a, const PairArgs 
     // a one-atom slot puts its second atom at the dummy's distance
     const float4 q1 = two ? a.xq[i0 + 1] : make_float4(3.0e18f, 3.0e18f, 3.0e18f, 0.f);
     const float rc2 = a.fc.rc2f;
-    float f0x = 0.f, f0y = 0.f, f0z = 0.f, f1x = 0.f, f1y = 0.f, f1z = 0.f, e0 = 0.f, e1 = 0.f;
+    float2 fx = dup2(0.f), fy = dup2(0.f), fz = dup2(0.f), en = dup2(0.f);
     unsigned np0 = 0, np1 = 0;
     {
         // the slot's own pair, once: f_i0 -= fs e, f_i1 += fs e
         const float ex = q1.x - q0.x, ey = q1.y - q0.y, ez = q1.z - q0.z;
         const float r2 = ex * ex + ey * ey + ez * ez;
         if (r2 < rc2) {
-            float gx = 0.f, gy = 0.f, gz = 0.f, en = 0.f;
+            float gx = 0.f, gy = 0.f, gz = 0.f, e = 0.f;
             unsigned k = 0;
-            lj_term<ENERGY>(a.fc, ex, ey, ez, r2, gx, gy, gz, en, k);
-            f0x = gx; f0y = gy; f0z = gz;
-            f1x = -gx; f1y = -gy; f1z = -gz;
+            lj_term<ENERGY>(a.fc, ex, ey, ez, r2, gx, gy, gz, e, k);
+            fx = make_float2(gx, -gx);
+            fy = make_float2(gy, -gy);
+            fz = make_float2(gz, -gz);
             if (ENERGY) {
-                e0 = e1 = en;
+                en = dup2(e);
                 np0 = np1 = 1;
             }
         }
     }
+    // the slot's atoms negated, in the two lanes of each pair
+    const float2 nqx = make_float2(-q0.x, -q1.x), nqy = make_float2(-q0.y, -q1.y),
+                 nqz = make_float2(-q0.z, -q1.z);
     const int nq = (min(p.count[s], p.cap) + 3) >> 2;
     const uint4 *lq = reinterpret_cast<const uint4 *>(p.list + list_group(s, p.cap)) + (s & 31);
-    // one gather and one stencil shift per entry, two pair evaluations
+    // one gather and one stencil shift per entry, both atoms' pair terms in
+    // packed instructions; -fs = r2i s6 (e48 / 2 - e48 s6) is added with one fma
     auto pair = [&](uint32_t ent) {
         const float4 qj = __ldg(a.xq + (ent & kIndexMask));
         const uint32_t st = ent >> kIndexBits;
         const float tx = qj.x + sh->x[st], ty = qj.y + sh->y[st], tz = qj.z + sh->z[st];
-        const float ax = tx - q0.x, ay = ty - q0.y, az = tz - q0.z;
-        const float ra = ax * ax + ay * ay + az * az;
-        if (ra < rc2) lj_term<ENERGY>(a.fc, ax, ay, az, ra, f0x, f0y, f0z, e0, np0);
-        const float bx = tx - q1.x, by = ty - q1.y, bz = tz - q1.z;
-        const float rb = bx * bx + by * by + bz * bz;
-        if (rb < rc2) lj_term<ENERGY>(a.fc, bx, by, bz, rb, f1x, f1y, f1z, e1, np1);
+        const float2 dx = add2(dup2(tx), nqx), dy = add2(dup2(ty), nqy), dz = add2(dup2(tz), nqz);
+        const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        const float2 r2i = make_float2(__fdividef(1.0f, r2.x), __fdividef(1.0f, r2.y));
+        const float2 s2 = mul2(dup2(a.fc.sig2f), r2i);
+        const float2 s6 = mul2(mul2(s2, s2), s2);
+        float2 nfs = mul2(mul2(fma2(s6, dup2(-a.fc.eps48f), dup2(0.5f * a.fc.eps48f)), s6), r2i);
+        const bool in0 = r2.x < rc2, in1 = r2.y < rc2;
+        nfs.x = in0 ? nfs.x : 0.f;
+        nfs.y = in1 ? nfs.y : 0.f;
+        fx = fma2(nfs, dx, fx);
+        fy = fma2(nfs, dy, fy);
+        fz = fma2(nfs, dz, fz);
+        if (ENERGY) {
+            float2 u = add2(mul2(fma2(s6, dup2(a.fc.eps4f), dup2(-a.fc.eps4f)), s6),
+                            dup2(-a.fc.shiftf));
+            u.x = in0 ? u.x : 0.f;
+            u.y = in1 ? u.y : 0.f;
+            en = add2(en, u);
+            np0 += in0 ? 1u : 0u;
+            np1 += in1 ? 1u : 0u;
+        }
     };
     uint4 nxt = nq > 0 ? __ldcs(lq) : make_uint4(0u, 0u, 0u, 0u);
     for (int q = 0; q < nq; ++q) {
@@ -252,20 +300,18 @@ __device__ __forceinline__ void lj_pair_slot(const ForceArgs &a, const PairArgs 
         pair(e4.z);
         pair(e4.w);
     }
-    const double F0x = f0x, F0y = f0y, F0z = f0z, F1x = f1x, F1y = f1y, F1z = f1z;
-    const double E0 = e0, E1 = e1;
-    pair_atom_out<MODE, ENERGY>(a, i0, F0x, F0y, F0z, E0, np0, q0.w, store_f);
-    if (two) pair_atom_out<MODE, ENERGY>(a, i0 + 1, F1x, F1y, F1z, E1, np1, q1.w, store_f);
+    pair_atom_out<MODE, ENERGY>(a, i0, fx.x, fy.x, fz.x, en.x, np0, q0.w, store_f);
+    if (two) pair_atom_out<MODE, ENERGY>(a, i0 + 1, fx.y, fy.y, fz.y, en.y, np1, q1.w, store_f);
 }
 
-// Measured on GB300 (porous LJ, 9.8 M atoms, one force launch, from the
-// generated state): this form at 56 registers (9 CTAs per SM) 1.387 ms; with
-// float64 chunk accumulators at 72 registers (7 CTAs) 1.498 ms, and with
-// packed float32 pair arithmetic (add/mul/fma.rn.f32x2, both atoms in one
-// instruction) on top 1.551 ms; the per-atom kernel 1.308 ms.  The slot
-// lists hold 0.68 times the per-atom entries and the kernel issues fewer
-// instructions and L1 wavefronts, but fewer of its lanes stay active (a
-// warp's 64 atoms span more cells, whose list lengths differ).
+// Measured on GB300 (porous LJ, 9.8 M atoms, one force launch): this form
+// (packed pairs, float32 sums, 56 registers, 9 CTAs per SM) 1.232 ms against
+// 1.304 ms for the per-atom kernel from the generated state, 1.342 against
+// 1.440 ms on the equilibrated one; the same arithmetic unpacked 1.387 ms
+// (issue-bound: the second atom's pair terms cost as many instructions as
+// the first's); with float64 chunk accumulators at 72 registers (7 CTAs)
+// 1.498 ms unpacked and 1.551 ms packed (latency-bound).  At 1 M atoms the
+// two layouts tie (porous) or the per-atom kernel leads by 2 % (liquid).
 template <int MODE, bool ENERGY>
 __global__ void __launch_bounds__(kPairBlock, 9) lj_pair_kernel(ForceArgs a, PairArgs p,
                                                                 int store_f) {
