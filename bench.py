@@ -42,7 +42,8 @@ POROUS_DESC = ("porous Lennard-Jones solid: 160^3 fcc cells = 16,384,000 sites a
 # of a smaller porous case (profiles/); the figure is used only while the
 # kernel sources still hash to the captured version.
 FORCE_SOURCES = ("paper_1611_00075_gb300/csrc/k_lj.cu", "paper_1611_00075_gb300/csrc/k_common.cuh",
-                 "paper_1611_00075_gb300/csrc/md_internal.cuh")
+                 "paper_1611_00075_gb300/csrc/md_internal.cuh",
+                 "paper_1611_00075_gb300/csrc/k_pair.cuh")
 PROFILED_TRAFFIC = {
     # kernel: (sources sha1[:16], DRAM bytes per atom, capture)
     "lj_mixed_persist": ("bfa90097e980e658", 482.6,
@@ -82,6 +83,9 @@ def parse_args(argv):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nc", type=int, default=0,
                     help="fcc cells per side (0 = the workload's own size; smaller for profiling)")
+    ap.add_argument("--force-variant", default="paired", choices=["paired", "full"],
+                    help="force layout of the timed Lennard-Jones steps: two atoms per "
+                         "thread (union lists) or one atom per thread (per-atom lists)")
     ap.add_argument("--no-equilibrate", dest="equilibrate", action="store_false",
                     help="porous: time from the generated state instead of the equilibrated one")
     return ap.parse_args(argv)
@@ -278,6 +282,11 @@ def run_gpu(args, rank, world, local):
         args.scheduler = "grid"  # the persistent schedulers drive the Lennard-Jones kernel
     sched = {"grid": md.MD_SCHED_GRID, "paircount": md.MD_SCHED_PAIRCOUNT,
              "mlp": md.MD_SCHED_MLP, "dynamic": md.MD_SCHED_DYNAMIC}[args.scheduler]
+    # the two-atom layout serves one-species Lennard-Jones of one box
+    paired = (args.force_variant == "paired" and kw["potential"] == "lj" and
+              "species" not in kw and not ensemble)
+    fv = md.MD_FORCE_PAIRED if paired else md.MD_FORCE_FULL
+    kw["force_variant"] = fv
 
     def barrier():
         rank_barrier(world)
@@ -371,7 +380,7 @@ def run_gpu(args, rank, world, local):
             # the learned part first: per-cell clock64 timings of this state,
             # then the network trained on the GPU
             if args.scheduler == "mlp" or args.compare_steps > 0:
-                md.md_set_variant(mixed.h, md.MD_FORCE_FULL, md.MD_SCHED_DYNAMIC)
+                md.md_set_variant(mixed.h, fv, md.MD_SCHED_DYNAMIC)
                 t0 = time.perf_counter()
                 nsamp = md.md_cost_model(mixed.h, md.MD_COST_SAMPLE)
                 loss = md.md_cost_model(mixed.h, md.MD_COST_TRAIN)
@@ -392,7 +401,7 @@ def run_gpu(args, rank, world, local):
             if args.compare_steps > 0:
                 for name, code in (("grid", md.MD_SCHED_GRID), ("paircount", md.MD_SCHED_PAIRCOUNT),
                                    ("dynamic", md.MD_SCHED_DYNAMIC), ("mlp", md.MD_SCHED_MLP)):
-                    from_s0(md.MD_FORCE_FULL, code)
+                    from_s0(fv, code)
                     msx, stx = timed(mixed, args.compare_steps)
                     sched_info[name] = {
                         "atom_steps_per_s": n_of(mixed) * args.compare_steps / (msx * 1e-3),
@@ -402,7 +411,7 @@ def run_gpu(args, rank, world, local):
                 # the same static partitions with no dynamically claimed tail:
                 # the cost estimate alone balances the CTAs
                 for name, code in (("paircount", md.MD_SCHED_PAIRCOUNT), ("mlp", md.MD_SCHED_MLP)):
-                    from_s0(md.MD_FORCE_FULL, code)
+                    from_s0(fv, code)
                     md.md_set_schedule(mixed.h, 0, 0)
                     msx, stx = timed(mixed, args.compare_steps)
                     sched_info[name + "_static"] = {
@@ -413,10 +422,11 @@ def run_gpu(args, rank, world, local):
                     md.md_set_schedule(mixed.h, 0, 20)
                 # the Newton's-third-law variants (half lists) against the full list
                 variants = {}
-                for name, code in (("half_color", md.MD_FORCE_HALF_COLOR),
+                for name, code in (("full", md.MD_FORCE_FULL),
+                                   ("paired", md.MD_FORCE_PAIRED),
+                                   ("half_color", md.MD_FORCE_HALF_COLOR),
                                    ("half_atomic", md.MD_FORCE_HALF_ATOMIC),
-                                   ("cluster_pairs", md.MD_FORCE_CLUSTER),
-                                   ("paired", md.MD_FORCE_PAIRED)):
+                                   ("cluster_pairs", md.MD_FORCE_CLUSTER)):
                     from_s0(code, md.MD_SCHED_GRID)
                     msx, stx = timed(mixed, args.compare_steps)
                     variants[name] = {
@@ -428,9 +438,9 @@ def run_gpu(args, rank, world, local):
                         variants[name]["pair_slots_per_atom"] = 32.0 * stx["cluster_pairs"] / n_of(mixed)
                     if code == md.MD_FORCE_PAIRED:
                         variants[name]["slot_entries_per_atom"] = stx["slot_entries"] / n_of(mixed)
+                    if code == md.MD_FORCE_FULL:
                         variants[name]["list_entries_per_atom"] = stx["list_entries"] / n_of(mixed)
-                variants["full"] = {"atom_steps_per_s": sched_info["grid"]["atom_steps_per_s"],
-                                    "force_ms_per_launch": sched_info["grid"]["force_ms_per_launch"]}
+                variants["note"] = "every layout under the hardware block scheduler"
                 sched_info["force_variants"] = variants
                 # the inner/outer split of Sec. 2.1 (virtual domains, boundary
                 # positions exchanged on a second stream) against the fused pass
@@ -444,9 +454,9 @@ def run_gpu(args, rank, world, local):
                         "force_ms_per_launch": stx["ms"]["force"] / max(1, stx["count"]["force"])}
                     md.md_set_decomposition(mixed.h, 1, 1, 1)
                 sched_info["inner_outer_split"] = split
-            from_s0(md.MD_FORCE_FULL, sched)
+            from_s0(fv, sched)
         else:
-            md.md_set_variant(mixed.h, md.MD_FORCE_FULL, sched)
+            md.md_set_variant(mixed.h, fv, sched)
         builds0 = json.loads(md.md_stats(mixed.h))["builds"]
         sampler.start()
         # batches of small replicas are launch-bound: their timed region replays
@@ -473,9 +483,10 @@ def run_gpu(args, rank, world, local):
         fp64 = None
         if args.fp64_steps > 0:
             sched64 = "paircount" if (kw["potential"] == "lj" and "species" not in kw) else "grid"
+            kw64 = dict(kw, force_variant=md.MD_FORCE_FULL)  # the plain method: per-atom lists
             plain = md.System(s.pos, s.vel, s.box, precision="fp64", stream=stream,
                               scheduler=md.MD_SCHED_PAIRCOUNT if sched64 == "paircount"
-                              else md.MD_SCHED_GRID, **kw)
+                              else md.MD_SCHED_GRID, **kw64)
             md.md_step(plain.h, min(args.warmup, 3))
             ms64, st64 = timed(plain, args.fp64_steps)
             ms64 = max_over_ranks(ms64)
@@ -536,7 +547,14 @@ def run_gpu(args, rank, world, local):
     t_force = st["ms"]["force"] / n_force * 1e-3
     entries = st_e["list_entries"]
     pairs = st_e["pairs_cut"]
-    if kw["potential"] == "lj":
+    if kw["potential"] == "lj" and kw.get("force_variant") == md.MD_FORCE_PAIRED:
+        # two atoms per thread: 12 flops per evaluated (atom, entry) and 14 per
+        # pair inside r_c; 168 B of state per atom, 8 B per slot (its first
+        # atom and list length) and 4 B per union-list entry
+        entries = st_e["slot_entries"]
+        flops = 12.0 * 2 * entries + 14.0 * pairs
+        bytes_ = 168.0 * n + 8.0 * st_e["slots"] + 4.0 * entries
+    elif kw["potential"] == "lj":
         flops = 12.0 * entries + 14.0 * pairs
         bytes_ = 168.0 * n + 4.0 * entries
     elif kw["potential"] == "eam":
@@ -550,8 +568,8 @@ def run_gpu(args, rank, world, local):
         flops = 2 * (12.0 * entries) + 10.0 * pairs + 26.0 * pairs
         bytes_ = 2 * 4.0 * entries + 250.0 * n
     traffic, traffic_note = None, "no capture of this kernel version"
-    kname = ("lj_mixed_persist" if (kw["potential"] == "lj" and args.scheduler != "grid"
-                                    and not ensemble) else None)
+    kname = (("lj_mixed_persist_paired" if paired else "lj_mixed_persist")
+             if (kw["potential"] == "lj" and args.scheduler != "grid" and not ensemble) else None)
     if kname in PROFILED_TRAFFIC and PROFILED_TRAFFIC[kname][0] == sources_sha1():
         traffic = PROFILED_TRAFFIC[kname][1] * n
         traffic_note = PROFILED_TRAFFIC[kname][2] + ", scaled by atoms"
@@ -572,8 +590,11 @@ def run_gpu(args, rank, world, local):
             "traffic": traffic,
             "traffic_note": traffic_note,
             "kernel": ("lj_typed_kernel<FM_FUSED_FULL>" if "species" in kw else
-                       "lj_mixed_persist<FM_FUSED_FULL> (%s)" % args.scheduler if args.scheduler != "grid"
-                       else "lj_mixed_kernel<FM_FUSED_FULL>") if kw["potential"] == "lj" else
+                       ("lj_mixed_persist<FM_FUSED_FULL, two-atom slots> (%s)" if paired else
+                        "lj_mixed_persist<FM_FUSED_FULL> (%s)") % args.scheduler
+                       if args.scheduler != "grid" else
+                       ("lj_pair_kernel<FM_FUSED_FULL>" if paired else
+                        "lj_mixed_kernel<FM_FUSED_FULL>")) if kw["potential"] == "lj" else
                       ("eam_force_mixed" if kw["potential"] == "eam" else "sc_force_mixed"),
             "multi_box": ensemble,
             "peak_source": peak_src,
@@ -588,7 +609,7 @@ def run_gpu(args, rank, world, local):
         k = int(np.argmax([r.n for r in reps]))
         a0 = sum(r.n for r in reps[:k])
         pos, force, box, n_chk = pos[a0:a0 + reps[k].n], force[a0:a0 + reps[k].n], reps[k].box, reps[k].n
-    return dict(n=n, value=value, ms=ms, st=st, st_e=st_e, fp64=fp64, e2e=e2e, roof=roof,
+    return dict(n=n, value=value, ms=ms, st=st, st_e=st_e, fp64=fp64, e2e=e2e, roof=roof, paired=paired,
                 clk=clk, desc=desc, pos=pos, force=force, n_check=n_chk,
                 box=box, params=s.params, ke=ke, pe=pe, builds_timed=builds_timed,
                 sched_info=sched_info)
@@ -826,9 +847,12 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair terms / f64 state",
         "data": "synthetic",
         "config": {"workload": g["desc"], "atoms": g["n"], "precision": "mixed",
-                   "force_variant": "full list", "scheduler": args.scheduler,
+                   "force_variant": ("two atoms per thread, union lists"
+                                     if g["paired"] else "one atom per thread, per-atom lists"),
+                   "scheduler": args.scheduler,
                    "l2": "inputs larger than L2 (%.1f GB resident state + list)"
-                         % ((g["n"] * 300 + g["st_e"]["list_entries"] * 4) / 1e9),
+                         % ((g["n"] * 300 + 4 * (g["st_e"]["slot_entries"] if g["paired"]
+                                                  else g["st_e"]["list_entries"])) / 1e9),
                    "list_builds_in_timed_steps": g["builds_timed"],
                    "start_state": start_state(g["sched_info"])},
         "fp64_baseline": g["fp64"],

@@ -65,10 +65,12 @@ enum { MD_FP64 = 0, MD_MIXED = 1 };
  * grouping atoms saves neighbour loads): each thread owns two consecutive
  * atoms of one cell and walks the union of their lists, so that one gathered
  * neighbour position serves two pair evaluations.  The full pair set, the
- * same forces as MD_FORCE_FULL up to float32 rounding; the per-atom list is
- * still built (for md_get_neighbors).  Mixed-precision one-species
- * Lennard-Jones of one box under MD_SCHED_GRID.  Both are measured
- * alternatives: on GB300 the per-atom full list is faster. */
+ * same forces as MD_FORCE_FULL up to float32 rounding.  Its rebuilds make the
+ * slot lists only; md_get_neighbors builds per-atom rows on demand from the
+ * positions of the last build.  Mixed-precision one-species Lennard-Jones
+ * of one box, under any scheduler (the persistent kernel then takes tiles of
+ * 32 slots).  MD_FORCE_CLUSTER is a measured alternative (slower on GB300);
+ * MD_FORCE_PAIRED is faster than the per-atom list on large systems. */
 enum { MD_FORCE_FULL = 0, MD_FORCE_HALF_COLOR = 1, MD_FORCE_HALF_ATOMIC = 2,
        MD_FORCE_CLUSTER = 3, MD_FORCE_PAIRED = 4 };
 /* How force work is spread over the SMs.  The static schedulers cut the
@@ -278,7 +280,8 @@ md_status md_get_atom_energy(md_system *h, double *e_dev);
  * by the lower original id) are built for one-species Lennard-Jones on
  * either path; the cluster and two-atom layouts for its mixed path; the
  * persistent schedulers drive the full-list Lennard-Jones pass of either
- * precision, and every other combination runs one thread per atom. */
+ * precision and the two-atom pass, and every other combination runs one
+ * thread per atom (per slot, per i-cluster). */
 md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler);
 
 /* Colour of every cell of an ncell_host[0] x [1] x [2] grid (each >= 3) as

@@ -26,7 +26,7 @@
 // buffer of a double-buffered pair; FM_FUSED_HALF applies the closing half
 // kick (v += dt f / 2m).  The drift also measures the displacement since the
 // last list build and raises the rebuild flag past half the skin (Sec. 3.3).
-#include "k_common.cuh"
+#include "k_pair.cuh"
 
 namespace mdg {
 
@@ -233,17 +233,24 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 }
 
 // F64: the same scheduling of the plain float64 per-atom job (the baseline
-// the mixed path is measured against).
+// the mixed path is measured against).  PAIRED: the items are the two-atom
+// slots of MD_FORCE_PAIRED (tiles of 32 slots; sa.cell_start then holds the
+// first slot of every cell) and each runs the slot job of k_pair.cuh.
 // CTAs of 128 threads at up to 56 registers (9 per SM) were measured fastest:
 // 1.359 ms against 1.395 ms for 256 threads at 48 registers on the 9.8 M-atom
 // porous system.
 constexpr int kPersistBlock = 128;
+// The slot job holds twice the accumulators: its persistent kernel gets up to
+// 64 registers (8 CTAs per SM) instead of spilling at 56.
+constexpr int kPersistPairedCtas = 8;
 
-template <int MODE, bool ENERGY, bool DYNAMIC, bool TIMING, bool MULTI = false, bool F64 = false>
-__global__ void __launch_bounds__(kPersistBlock, F64 ? 8 : 9)
-lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
+template <int MODE, bool ENERGY, bool DYNAMIC, bool TIMING, bool MULTI = false, bool F64 = false,
+          bool PAIRED = false>
+__global__ void __launch_bounds__(kPersistBlock, F64 ? 8 : (PAIRED ? kPersistPairedCtas : 9))
+lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa, PairArgs pa) {
     static_assert(kSchedRounds <= 8, "per-CTA range table holds 8 rounds");
     static_assert(!(F64 && MULTI), "batches run the mixed path");
+    static_assert(!(PAIRED && (F64 || MULTI || ENERGY)), "slots: one box, mixed path, forces");
     __shared__ ShiftTab sh;
     __shared__ double3 sh64[F64 ? kStencil : 1];
     __shared__ int s_first[8], s_pre[9], s_next;  // this CTA's ranges (static mode)
@@ -257,7 +264,8 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
     if (s_stop != 0) return;
     step_bookkeeping<MODE>(a);
     const int lane = threadIdx.x & 31;
-    const int ntiles = (a.n + 31) >> 5;
+    const int nitems = PAIRED ? pa.slot_start[pa.ncells] : a.n;
+    const int ntiles = (nitems + 31) >> 5;
     long long cta_t0 = 0;
     if (TIMING) cta_t0 = clock64();
     int nlocal = 0;       // static mode: tiles of all this CTA's ranges
@@ -319,29 +327,39 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa) {
         const int tn = claim();
         if (tn >= 0) {
             const int in = (tn << 5) + lane;
-            if (in < a.n) {
-                prefetch_l2(a.nlist + list_group(in, a.cap) + ((in & 31) << 2));
-                if (F64) prefetch_l2(a.xr + in);
-                else prefetch_l2(a.xq + in);
-                prefetch_l2(a.ncount + in);
+            if (in < nitems) {
+                if (PAIRED) {
+                    prefetch_l2(pa.list + list_group(in, pa.cap) + ((in & 31) << 2));
+                    prefetch_l2(pa.slot_atom + in);
+                    prefetch_l2(pa.count + in);
+                } else {
+                    prefetch_l2(a.nlist + list_group(in, a.cap) + ((in & 31) << 2));
+                    if (F64) prefetch_l2(a.xr + in);
+                    else prefetch_l2(a.xq + in);
+                    prefetch_l2(a.ncount + in);
+                }
             }
         }
         const int i = (t << 5) + lane;
-        const bool active = i < a.n;
+        const bool active = i < nitems;
         long long t0 = 0;
         if (TIMING) {
             __syncwarp();
             t0 = clock64();
         }
         if (active) {
-            if (F64) lj_fp64_atom<MODE, ENERGY>(a, sh64, i, store_f);
+            if (PAIRED) lj_pair_slot<MODE, false>(a, pa, &sh, i, store_f);
+            else if (F64) lj_fp64_atom<MODE, ENERGY>(a, sh64, i, store_f);
             else lj_mixed_atom<MODE, ENERGY, MULTI>(a, &sh, i, store_f);
         }
         if (TIMING) {
             __syncwarp();
             const long long dt = clock64() - t0;
             const unsigned act = __ballot_sync(0xffffffffu, active);
-            if (active) atomicAdd(&sa.cell_cycles[sa.cell[i]], (float)dt / (float)__popc(act));
+            if (active) {
+                const int c = PAIRED ? sa.cell[pa.slot_atom[i] & ~kSingle] : sa.cell[i];
+                atomicAdd(&sa.cell_cycles[c], (float)dt / (float)__popc(act));
+            }
         }
         t = tn;
     }
@@ -654,11 +672,14 @@ cudaError_t launch_lj(md_system *h, int mode, bool energy, bool store_f) {
 
 namespace mdg {
 
-int persist_ctas_per_sm(bool f64) {
+int persist_ctas_per_sm(bool f64, bool paired) {
     int nb = 0;
     const cudaError_t e =
         f64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                   &nb, lj_mixed_persist<FM_FUSED_FULL, false, false, false, false, true>, kPersistBlock, 0)
+        : paired ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &nb, lj_mixed_persist<FM_FUSED_FULL, false, false, false, false, false, true>,
+                  kPersistBlock, 0)
             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                   &nb, lj_mixed_persist<FM_FUSED_FULL, false, false, false>, kPersistBlock, 0);
     if (e != cudaSuccess) nb = 1;
@@ -667,13 +688,23 @@ int persist_ctas_per_sm(bool f64) {
 
 cudaError_t launch_lj_persist(md_system *h, int mode, bool store_f, bool dynamic, bool timing) {
     ForceArgs a = make_force_args(h);
+    const bool paired = (h->p.force_variant == MD_FORCE_PAIRED);
     SchedArgs sa;
-    sa.cell_start = h->cell_start;
+    sa.cell_start = paired ? h->ps_start : h->cell_start;
     sa.bounds = h->part_bounds;
     sa.cell = h->cell;
     sa.cell_cycles = h->cell_cycles;
     sa.cta_cycles = h->cta_cycles;
     sa.rounds = h->sched_rounds;
+    PairArgs pa{};
+    if (paired) {
+        pa.slot_start = h->ps_start;
+        pa.slot_atom = h->ps_atom;
+        pa.list = h->ps_list;
+        pa.count = h->ps_count;
+        pa.cap = h->ps_cap;
+        pa.ncells = h->g.ncells;
+    }
     const int G = h->sched_ctas;
     const int sf = store_f ? 1 : 0;
     cudaStream_t s = h->stream;
@@ -681,34 +712,44 @@ cudaError_t launch_lj_persist(md_system *h, int mode, bool store_f, bool dynamic
         // several boxes: the tile queue (the static partitions are single-box)
         switch (mode) {
             case FM_STORE:
-                lj_mixed_persist<FM_STORE, false, true, false, true><<<G, kPersistBlock, 0, s>>>(a, sf, sa);
+                lj_mixed_persist<FM_STORE, false, true, false, true><<<G, kPersistBlock, 0, s>>>(a, sf, sa, pa);
                 break;
             case FM_FUSED_FULL:
-                lj_mixed_persist<FM_FUSED_FULL, false, true, false, true><<<G, kPersistBlock, 0, s>>>(a, sf, sa);
+                lj_mixed_persist<FM_FUSED_FULL, false, true, false, true><<<G, kPersistBlock, 0, s>>>(a, sf, sa, pa);
                 break;
             default:
-                lj_mixed_persist<FM_FUSED_HALF, false, true, false, true><<<G, kPersistBlock, 0, s>>>(a, sf, sa);
+                lj_mixed_persist<FM_FUSED_HALF, false, true, false, true><<<G, kPersistBlock, 0, s>>>(a, sf, sa, pa);
                 break;
         }
         return cudaGetLastError();
     }
     if (timing) {
-        if (dynamic) lj_mixed_persist<FM_STORE, false, true, true><<<G, kPersistBlock, 0, s>>>(a, 1, sa);
-        else lj_mixed_persist<FM_STORE, false, false, true><<<G, kPersistBlock, 0, s>>>(a, 1, sa);
+        if (paired) {
+            if (dynamic) lj_mixed_persist<FM_STORE, false, true, true, false, false, true><<<G, kPersistBlock, 0, s>>>(a, 1, sa, pa);
+            else lj_mixed_persist<FM_STORE, false, false, true, false, false, true><<<G, kPersistBlock, 0, s>>>(a, 1, sa, pa);
+        } else {
+            if (dynamic) lj_mixed_persist<FM_STORE, false, true, true><<<G, kPersistBlock, 0, s>>>(a, 1, sa, pa);
+            else lj_mixed_persist<FM_STORE, false, false, true><<<G, kPersistBlock, 0, s>>>(a, 1, sa, pa);
+        }
         return cudaGetLastError();
     }
     const bool f64 = (h->p.precision == MD_FP64);
 #define MDG_P(M)                                                                               \
     do {                                                                                       \
-        if (f64) {                                                                             \
+        if (paired) {                                                                          \
             if (dynamic)                                                                       \
-                lj_mixed_persist<M, false, true, false, false, true><<<G, kPersistBlock, 0, s>>>(a, sf, sa);  \
+                lj_mixed_persist<M, false, true, false, false, false, true><<<G, kPersistBlock, 0, s>>>(a, sf, sa, pa);  \
             else                                                                               \
-                lj_mixed_persist<M, false, false, false, false, true><<<G, kPersistBlock, 0, s>>>(a, sf, sa); \
+                lj_mixed_persist<M, false, false, false, false, false, true><<<G, kPersistBlock, 0, s>>>(a, sf, sa, pa); \
+        } else if (f64) {                                                                      \
+            if (dynamic)                                                                       \
+                lj_mixed_persist<M, false, true, false, false, true><<<G, kPersistBlock, 0, s>>>(a, sf, sa, pa);  \
+            else                                                                               \
+                lj_mixed_persist<M, false, false, false, false, true><<<G, kPersistBlock, 0, s>>>(a, sf, sa, pa); \
         } else if (dynamic) {                                                                  \
-            lj_mixed_persist<M, false, true, false><<<G, kPersistBlock, 0, s>>>(a, sf, sa);            \
+            lj_mixed_persist<M, false, true, false><<<G, kPersistBlock, 0, s>>>(a, sf, sa, pa);            \
         } else {                                                                               \
-            lj_mixed_persist<M, false, false, false><<<G, kPersistBlock, 0, s>>>(a, sf, sa);           \
+            lj_mixed_persist<M, false, false, false><<<G, kPersistBlock, 0, s>>>(a, sf, sa, pa);           \
         }                                                                                      \
     } while (0)
     switch (mode) {

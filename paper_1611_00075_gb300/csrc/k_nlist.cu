@@ -312,16 +312,16 @@ __global__ void export_fill_kernel(int n, int cap, int half, const int32_t *__re
 
 }  // namespace
 
-cudaError_t launch_build_list(md_system *h, bool write, bool gated) {
+cudaError_t launch_build_list(md_system *h, bool write, bool gated, const float4 *positions) {
     int n = (int)h->n;
     cudaStream_t s = h->stream;
-    int cur = h->cur;
+    const float4 *xq = positions ? positions : h->xq[h->cur];
     const bool prefilter = (h->p.precision == MD_MIXED);
     const bool half = half_variant(h->p.force_variant);
     reset_max_count_kernel<<<1, 1, 0, s>>>(h->ds, gated);
 #define MDG_LIST(PF, WR, HF)                                                                    \
     build_list_kernel<PF, WR, HF><<<gs_blocks(n) * (kBlock / kListBlock), kListBlock, 0, s>>>(                                \
-        n, h->grids, h->rep, h->list_lo, h->list_hi, h->rl2, h->xq[cur], h->xabs, h->cell,   \
+        n, h->grids, h->rep, h->list_lo, h->list_hi, h->rl2, xq, h->xabs, h->cell,           \
         h->cell_start,                                                                         \
         h->nlist, h->ncount, h->cap, h->ds, gated)
     if (prefilter) {

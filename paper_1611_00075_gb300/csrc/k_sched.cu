@@ -5,11 +5,12 @@
 // fluctuations unbalance static decompositions (Sec. 1).  Here the cells are
 // split into contiguous ranges of (predicted) equal cost, one range per
 // resident CTA, by one of two estimates:
-//   pair count  cost(c) = list entries of the atoms of c
+//   pair count  cost(c) = list entries of the atoms of c (of the two-atom
+//               slots of c under MD_FORCE_PAIRED: the work units there)
 //   learned     cost(c) = exp(10 y) - 1, y = MLP(features of c)
 // Features of cell c, scaled to O(1):
 //   x0 = log1p(atoms in c) / 3
-//   x1 = log1p(list entries of c's atoms) / 8
+//   x1 = log1p(list entries of c's atoms, or of its slots) / 8
 //   x2 = log1p(atoms in the 26 neighbour cells) / 6
 // Training targets come from the persistent kernel's clock64 timing:
 //   y = log1p(cycles of c) / 10.
@@ -27,15 +28,18 @@ __device__ __forceinline__ bool chain_off(const DevStatus *ds, bool gated) {
     return ds != nullptr && (ds->status != 0 || (gated && ds->rebuild == 0));
 }
 
+// start: first atom of every cell; item_start / item_count: the force pass's
+// work units (atoms, or two-atom slots) of every cell and their list lengths
 __global__ void cell_features_kernel(int ncells, Grid g, const int32_t *__restrict__ start,
-                                     const int32_t *__restrict__ ncount, int cap,
+                                     const int32_t *__restrict__ item_start,
+                                     const int32_t *__restrict__ item_count, int cap,
                                      float *__restrict__ X, long long *__restrict__ paircost,
                                      const DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
     const int b = start[c], e = start[c + 1];
     long long np = 0;
-    for (int i = b; i < e; ++i) np += min(ncount[i], cap);
+    for (int i = item_start[c]; i < item_start[c + 1]; ++i) np += min(item_count[i], cap);
     const int cx = c % g.nx, cy = (c / g.nx) % g.ny, cz = c / (g.nx * g.ny);
     int occ = 0;
     for (int dz = -1; dz <= 1; ++dz)
@@ -94,9 +98,11 @@ __global__ void sample_scatter_kernel(int ncells, const int32_t *__restrict__ fl
 
 cudaError_t launch_cell_features(md_system *h, bool paircount, bool gated) {
     const int nc = h->g.ncells;
+    const bool slots = (h->p.force_variant == MD_FORCE_PAIRED);
     cell_features_kernel<<<gs_blocks(nc), kBlock, 0, h->stream>>>(
-        nc, h->g, h->cell_start, h->ncount, h->cap, h->cell_X, paircount ? h->cell_cost : nullptr,
-        h->ds, gated);
+        nc, h->g, h->cell_start, slots ? h->ps_start : h->cell_start,
+        slots ? h->ps_count : h->ncount, slots ? h->ps_cap : h->cap, h->cell_X,
+        paircount ? h->cell_cost : nullptr, h->ds, gated);
     return cudaGetLastError();
 }
 

@@ -255,12 +255,21 @@ void harvest(md_system *h) {
 // force pass; every other combination uses the one-thread-per-atom grid.
 bool persistent_path(const md_system *h) {
     return h->p.scheduler != MD_SCHED_GRID && h->p.potential == MD_POT_LJ &&
-           h->p.force_variant == MD_FORCE_FULL;
+           (h->p.force_variant == MD_FORCE_FULL || h->p.force_variant == MD_FORCE_PAIRED);
 }
 
 bool uses_partition(const md_system *h) {
     return persistent_path(h) &&
            (h->p.scheduler == MD_SCHED_PAIRCOUNT || h->p.scheduler == MD_SCHED_MLP);
+}
+
+// Resident CTAs and ranges per CTA of the persistent kernel of the current
+// force layout (the two-atom kernel runs fewer, larger CTAs per SM).
+void sched_shape(md_system *h) {
+    if (h->sched_sms <= 0) return;
+    const bool paired = (h->p.force_variant == MD_FORCE_PAIRED);
+    h->sched_ctas = h->sched_sms * persist_ctas_per_sm(h->p.precision == MD_FP64, paired);
+    h->sched_rounds = h->sched_rounds_set > 0 ? h->sched_rounds_set : sched_rounds(h->n, h->sched_ctas);
 }
 
 // Buffers of the scheduler and the cost model, allocated on first use.
@@ -270,7 +279,11 @@ md_status ensure_sched(md_system *h) {
     int dev = 0, sms = 0;
     MD_CK(cudaGetDevice(&dev));
     MD_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    h->sched_ctas = sms * persist_ctas_per_sm(h->p.precision == MD_FP64);
+    h->sched_sms = sms;
+    // buffers sized for the largest CTA count of any persistent kernel
+    const int ctas_max = sms * std::max(persist_ctas_per_sm(h->p.precision == MD_FP64, false),
+                                        persist_ctas_per_sm(false, true));
+    h->sched_ctas = ctas_max;
     const size_t C = (size_t)h->g.ncells;
     cudaError_t e = cudaSuccess;
     auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
@@ -282,7 +295,7 @@ md_status ensure_sched(md_system *h) {
     A(dalloc(&h->cell_X, 3 * C));
     A(dalloc(&h->cell_pred, C));
     A(dalloc(&h->cell_cycles, C));
-    A(dalloc(&h->cta_cycles, (size_t)h->sched_ctas));
+    A(dalloc(&h->cta_cycles, (size_t)ctas_max));
     A(dalloc(&h->samp_flag, 2 * (C + 1) + 2));  // flags, their scan, sample count
     A(dalloc(&h->samp_bsum, C / (kBlock * 8) + 8));
     A(dalloc(&h->samp_X, 3 * C));
@@ -296,6 +309,7 @@ md_status ensure_sched(md_system *h) {
     if (e != cudaSuccess)
         return fail(h, e == cudaErrorMemoryAllocation ? MD_ERR_OOM : MD_ERR_CUDA,
                     std::string("scheduler allocation: ") + cudaGetErrorString(e));
+    sched_shape(h);
     MD_CK(launch_mlp_init(h->mlp_P, 0x1611000075ull, h->stream));
     MD_CK(cudaMemsetAsync(h->mlp_m, 0, kMlpParams * sizeof(float), h->stream));
     MD_CK(cudaMemsetAsync(h->mlp_v, 0, kMlpParams * sizeof(float), h->stream));
@@ -321,8 +335,13 @@ md_status enqueue_sched_prep(md_system *h, bool gated) {
 // device flag asks for it.
 md_status enqueue_rebuild(md_system *h, bool gated) {
     MD_CK(launch_bin(h, gated));
-    MD_CK(launch_build_list(h, true, gated));
-    h->launches += kBinLaunches + 3;  // binning, list reset and build, finish
+    if (h->p.force_variant == MD_FORCE_PAIRED) {
+        MD_CK(launch_pair_build(h, true, gated));
+        h->launches += kBinLaunches + 8;  // binning, slot tables and lists, finish
+    } else {
+        MD_CK(launch_build_list(h, true, gated));
+        h->launches += kBinLaunches + 3;  // binning, list reset and build, finish
+    }
     if (h->ov_on) {
         MD_CK(launch_overlap_index(h, gated));
         h->launches += 5;
@@ -330,10 +349,6 @@ md_status enqueue_rebuild(md_system *h, bool gated) {
     if (h->p.force_variant == MD_FORCE_CLUSTER) {
         MD_CK(launch_cluster_build(h, gated));
         h->launches += 9;
-    }
-    if (h->p.force_variant == MD_FORCE_PAIRED) {
-        MD_CK(launch_pair_build(h, true, gated));
-        h->launches += 7;
     }
     md_status st = enqueue_sched_prep(h, gated);
     if (st != MD_OK) return st;
@@ -345,6 +360,18 @@ md_status enqueue_rebuild(md_system *h, bool gated) {
 // Host-driven rebuild with capacity repair (explicit calls and create).
 md_status rebuild_now(md_system *h, bool size_from_count) {
     MD_CK(launch_bin(h, false));
+    if (h->p.force_variant == MD_FORCE_PAIRED) {
+        // the slot lists carry the force pass; per-atom rows are built on
+        // demand for export (atom_list_for_export)
+        md_status st = pair_rebuild_now(h);
+        if (st != MD_OK) return st;
+        st = enqueue_sched_prep(h, false);
+        if (st != MD_OK) return st;
+        MD_CK(launch_finish_rebuild(h, false));
+        h->list_valid = true;
+        h->forces_valid = false;
+        return MD_OK;
+    }
     if (size_from_count || h->nlist == nullptr) {
         MD_CK(launch_build_list(h, false, false));
         md_status st = read_status(h);
@@ -379,15 +406,35 @@ md_status rebuild_now(md_system *h, bool size_from_count) {
         if (h->ds_host->status != 0)
             return fail(h, (md_status)h->ds_host->status, "device error during cluster build");
     }
-    if (h->p.force_variant == MD_FORCE_PAIRED) {
-        md_status st = pair_rebuild_now(h);
-        if (st != MD_OK) return st;
-    }
     md_status st = enqueue_sched_prep(h, false);
     if (st != MD_OK) return st;
     MD_CK(launch_finish_rebuild(h, false));
     h->list_valid = true;
     h->forces_valid = false;
+    return MD_OK;
+}
+
+// Per-atom rows for export under MD_FORCE_PAIRED, whose rebuilds build the
+// slot lists only: the list of the positions of the last build (xq_build,
+// xabs), rebuilt when a build happened since the rows were last made.
+md_status atom_list_for_export(md_system *h) {
+    md_status st = read_status(h);
+    if (st != MD_OK) return st;
+    if (h->nlist != nullptr && h->atom_list_at == h->ds_host->builds) return MD_OK;
+    MD_CK(launch_build_list(h, false, false, h->xq_build));
+    st = read_status(h);
+    if (st != MD_OK) return st;
+    if (h->ds_host->status != 0)
+        return fail(h, (md_status)h->ds_host->status, "device error during list count");
+    int cap = h->p.max_neighbors > 0 ? ((h->p.max_neighbors + 3) & ~3) : cap_for(h->ds_host->max_count);
+    cap = std::max(cap, 8);
+    if (cap != h->cap || h->nlist == nullptr) MD_CK(alloc_list(h, cap));
+    MD_CK(launch_build_list(h, true, false, h->xq_build));
+    st = read_status(h);
+    if (st != MD_OK) return st;
+    if (h->ds_host->status != 0)
+        return fail(h, (md_status)h->ds_host->status, "device error during the export list build");
+    h->atom_list_at = h->ds_host->builds;
     return MD_OK;
 }
 
@@ -407,7 +454,10 @@ md_status enqueue_forces(md_system *h, int mode, bool energy, bool store_f) {
         MD_CK(launch_cluster_forces(h, mode, energy, store_f));
         h->launches += 1;
     } else if (h->p.force_variant == MD_FORCE_PAIRED) {
-        MD_CK(launch_pair_forces(h, mode, energy, store_f));
+        if (persistent_path(h) && !energy)
+            MD_CK(launch_lj_persist(h, mode, store_f, h->p.scheduler == MD_SCHED_DYNAMIC, false));
+        else
+            MD_CK(launch_pair_forces(h, mode, energy, store_f));
         h->launches += 1;
     } else if (h->p.force_variant != MD_FORCE_FULL) {
         int nl = 0;
@@ -722,10 +772,8 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
             return fail(nullptr, MD_ERR_INVALID,
                         W + ": multi-element systems run full lists under MD_SCHED_GRID");
     }
-    if (p->force_variant == MD_FORCE_PAIRED &&
-        (R != 1 || p->scheduler != MD_SCHED_GRID || ltypes))
-        return fail(nullptr, MD_ERR_INVALID,
-                    W + ": two atoms per thread run one one-species box under MD_SCHED_GRID");
+    if (p->force_variant == MD_FORCE_PAIRED && (R != 1 || ltypes))
+        return fail(nullptr, MD_ERR_INVALID, W + ": two atoms per thread run one one-species box");
     if (p->force_variant == MD_FORCE_CLUSTER &&
         (R != 1 || p->scheduler != MD_SCHED_GRID || ltypes || n >= ((int64_t)1 << 25)))
         return fail(nullptr, MD_ERR_INVALID,
@@ -1028,14 +1076,15 @@ md_status md_step(md_system *h, int64_t nsteps) {
         if (st != MD_OK) return st;
         if (h->p.max_neighbors > 0)
             return fail(h, MD_ERR_LIST_OVERFLOW, "md_step: neighbour count exceeds max_neighbors");
-        MD_CK(alloc_list(h, cap_for(h->ds_host->max_count)));
-        MD_CK(launch_build_list(h, true, false));
-        if (h->ov_on) MD_CK(launch_overlap_index(h, false));
-        if (h->p.force_variant == MD_FORCE_CLUSTER) MD_CK(launch_cluster_build(h, false));
         if (h->p.force_variant == MD_FORCE_PAIRED) {
             st = pair_rebuild_now(h);
             if (st != MD_OK) return st;
+        } else {
+            MD_CK(alloc_list(h, cap_for(h->ds_host->max_count)));
+            MD_CK(launch_build_list(h, true, false));
         }
+        if (h->ov_on) MD_CK(launch_overlap_index(h, false));
+        if (h->p.force_variant == MD_FORCE_CLUSTER) MD_CK(launch_cluster_build(h, false));
         st = enqueue_sched_prep(h, false);
         if (st != MD_OK) return st;
         MD_CK(launch_finish_rebuild(h, false));
@@ -1115,6 +1164,10 @@ md_status md_get_neighbors(md_system *h, int32_t half, int64_t *offsets_dev, int
         md_status st = rebuild_now(h, false);
         if (st != MD_OK) return st;
     }
+    if (h->p.force_variant == MD_FORCE_PAIRED) {
+        md_status st = atom_list_for_export(h);
+        if (st != MD_OK) return st;
+    }
     if (!h->exp_tmp) MD_CK(dalloc(&h->exp_tmp, (size_t)h->n + 64));
     MD_CK(launch_export_list(h, half ? 1 : 0, offsets_dev, nullptr, h->exp_tmp));
     int32_t total32 = 0;
@@ -1190,19 +1243,18 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
         (scheduler != MD_SCHED_GRID || h->n >= ((int64_t)1 << 25)))
         return fail(h, MD_ERR_INVALID,
                     "md_set_variant: the cluster-pair list runs under MD_SCHED_GRID, n < 2^25");
-    if (force_variant == MD_FORCE_PAIRED && scheduler != MD_SCHED_GRID)
-        return fail(h, MD_ERR_INVALID, "md_set_variant: two atoms per thread run under MD_SCHED_GRID");
     // a change between half and full pair sets relists; entering the cluster
     // or the two-atom layout builds its tables and list
     const bool relist = half_variant(force_variant) != half_variant(h->p.force_variant) ||
                         (force_variant == MD_FORCE_CLUSTER && h->p.force_variant != MD_FORCE_CLUSTER) ||
-                        (force_variant == MD_FORCE_PAIRED && h->p.force_variant != MD_FORCE_PAIRED);
+                        ((force_variant == MD_FORCE_PAIRED) != (h->p.force_variant == MD_FORCE_PAIRED));
     drop_graphs(h);  // the captured steps launch the old variant's kernels
     h->p.force_variant = force_variant;
     h->p.scheduler = scheduler;
     md_status st = MD_OK;
     if (scheduler != MD_SCHED_GRID) st = ensure_sched(h);
     if (st != MD_OK) return st;
+    sched_shape(h);
     if (relist || !h->list_valid) return rebuild_now(h, true);
     // same list: only the partition of the new scheduler is needed
     return enqueue_sched_prep(h, false);
@@ -1324,10 +1376,12 @@ md_status cta_imbalance(md_system *h, float *out) {
 md_status md_cost_model(md_system *h, int32_t op, float *loss_out) {
     if (!h) return fail(nullptr, MD_ERR_INVALID, "md_cost_model: null handle");
     if (h->p.potential != MD_POT_LJ || h->p.precision != MD_MIXED ||
-        h->p.force_variant != MD_FORCE_FULL || h->R > 1 || h->fc.ntypes > 0)
+        (h->p.force_variant != MD_FORCE_FULL && h->p.force_variant != MD_FORCE_PAIRED) ||
+        h->R > 1 || h->fc.ntypes > 0)
         return fail(h, MD_ERR_INVALID,
                     "md_cost_model: the cost model drives the persistent mixed-precision "
-                    "Lennard-Jones full-list force kernel of a single box");
+                    "Lennard-Jones full-list force kernel (per atom or two atoms per thread) "
+                    "of a single box");
     md_status st = ensure_sched(h);
     if (st != MD_OK) return st;
     const int kPasses = 3, kIters = 400;
@@ -1420,14 +1474,14 @@ md_status md_stats(md_system *h, char *buf_host, size_t cap) {
                   "\"steps\": %lld, \"max_count\": %d, \"max_cell\": %d, \"status\": %d, "
                   "\"precision\": %d, \"force_variant\": %d, \"scheduler\": %d, "
                   "\"list_entries\": %llu, \"pairs_cut\": %llu, \"cluster_pairs\": %llu, "
-                  "\"slot_entries\": %llu, \"slot_max\": %d, \"launches\": %lld, "
+                  "\"slot_entries\": %llu, \"slot_max\": %d, \"slots\": %d, \"launches\": %lld, "
                   "\"ms\": {\"rebuild\": %.6f, \"force\": %.6f, \"integrate\": %.6f, "
                   "\"other\": %.6f}, \"count\": {\"rebuild\": %lld, \"force\": %lld, "
                   "\"integrate\": %lld, \"other\": %lld}}",
                   (long long)h->n, h->g.nx, h->g.ny, h->g.nz, h->cap, d.builds,
                   (long long)h->steps_total, d.max_count, d.max_cell, d.status, h->p.precision,
                   h->p.force_variant, h->p.scheduler, d.list_entries, d.pairs_cut,
-                  d.cluster_pairs, d.pair_entries, d.pair_max,
+                  d.cluster_pairs, d.pair_entries, d.pair_max, d.pair_slots,
                   h->launches + d.cond_runs * h->body_launches,
                   h->ms_kind[0], h->ms_kind[1], h->ms_kind[2], h->ms_kind[3], h->n_kind[0],
                   h->n_kind[1], h->n_kind[2], h->n_kind[3]);

@@ -85,7 +85,7 @@ struct DevStatus {
     unsigned long long cluster_pairs; // (i-cluster, j-cluster) entries of the last cluster list
     unsigned long long pair_entries;  // entries of the last two-atom slot list
     int pair_max;                     // its longest row
-    int pad1;
+    int pair_slots;                   // its slots
 };
 
 // What the persistent force kernel needs besides ForceArgs.
@@ -256,6 +256,7 @@ struct md_system {
 
     // persistent scheduler and learned cost model (allocated on first use)
     int sched_ctas = 0;                 // resident CTAs of the persistent force kernel
+    int sched_sms = 0;                  // SMs of the device (0: scheduler not set up)
     int sched_rounds = 1;               // static ranges per CTA (sched_rounds())
     int sched_rounds_set = 0;           // md_set_schedule: fixed ranges per CTA (0 = by size)
     int sched_tail_pct = mdg::kTailPctDefault;  // md_set_schedule: share of the cost in the tail
@@ -296,6 +297,7 @@ struct md_system {
     uint32_t *ps_list = nullptr;   // union lists, per-atom layout over slots
     int32_t *ps_count = nullptr;   // their lengths
     int ps_cap = 0;
+    int atom_list_at = -1;         // build count when the per-atom rows were last made
 
     // inner/outer split of the force pass (md_set_decomposition)
     bool ov_on = false;
@@ -351,7 +353,10 @@ cudaError_t launch_scan_i32(const int32_t *in, int32_t *out, int n, int32_t *bsu
 cudaError_t launch_export_cells(md_system *h, int32_t *cell_of_atom, int64_t *cell_start);
 
 // ---- neighbour list (k_nlist.cu) ------------------------------------------
-cudaError_t launch_build_list(md_system *h, bool write, bool gated);
+// positions: the float32 positions the list is built from (default: the
+// current buffer, right after binning)
+cudaError_t launch_build_list(md_system *h, bool write, bool gated,
+                              const float4 *positions = nullptr);
 cudaError_t launch_finish_rebuild(md_system *h, bool gated);
 cudaError_t launch_export_list(md_system *h, int half, int64_t *offsets, int32_t *ids,
                                int64_t *row_counts_tmp);
@@ -362,7 +367,7 @@ cudaError_t launch_lj(md_system *h, int mode, bool energy, bool store_f);
 cudaError_t launch_lj_half(md_system *h, int mode, bool energy, int *launches);
 // persistent LJ kernel (mixed precision, full list); timing only with FM_STORE
 cudaError_t launch_lj_persist(md_system *h, int mode, bool store_f, bool dynamic, bool timing);
-int persist_ctas_per_sm(bool f64);
+int persist_ctas_per_sm(bool f64, bool paired);
 cudaError_t launch_sc_density(md_system *h);
 cudaError_t launch_sc_force(md_system *h, int mode, bool energy, bool store_f);
 // cluster-pair list (k_cluster.cu): tables and list after a rebuild (10 kernels),
