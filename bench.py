@@ -419,7 +419,7 @@ def run_gpu(args, rank, world, local):
                         "force_ms_per_launch": stx["ms"]["force"] / max(1, stx["count"]["force"]),
                         "cta_imbalance": md.md_cost_model(mixed.h, md.MD_COST_PROFILE),
                         "note": "static ranges only (md_set_schedule tail_percent = 0)"}
-                    md.md_set_schedule(mixed.h, 0, 20)
+                    md.md_set_schedule(mixed.h, 0, -1)  # the layout's default tail
                 # the Newton's-third-law variants (half lists) against the full list
                 variants = {}
                 for name, code in (("full", md.MD_FORCE_FULL),

@@ -329,12 +329,13 @@ md_status md_set_decomposition(md_system *h, int32_t px, int32_t py, int32_t pz)
 
 /* Shape of the static partition used by MD_SCHED_PAIRCOUNT and MD_SCHED_MLP
  * (the load-balance question of Sec. 1 and Sec. 2.1 for inhomogeneous
- * systems): rounds = equal-cost ranges per persistent CTA (1..8; 0 = sized
- * from the system, about 24 tiles of 32 atoms per range), tail_percent =
- * share of the estimated cost left as a tail that CTAs claim tile by tile
- * once their ranges are done (0..50, default 20).  tail_percent = 0 makes
- * the partition purely static, so the cost estimate alone balances the
- * CTAs.  Recomputes the partition; captured step graphs are dropped.
+ * systems): rounds = equal-cost ranges per persistent CTA (1..16; 0 = sized
+ * from the system, about 24 tiles of 32 work items per range), tail_percent
+ * = share of the estimated cost left as a tail that CTAs claim tile by tile
+ * once their ranges are done (0..80; -1 = the layout's default, measured:
+ * 20 for the per-atom list, 40 for two atoms per thread).  tail_percent = 0
+ * makes the partition purely static, so the cost estimate alone balances
+ * the CTAs.  Recomputes the partition; captured step graphs are dropped.
  * MD_ERR_INVALID outside those ranges. */
 md_status md_set_schedule(md_system *h, int32_t rounds, int32_t tail_percent);
 

@@ -242,18 +242,18 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 constexpr int kPersistBlock = 128;
 // The slot job holds twice the accumulators: its persistent kernel gets up to
 // 64 registers (8 CTAs per SM) instead of spilling at 56.
-constexpr int kPersistPairedCtas = 8;
+constexpr int kPersistPairedCtas = 9;
 
 template <int MODE, bool ENERGY, bool DYNAMIC, bool TIMING, bool MULTI = false, bool F64 = false,
           bool PAIRED = false>
 __global__ void __launch_bounds__(kPersistBlock, F64 ? 8 : (PAIRED ? kPersistPairedCtas : 9))
 lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa, PairArgs pa) {
-    static_assert(kSchedRounds <= 8, "per-CTA range table holds 8 rounds");
+
     static_assert(!(F64 && MULTI), "batches run the mixed path");
     static_assert(!(PAIRED && (F64 || MULTI || ENERGY)), "slots: one box, mixed path, forces");
     __shared__ ShiftTab sh;
     __shared__ double3 sh64[F64 ? kStencil : 1];
-    __shared__ int s_first[8], s_pre[9], s_next;  // this CTA's ranges (static mode)
+    __shared__ int s_first[kSchedRounds], s_pre[kSchedRounds + 1], s_next;  // this CTA's ranges
     __shared__ int s_stop;
     if (F64) load_shifts_f64(a.g, sh64);
     else if (!MULTI) load_shifts_f32(a.g, &sh);
@@ -268,16 +268,24 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa, PairArgs pa) {
     const int ntiles = (nitems + 31) >> 5;
     long long cta_t0 = 0;
     if (TIMING) cta_t0 = clock64();
-    int nlocal = 0;       // static mode: tiles of all this CTA's ranges
-    int tail0 = ntiles;   // static mode: first tile of the tail
+    // The claim state lives in shared memory (the CTA's ranges, and each
+    // warp's queue cursor), so that no register is held through the work of
+    // a tile: the slot job needs all of them.
+    __shared__ int s_nlocal, s_tail0;
+    __shared__ int s_wq[kPersistBlock / 32][4];  // per warp: claim end, next, range, local done
+    if (threadIdx.x == 0) {
+        s_nlocal = 0;
+        s_tail0 = ntiles;
+    }
+    if (lane < 4) s_wq[threadIdx.x >> 5][lane] = (lane == 3) ? (DYNAMIC ? 1 : 0) : 0;
     if (!DYNAMIC) {
-        const long long qt = (long long)sa.rounds * gridDim.x;
-        tail0 = (sa.cell_start[sa.bounds[qt]] + 31) >> 5;
         // cyclic static partition: this CTA owns ranges b, b + G, b + 2G, ...
         // so that at any time all CTAs work in one window of the sorted atoms
         // (neighbour gathers then hit in L2).  Its warps claim the ranges'
         // tiles one at a time from a shared counter, so they finish together.
         if (threadIdx.x == 0) {
+            const long long qt = (long long)sa.rounds * gridDim.x;
+            s_tail0 = (sa.cell_start[sa.bounds[qt]] + 31) >> 5;
             int acc = 0;
             for (int r = 0; r < sa.rounds; ++r) {
                 const long long q = (long long)r * gridDim.x + blockIdx.x;
@@ -288,36 +296,51 @@ lj_mixed_persist(ForceArgs a, int store_f, SchedArgs sa, PairArgs pa) {
                 acc += te - tf;
             }
             s_pre[sa.rounds] = acc;
+            s_nlocal = acc;
             s_next = 0;
         }
-        __syncthreads();
-        nlocal = s_pre[sa.rounds];
     }
-    // next tile of this warp, or -1 when none is left
-    int claim_end = 0, tdyn = 0;
-    bool local_done = DYNAMIC;
+    __syncthreads();
+    // next tile of this warp, or -1 when none is left; every lane computes the
+    // same values, so the lanes' identical stores to the warp's cursor agree
     auto claim = [&]() -> int {
-        if (!local_done) {
+        int *wq = s_wq[threadIdx.x >> 5];
+        int res = -1;
+        bool done = wq[3] != 0;
+        if (!done) {
             int k = 0;
             if (lane == 0) k = atomicAdd(&s_next, 1);
             k = __shfl_sync(0xffffffffu, k, 0);
-            if (k < nlocal) {
-                int r = 0;
+            if (k < s_nlocal) {
+                int r = wq[2];  // this warp's claims only grow: its range only advances
                 while (k >= s_pre[r + 1]) ++r;
-                return s_first[r] + (k - s_pre[r]);
+                res = s_first[r] + (k - s_pre[r]);
+                __syncwarp();
+                wq[2] = r;
+            } else {
+                done = true;
+                __syncwarp();
+                wq[3] = 1;
             }
-            local_done = true;
         }
-        // the global queue: all tiles (dynamic mode) or the tail (static mode)
-        const int base = DYNAMIC ? 0 : tail0;
-        const int step = DYNAMIC ? kClaim : kClaimTail;
-        if (tdyn >= claim_end) {
-            int c = 0;
-            if (lane == 0) c = atomicAdd(&a.ds->tile_counter, step);
-            tdyn = base + __shfl_sync(0xffffffffu, c, 0);
-            claim_end = tdyn + step;
+        if (done) {
+            // the global queue: all tiles (dynamic mode) or the tail (static mode)
+            const int base = DYNAMIC ? 0 : s_tail0;
+            const int step = DYNAMIC ? kClaim : kClaimTail;
+            int tnext = wq[1], cend = wq[0];
+            if (tnext >= cend) {
+                int c = 0;
+                if (lane == 0) c = atomicAdd(&a.ds->tile_counter, step);
+                tnext = base + __shfl_sync(0xffffffffu, c, 0);
+                cend = tnext + step;
+            }
+            if (tnext < ntiles) res = tnext++;
+            __syncwarp();
+            wq[1] = tnext;
+            wq[0] = cend;
         }
-        return tdyn < ntiles ? tdyn++ : -1;
+        __syncwarp();
+        return res;
     };
     int t = claim();
     while (t >= 0) {

@@ -266,10 +266,15 @@ bool uses_partition(const md_system *h) {
 // Resident CTAs and ranges per CTA of the persistent kernel of the current
 // force layout (the two-atom kernel runs fewer, larger CTAs per SM).
 void sched_shape(md_system *h) {
+    if (!h->sched_tail_set)
+        h->sched_tail_pct = h->p.force_variant == MD_FORCE_PAIRED ? kTailPctPaired : kTailPctDefault;
     if (h->sched_sms <= 0) return;
     const bool paired = (h->p.force_variant == MD_FORCE_PAIRED);
     h->sched_ctas = h->sched_sms * persist_ctas_per_sm(h->p.precision == MD_FP64, paired);
-    h->sched_rounds = h->sched_rounds_set > 0 ? h->sched_rounds_set : sched_rounds(h->n, h->sched_ctas);
+    // ranges of about kTilesPerRange tiles of the layout's work items (atoms,
+    // or slots of two atoms)
+    const int64_t items = paired ? (h->n + 1) / 2 : h->n;
+    h->sched_rounds = h->sched_rounds_set > 0 ? h->sched_rounds_set : sched_rounds(items, h->sched_ctas);
 }
 
 // Buffers of the scheduler and the cost model, allocated on first use.
@@ -1262,13 +1267,15 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
 
 md_status md_set_schedule(md_system *h, int32_t rounds, int32_t tail_percent) {
     if (!h) return fail(nullptr, MD_ERR_INVALID, "md_set_schedule: null handle");
-    if (rounds < 0 || rounds > kSchedRounds || tail_percent < 0 || tail_percent > kTailPctMax)
-        return fail(h, MD_ERR_INVALID, "md_set_schedule: rounds must be 0..8 and tail_percent 0..50");
+    if (rounds < 0 || rounds > kSchedRounds || tail_percent < -1 || tail_percent > kTailPctMax)
+        return fail(h, MD_ERR_INVALID,
+                    "md_set_schedule: rounds must be 0..16 and tail_percent -1..80");
     drop_graphs(h);  // the captured steps hold the old partition's shape
     h->sched_rounds_set = rounds;
-    h->sched_tail_pct = tail_percent;
+    h->sched_tail_set = tail_percent >= 0;
+    if (h->sched_tail_set) h->sched_tail_pct = tail_percent;
+    sched_shape(h);
     if (!h->part_bounds) return MD_OK;  // applied when the scheduler allocates
-    h->sched_rounds = rounds > 0 ? rounds : sched_rounds(h->n, h->sched_ctas);
     if (!h->list_valid) return rebuild_now(h, false);
     return enqueue_sched_prep(h, false);
 }

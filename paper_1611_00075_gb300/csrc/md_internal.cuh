@@ -20,8 +20,9 @@ constexpr uint32_t kIndexMask = (1u << kIndexBits) - 1u;
 constexpr int64_t kMaxAtoms = (int64_t)1 << kIndexBits;
 // share of the estimated cost in the dynamically claimed tail of the static
 // schedulers (percent): default and largest accepted by md_set_schedule
-constexpr int kTailPctDefault = 20;
-constexpr int kTailPctMax = 50;
+constexpr int kTailPctDefault = 20;  // per-atom layout
+constexpr int kTailPctPaired = 40;   // two-atom layout (measured: 20 % left it 15 % slower)
+constexpr int kTailPctMax = 80;
 
 // Neighbour-list layout.  Atoms are grouped by 32 (one warp); inside a group
 // each atom's entries are stored in quads: uint32 [n/32][cap/4][32][4].  A
@@ -259,7 +260,8 @@ struct md_system {
     int sched_sms = 0;                  // SMs of the device (0: scheduler not set up)
     int sched_rounds = 1;               // static ranges per CTA (sched_rounds())
     int sched_rounds_set = 0;           // md_set_schedule: fixed ranges per CTA (0 = by size)
-    int sched_tail_pct = mdg::kTailPctDefault;  // md_set_schedule: share of the cost in the tail
+    int sched_tail_pct = mdg::kTailPctDefault;  // share of the cost in the tail
+    bool sched_tail_set = false;                // md_set_schedule chose it (else the layout's)
     long long *part_bounds = nullptr;   // sched_parts(sched_ctas, sched_rounds) + 1 cell bounds
     long long *cell_cost = nullptr;     // quantised per-cell cost (ncells)
     long long *part_scratch = nullptr;  // prefix sums of the partition
@@ -408,7 +410,7 @@ constexpr int kMlpParams = 1217;
 // that the persistent kernel hands out dynamically.  Rounds grow with the
 // system so that a range keeps about kTilesPerRange 32-atom tiles, up to
 // kSchedRounds (measured: one round at 1 M atoms, eight at 9.8 M).
-constexpr int kSchedRounds = 8;
+constexpr int kSchedRounds = 16;
 constexpr int kTilesPerRange = 24;
 inline int sched_rounds(int64_t n, int ctas) {
     const int64_t r = ((n + 31) / 32) / ((int64_t)ctas * kTilesPerRange);

@@ -186,7 +186,7 @@ def test_learned_partition_balances_measured_work_better(md, orc):
             md.md_set_variant(a.h, md.MD_FORCE_FULL, code)
             md.md_set_schedule(a.h, 2, 0)  # two static ranges per CTA, no tail
             timed[name] = md.md_cost_model(a.h, md.MD_COST_PROFILE)
-        md.md_set_schedule(a.h, 0, 20)
+        md.md_set_schedule(a.h, 0, -1)
     cyc, pred, pair = (t.cpu().numpy() for t in (cyc, pred, pair))
     pref = np.concatenate([[0.0], np.cumsum(cyc.astype(np.float64))])
     for parts in (64, 256):
