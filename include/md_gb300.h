@@ -202,7 +202,12 @@ md_status md_energy_batch(md_system *h, double *ke_host, double *pe_host);
 /* Cell binning only (Sec. 2.1): assigns each atom to cell
  * c = min(floor(x * n_d / L_d), n_d - 1) per dimension, n_d = floor(L_d /
  * r_list), linear id (cz * ny + cy) * nx + cx, and reorders the private copy
- * stably by (cell, original id).  Invalidates the neighbour list. */
+ * stably by (cell, original id).  Under MD_FORCE_PAIRED each cell of up to
+ * 32 atoms is put in a pairing order instead (ranked by the Morton code of
+ * the position at 1/8 of the cell width; the first unpaired atom takes its
+ * nearest unpaired cell mate), so the atoms 2k and 2k + 1 that form slot k
+ * are near neighbours.  Either order is deterministic and invisible to the
+ * exports, which are in original order.  Invalidates the neighbour list. */
 md_status md_bin_cells(md_system *h);
 
 /* Rebuilds the Verlet list from the current positions (bins first).  An

@@ -5,7 +5,10 @@
 // dimension, counted with atomics, the counts are scanned into cell starts,
 // atoms are scattered into their cell's range and each cell's range is put in
 // ascending original-id order, so the sorted layout is deterministic and
-// equals a stable sort by (cell, original id).  The gather then rewrites the
+// equals a stable sort by (cell, original id).  For the two-atom layout,
+// whose slots take a cell's atoms two at a time, each cell is instead put in
+// a pairing order (cell_pair_order_kernel), also deterministic, that places
+// near neighbours next to each other.  The gather then rewrites the
 // state in the new order as float64 positions relative to the cell centre
 // plus their float32 copy (the layout the force kernels read).
 //
@@ -20,6 +23,7 @@
 #include "k_scan.cuh"
 
 #include <algorithm>
+#include <climits>
 
 namespace mdg {
 
@@ -134,6 +138,21 @@ __global__ void scatter_kernel(int n, const int32_t *__restrict__ new_cell,
 // systems) is insertion-sorted by one lane.
 constexpr int kSortBlock = 256;
 
+__device__ void insertion_sort_cell(int b, int m, int32_t *__restrict__ key,
+                                    int32_t *__restrict__ src) {
+    for (int a = b + 1; a < b + m; ++a) {
+        const int k = key[a], sv = src[a];
+        int q = a - 1;
+        while (q >= b && key[q] > k) {
+            key[q + 1] = key[q];
+            src[q + 1] = src[q];
+            --q;
+        }
+        key[q + 1] = k;
+        src[q + 1] = sv;
+    }
+}
+
 __global__ void __launch_bounds__(kSortBlock)
 cell_sort_kernel(int ncells, const int32_t *__restrict__ start, int32_t *__restrict__ key,
                  int32_t *__restrict__ src, const DevStatus *ds, bool gated) {
@@ -153,17 +172,91 @@ cell_sort_kernel(int ncells, const int32_t *__restrict__ start, int32_t *__restr
                 src[b + rank] = sv;
             }
         } else if (lane == 0) {
-            for (int a = b + 1; a < b + m; ++a) {
-                const int k = key[a], sv = src[a];
-                int q = a - 1;
-                while (q >= b && key[q] > k) {
-                    key[q + 1] = key[q];
-                    src[q + 1] = src[q];
-                    --q;
-                }
-                key[q + 1] = k;
-                src[q + 1] = sv;
-            }
+            insertion_sort_cell(b, m, key, src);
+        }
+    }
+}
+
+// three bits per axis interleaved (x lowest): the octree position of a point
+// in its cell at 1/8 of the cell width
+__device__ __forceinline__ unsigned morton9(unsigned qx, unsigned qy, unsigned qz) {
+    auto spread = [](unsigned v) { return (v & 1u) | ((v & 2u) << 2) | ((v & 4u) << 4); };
+    return spread(qx) | (spread(qy) << 1) | (spread(qz) << 2);
+}
+
+// the octree coordinate, from float32 position and inverse width (products
+// and differences rounded one by one)
+__device__ __forceinline__ unsigned octree_coord(float x, float inv_w) {
+    const float t = __fmul_rn(x, inv_w);
+    const int q = (int)__fmul_rn(__fsub_rn(t, floorf(t)), 8.0f);
+    return (unsigned)min(max(q, 0), 7);
+}
+
+// Pairing order for the two-atom layout, whose slot k of a cell holds the
+// cell's sorted atoms 2k and 2k + 1: the union of two cut-off spheres grows
+// with the distance between their centres, and a warp's loop runs as long as
+// its longest slot list, so the pairs should be near neighbours.  One warp
+// per cell of up to 32 atoms: the atoms are ranked by the Morton code of
+// their octree position in the cell (ties by original id); then, while two
+// or more are left, the first unpaired atom in that rank takes the nearest
+// unpaired atom (ties by rank), and the two fill the next two places.  A
+// cell of odd occupancy ends with the atom left over.  The order depends on
+// positions and ids only, so it is deterministic; a larger cell falls back to
+// the original-id order.
+__global__ void __launch_bounds__(kSortBlock)
+cell_pair_order_kernel(int ncells, const Grid *__restrict__ grids,
+                       const int32_t *__restrict__ start, const double4 *__restrict__ tabs,
+                       int32_t *__restrict__ key, int32_t *__restrict__ src, const DevStatus *ds,
+                       bool gated) {
+    if (chain_off(ds, gated)) return;
+    constexpr unsigned full = 0xffffffffu;
+    const Grid &g = grids[0];
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (kSortBlock / 32);
+    for (int c = blockIdx.x * (kSortBlock / 32) + (threadIdx.x >> 5); c < ncells; c += nw) {
+        const int b = start[c], m = start[c + 1] - b;
+        if (m <= 1) continue;
+        if (m > 32) {
+            if (lane == 0) insertion_sort_cell(b, m, key, src);
+            continue;
+        }
+        const bool on = lane < m;
+        const int o = on ? key[b + lane] : 0x7fffffff;
+        const int sv = on ? src[b + lane] : 0;
+        // a layout heuristic: float32 positions suffice (and the float64 pipe
+        // is slow on this part)
+        const double4 a = on ? tabs[sv] : make_double4(0.0, 0.0, 0.0, 0.0);
+        const float px = (float)a.x, py = (float)a.y, pz = (float)a.z;
+        const unsigned mk = morton9(octree_coord(px, (float)g.inv_w[0]),
+                                    octree_coord(py, (float)g.inv_w[1]),
+                                    octree_coord(pz, (float)g.inv_w[2]));
+        const long long K = on ? (((long long)mk << 32) | (long long)o) : LLONG_MAX;
+        unsigned rank = 0;
+        for (int q = 0; q < m; ++q) rank += (__shfl_sync(full, K, q) < K) ? 1u : 0u;
+        unsigned left = __ballot_sync(full, on);
+        int dst = 0, next = 0;
+        while (__popc(left) >= 2) {
+            const bool mine = (left >> lane) & 1u;
+            const unsigned r = mine ? rank : full;
+            const int first = __ffs(__ballot_sync(full, r == __reduce_min_sync(full, r))) - 1;
+            const float fx = __shfl_sync(full, px, first), fy = __shfl_sync(full, py, first),
+                        fz = __shfl_sync(full, pz, first);
+            // atoms of one cell need no periodic image
+            const float dx = __fsub_rn(px, fx), dy = __fsub_rn(py, fy), dz = __fsub_rn(pz, fz);
+            const float d2 =
+                __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+            const unsigned k2 = (mine && lane != first) ? ((__float_as_uint(d2) & ~31u) | rank)
+                                                        : full;
+            const int mate = __ffs(__ballot_sync(full, k2 == __reduce_min_sync(full, k2))) - 1;
+            if (lane == first) dst = next;
+            if (lane == mate) dst = next + 1;
+            next += 2;
+            left &= ~((1u << first) | (1u << mate));
+        }
+        if ((left >> lane) & 1u) dst = next;
+        if (on) {
+            key[b + dst] = o;
+            src[b + dst] = sv;
         }
     }
 }
@@ -240,8 +333,12 @@ cudaError_t launch_bin(md_system *h, bool gated) {
                                                    h->orig, h->src, h->key, h->ds, gated);
     const int sort_blocks = std::min((h->g.ncells + kSortBlock / 32 - 1) / (kSortBlock / 32),
                                      kGridCap * 2);
-    cell_sort_kernel<<<std::max(sort_blocks, 1), kSortBlock, 0, s>>>(h->g.ncells, h->cell_start,
-                                                                     h->key, h->src, h->ds, gated);
+    if (h->p.force_variant == MD_FORCE_PAIRED)
+        cell_pair_order_kernel<<<std::max(sort_blocks, 1), kSortBlock, 0, s>>>(
+            h->g.ncells, h->grids, h->cell_start, h->tmp_abs, h->key, h->src, h->ds, gated);
+    else
+        cell_sort_kernel<<<std::max(sort_blocks, 1), kSortBlock, 0, s>>>(
+            h->g.ncells, h->cell_start, h->key, h->src, h->ds, gated);
     gather_kernel<<<gs_blocks(n), kBlock, 0, s>>>(n, h->grids, h->src, h->tmp_abs, h->tmp_v,
                                                   h->xr64[cur], h->xq[cur], h->xq_build, h->xabs,
                                                   h->v, h->orig, h->cell, h->rep, h->type_orig,

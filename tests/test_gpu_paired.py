@@ -245,3 +245,84 @@ def test_paired_export_follows_the_builds(md, orc):
         np.testing.assert_array_equal(o.cpu().numpy(), ooff)
         np.testing.assert_array_equal(i.cpu().numpy(), oids)
     assert st["slot_entries"] > 0
+
+
+def _morton9(q):
+    k = np.zeros(len(q), np.int64)
+    for bit in range(3):
+        for d in range(3):
+            k |= ((q[:, d] >> bit) & 1) << (3 * bit + d)
+    return k
+
+
+def pairing_model(pos, start, order, inv_w, spatial):
+    """Slots of the two-atom layout as (a, b) original ids, cell by cell.
+    spatial=False: the cell's atoms in original-id order, two at a time.
+    spatial=True: ranked by the Morton code of their position at 1/8 of the
+    cell width (ties by id); the first unpaired atom in rank takes the nearest
+    unpaired atom (squared distance, low 5 bits dropped, ties by rank); an
+    odd cell ends with the atom left over.  Positions, widths and distances
+    in float32, rounded operation by operation."""
+    slots = []
+    p32 = pos.astype(np.float32)
+    w32 = np.asarray(inv_w).astype(np.float32)
+    for c in range(len(start) - 1):
+        atoms = order[start[c]:start[c + 1]]
+        if len(atoms) == 0:
+            continue
+        if spatial and len(atoms) <= 32:
+            t = p32[atoms] * w32
+            q = np.clip(((t - np.floor(t)) * np.float32(8)).astype(np.int64), 0, 7)
+            left = list(atoms[np.lexsort((atoms, _morton9(q)))])
+            while len(left) >= 2:
+                a = left.pop(0)
+                d = p32[left] - p32[a]
+                d2 = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2]
+                key = d2.view(np.uint32) & np.uint32(~31 & 0xffffffff)
+                slots.append((a, left.pop(int(np.argmin(key)))))
+            slots += [(x, x) for x in left]
+        else:
+            slots += [(atoms[k], atoms[min(k + 1, len(atoms) - 1)])
+                      for k in range(0, len(atoms), 2)]
+    return slots
+
+
+def union_entries(slots, off, ids):
+    tot = 0
+    for a, b in slots:
+        u = set(ids[off[a]:off[a + 1]].tolist()) | set(ids[off[b]:off[b + 1]].tolist())
+        u.discard(a)
+        u.discard(b)
+        tot += len(u)
+    return tot
+
+
+@pytest.mark.parametrize("name", ["porous", "disordered", "dilute"])
+def test_pairing_order_shortens_the_slot_lists(md, orc, name):
+    """Under MD_FORCE_PAIRED each cell is put in a pairing order (near
+    neighbours next to each other) before its atoms are taken two at a time:
+    the slot entries equal the union sizes of that pairing, computed here
+    from the oracle's cells and rows, and are fewer than those of the
+    original-id order.  Cells and lists stay exact."""
+    s, pos = systems(name)
+    off, ids = orc.neighbors_cells(pos, s.box, 2.8)
+    _, cell_of0, start0, order = orc.bin_cells(pos, s.box, 2.8)
+    _, inv_w = orc.cell_grid(s.box, 2.8)
+    want = union_entries(pairing_model(pos, start0, order, inv_w, True), off, ids)
+    plain = union_entries(pairing_model(pos, start0, order, inv_w, False), off, ids)
+    with md.System(pos, s.vel, s.box, precision="mixed",
+                   force_variant=md.MD_FORCE_PAIRED) as sy:
+        st = sy.stats()
+        _, cell_of, start = sy.cells()
+        goff, gids = sy.neighbors()
+    np.testing.assert_array_equal(cell_of.cpu().numpy(), cell_of0)
+    np.testing.assert_array_equal(start.cpu().numpy(), start0)
+    np.testing.assert_array_equal(goff.cpu().numpy(), off)
+    np.testing.assert_array_equal(gids.cpu().numpy(), ids)
+    got = st["slot_entries"]
+    print("%s: slot entries %d, model %d, original-id order %d (%.3f)"
+          % (name, got, want, plain, got / plain))
+    # float32 band candidates within r_list (1 + 2^-14), and pairings that
+    # differ only where two distances tie after rounding
+    assert abs(got - want) <= 2e-3 * want + 8
+    assert got < plain
