@@ -68,10 +68,48 @@ __global__ void slot_fill_kernel(int n, const int32_t *__restrict__ cell,
     }
 }
 
+// One stencil cell of a slot's union-list scan (HOME: the slot's own cell,
+// the only one holding i0 and i1); returns the running entry count.
+template <bool WRITE, bool HOME>
+__device__ __forceinline__ int scan_cell(int cnt, int b, int e, const float4 *__restrict__ xq,
+                                         float sx, float sy, float sz, float ux, float uy,
+                                         float uz, float lim, int i0, int i1, uint32_t *row,
+                                         int cap, uint32_t sbits) {
+#pragma unroll 4
+    for (int j = b; j < e; ++j) {
+        const float4 qj = xq[j];
+        const float ex = qj.x - sx, ey = qj.y - sy, ez = qj.z - sz;
+        const float r2 = ex * ex + ey * ey + ez * ez;
+        const float p = ex * ux + ey * uy + ez * uz;
+        bool acc = fmaf(-2.0f, fabsf(p), r2) < lim;
+        if (HOME) acc = acc & (j != i0) & (j != i1);
+        // past the capacity the row's last entry is overwritten: the
+        // overflow status discards the list
+        if (WRITE && acc) row[row_off(min(cnt, cap - 1))] = sbits | (uint32_t)j;
+        cnt += acc ? 1 : 0;
+    }
+    return cnt;
+}
+
 // The union list of each slot: the 27 cells around the slot's cell, in
-// stencil order, each candidate tested against both atoms in float32.
+// stencil order.  A candidate j is tested against both atoms at once from
+// the slot's midpoint m = (x0 + x1) / 2 and half separation u = (x1 - x0) / 2:
+// with e = x_j - m, the nearer atom's squared distance is
+// |e|^2 + |u|^2 - 2 |e.u|, so the test is |e|^2 - 2 |e.u| < hi - |u|^2 (one
+// difference vector and two dot products instead of two distances).  In
+// float32 the terms stay below about 16 sigma^2, so the rounding error of
+// this form is below 1e-5 sigma^2 against the 2^-14 r_list^2 (5e-4 sigma^2)
+// margin of hi: the list stays a superset of both atoms' r_list spheres.
+// Only the home cell holds i0 and i1, so only its scan excludes them.
+//
+// Measured on GB300 (porous LJ, 9.8 M atoms, 300 steps from the generated
+// state, one build of the union lists): 3.68 ms against 4.19 ms for two
+// direct distances per candidate.  Seven CTAs per SM (71 registers) against
+// 3.93 ms at eight and 4.16 ms at nine; the candidate loop unrolled by 4
+// against 4.13 ms by 2 and 4.30 ms by 8 (at eight CTAs).  Packed f32x2
+// distances for the two atoms were slower (4.98 against 4.45 ms).
 template <bool WRITE>
-__global__ void __launch_bounds__(kPairBlock)
+__global__ void __launch_bounds__(kPairBlock, 7)
 pair_list_kernel(int n, Grid g, float hi, const float4 *__restrict__ xq,
                  const int32_t *__restrict__ cell, const int32_t *__restrict__ start,
                  const int32_t *__restrict__ slot_start, const uint32_t *__restrict__ slot_atom,
@@ -93,6 +131,10 @@ pair_list_kernel(int n, Grid g, float hi, const float4 *__restrict__ xq,
             const int i0 = (int)(sa & ~kSingle);
             const int i1 = (sa & kSingle) ? i0 : i0 + 1;
             const float4 q0 = xq[i0], q1 = xq[i1];
+            const float ux = 0.5f * (q1.x - q0.x), uy = 0.5f * (q1.y - q0.y),
+                        uz = 0.5f * (q1.z - q0.z);
+            const float mx = q0.x + ux, my = q0.y + uy, mz = q0.z + uz;
+            const float lim = hi - (ux * ux + uy * uy + uz * uz);
             const int c = cell[i0];
             const int cx = c % g.nx, cy = (c / g.nx) % g.ny, cz = c / (g.nx * g.ny);
             uint32_t *row = list + list_group(s, cap) + ((s & 31) << 2);
@@ -104,25 +146,18 @@ pair_list_kernel(int n, Grid g, float hi, const float4 *__restrict__ xq,
                     for (int dx = -1; dx <= 1; ++dx) {
                         const int xx = (cx + dx + g.nx) % g.nx;
                         const int cn = (zz * g.ny + yy) * g.nx + xx;
-                        const uint32_t sbits =
-                            (uint32_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)) << kIndexBits;
-                        // home positions moved against the cell shift
-                        const float ax = q0.x - (float)dx * wx, ay = q0.y - (float)dy * wy,
-                                    az = q0.z - (float)dz * wz;
-                        const float bx = q1.x - (float)dx * wx, by = q1.y - (float)dy * wy,
-                                    bz = q1.z - (float)dz * wz;
+                        const uint32_t st = (uint32_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
+                        // the midpoint moved against the cell shift
+                        const float sx = mx - (float)dx * wx, sy = my - (float)dy * wy,
+                                    sz = mz - (float)dz * wz;
                         const int b = start[cn], e = start[cn + 1];
-#pragma unroll 4
-                        for (int j = b; j < e; ++j) {
-                            const float4 qj = xq[j];
-                            const float ex = qj.x - ax, ey = qj.y - ay, ez = qj.z - az;
-                            const float fx = qj.x - bx, fy = qj.y - by, fz = qj.z - bz;
-                            const float r0 = ex * ex + ey * ey + ez * ez;
-                            const float r1 = fx * fx + fy * fy + fz * fz;
-                            const bool acc = (fminf(r0, r1) < hi) & (j != i0) & (j != i1);
-                            if (WRITE && acc && cnt < cap) row[row_off(cnt)] = sbits | (uint32_t)j;
-                            cnt += acc ? 1 : 0;
-                        }
+                        const uint32_t sbits = st << kIndexBits;
+                        if (st == kHomeStencil)
+                            cnt = scan_cell<WRITE, true>(cnt, b, e, xq, sx, sy, sz, ux, uy, uz,
+                                                         lim, i0, i1, row, cap, sbits);
+                        else
+                            cnt = scan_cell<WRITE, false>(cnt, b, e, xq, sx, sy, sz, ux, uy, uz,
+                                                          lim, i0, i1, row, cap, sbits);
                     }
                 }
             }
