@@ -192,17 +192,31 @@ __device__ __forceinline__ unsigned octree_coord(float x, float inv_w) {
     return (unsigned)min(max(q, 0), 7);
 }
 
+// float64 to float32 rounded toward zero, from the IEEE-754 fields with
+// integer operations (the float64 pipe is slow on this part); a value below
+// the float32 normal range, zero included, gives 0
+__device__ __forceinline__ float f32_toward_zero(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return e <= 0 ? 0.0f : __uint_as_float((hi & 0x80000000u) | ((unsigned)e << 23) | m);
+}
+
 // Pairing order for the two-atom layout, whose slot k of a cell holds the
 // cell's sorted atoms 2k and 2k + 1: the union of two cut-off spheres grows
 // with the distance between their centres, and a warp's loop runs as long as
 // its longest slot list, so the pairs should be near neighbours.  One warp
 // per cell of up to 32 atoms: the atoms are ranked by the Morton code of
-// their octree position in the cell (ties by original id); then, while two
-// or more are left, the first unpaired atom in that rank takes the nearest
-// unpaired atom (ties by rank), and the two fill the next two places.  A
-// cell of odd occupancy ends with the atom left over.  The order depends on
-// positions and ids only, so it is deterministic; a larger cell falls back to
-// the original-id order.
+// their octree position in the cell (ties by original id) and moved to the
+// lane of their rank; then, while two or more are left, the first unpaired
+// atom in rank takes the nearest unpaired atom (squared distance with its low
+// 5 bits replaced by the rank, so ties go to the lower rank), and the two
+// fill the next two places.  A cell of odd occupancy ends with the atom left
+// over.  Positions are float32 (rounded toward zero from float64) and every
+// product and sum is rounded on its own, so the order depends on positions
+// and ids only and is deterministic; a larger cell falls back to the
+// original-id order.
 __global__ void __launch_bounds__(kSortBlock)
 cell_pair_order_kernel(int ncells, const Grid *__restrict__ grids,
                        const int32_t *__restrict__ start, const double4 *__restrict__ tabs,
@@ -210,7 +224,10 @@ cell_pair_order_kernel(int ncells, const Grid *__restrict__ grids,
                        bool gated) {
     if (chain_off(ds, gated)) return;
     constexpr unsigned full = 0xffffffffu;
-    const Grid &g = grids[0];
+    __shared__ int s_lane_of[kSortBlock / 32][32];
+    int *lane_of = s_lane_of[threadIdx.x >> 5];
+    const float iwx = (float)grids[0].inv_w[0], iwy = (float)grids[0].inv_w[1],
+                iwz = (float)grids[0].inv_w[2];
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * (kSortBlock / 32);
     for (int c = blockIdx.x * (kSortBlock / 32) + (threadIdx.x >> 5); c < ncells; c += nw) {
@@ -221,33 +238,38 @@ cell_pair_order_kernel(int ncells, const Grid *__restrict__ grids,
             continue;
         }
         const bool on = lane < m;
-        const int o = on ? key[b + lane] : 0x7fffffff;
-        const int sv = on ? src[b + lane] : 0;
-        // a layout heuristic: float32 positions suffice (and the float64 pipe
-        // is slow on this part)
+        int o = on ? key[b + lane] : 0x7fffffff;
+        int sv = on ? src[b + lane] : 0;
         const double4 a = on ? tabs[sv] : make_double4(0.0, 0.0, 0.0, 0.0);
-        const float px = (float)a.x, py = (float)a.y, pz = (float)a.z;
-        const unsigned mk = morton9(octree_coord(px, (float)g.inv_w[0]),
-                                    octree_coord(py, (float)g.inv_w[1]),
-                                    octree_coord(pz, (float)g.inv_w[2]));
+        float px = f32_toward_zero(a.x), py = f32_toward_zero(a.y), pz = f32_toward_zero(a.z);
+        const unsigned mk =
+            morton9(octree_coord(px, iwx), octree_coord(py, iwy), octree_coord(pz, iwz));
         const long long K = on ? (((long long)mk << 32) | (long long)o) : LLONG_MAX;
-        unsigned rank = 0;
-        for (int q = 0; q < m; ++q) rank += (__shfl_sync(full, K, q) < K) ? 1u : 0u;
-        unsigned left = __ballot_sync(full, on);
+        int rank = 0;
+        for (int q = 0; q < m; ++q) rank += (__shfl_sync(full, K, q) < K) ? 1 : 0;
+        // lane r takes the atom of rank r
+        if (on) lane_of[rank] = lane;
+        __syncwarp();
+        const int from = on ? lane_of[lane] : lane;
+        __syncwarp();
+        o = __shfl_sync(full, o, from);
+        sv = __shfl_sync(full, sv, from);
+        px = __shfl_sync(full, px, from);
+        py = __shfl_sync(full, py, from);
+        pz = __shfl_sync(full, pz, from);
+        unsigned left = (m == 32) ? full : ((1u << m) - 1u);
         int dst = 0, next = 0;
         while (__popc(left) >= 2) {
-            const bool mine = (left >> lane) & 1u;
-            const unsigned r = mine ? rank : full;
-            const int first = __ffs(__ballot_sync(full, r == __reduce_min_sync(full, r))) - 1;
+            const int first = __ffs(left) - 1;
             const float fx = __shfl_sync(full, px, first), fy = __shfl_sync(full, py, first),
                         fz = __shfl_sync(full, pz, first);
             // atoms of one cell need no periodic image
             const float dx = __fsub_rn(px, fx), dy = __fsub_rn(py, fy), dz = __fsub_rn(pz, fz);
             const float d2 =
                 __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-            const unsigned k2 = (mine && lane != first) ? ((__float_as_uint(d2) & ~31u) | rank)
-                                                        : full;
-            const int mate = __ffs(__ballot_sync(full, k2 == __reduce_min_sync(full, k2))) - 1;
+            const bool cand = ((left >> lane) & 1u) && lane != first;
+            const unsigned k2 = cand ? ((__float_as_uint(d2) & ~31u) | (unsigned)lane) : full;
+            const int mate = (int)(__reduce_min_sync(full, k2) & 31u);
             if (lane == first) dst = next;
             if (lane == mate) dst = next + 1;
             next += 2;

@@ -255,16 +255,27 @@ def _morton9(q):
     return k
 
 
+def f32_toward_zero(x):
+    """float64 -> float32 rounded toward zero (positions are >= 0)."""
+    b = np.ascontiguousarray(x, dtype=np.float64).view(np.uint64)
+    hi = (b >> np.uint64(32)).astype(np.uint32)
+    lo = (b & np.uint64(0xffffffff)).astype(np.uint32)
+    e = ((hi >> np.uint32(20)) & np.uint32(0x7ff)).astype(np.int64) - 1023 + 127
+    m = ((hi & np.uint32(0xfffff)) << np.uint32(3)) | (lo >> np.uint32(29))
+    bits = (hi & np.uint32(0x80000000)) | (np.clip(e, 0, 255).astype(np.uint32) << np.uint32(23)) | m
+    return np.where(e <= 0, np.uint32(0), bits).astype(np.uint32).view(np.float32)
+
+
 def pairing_model(pos, start, order, inv_w, spatial):
     """Slots of the two-atom layout as (a, b) original ids, cell by cell.
     spatial=False: the cell's atoms in original-id order, two at a time.
     spatial=True: ranked by the Morton code of their position at 1/8 of the
     cell width (ties by id); the first unpaired atom in rank takes the nearest
     unpaired atom (squared distance, low 5 bits dropped, ties by rank); an
-    odd cell ends with the atom left over.  Positions, widths and distances
-    in float32, rounded operation by operation."""
+    odd cell ends with the atom left over.  Positions (rounded toward zero),
+    widths and distances in float32, rounded operation by operation."""
     slots = []
-    p32 = pos.astype(np.float32)
+    p32 = f32_toward_zero(pos)
     w32 = np.asarray(inv_w).astype(np.float32)
     for c in range(len(start) - 1):
         atoms = order[start[c]:start[c + 1]]
