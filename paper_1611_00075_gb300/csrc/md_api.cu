@@ -237,9 +237,12 @@ cudaError_t mark(md_system *h, int kind) {
     return cudaEventRecord(h->ev_pool[h->ev_used++], h->stream);
 }
 
-// after a synchronize: accumulate intervals ev[k-1] -> ev[k] by the kind of ev[k]
-void harvest(md_system *h) {
-    for (size_t k = 1; k < h->ev_used; ++k) {
+// after a synchronize: accumulate intervals ev[k-1] -> ev[k] by the kind of
+// ev[k], for the first `upto` events (all of them by default); the rest are
+// dropped
+void harvest(md_system *h, size_t upto = SIZE_MAX) {
+    const size_t used = std::min(upto, h->ev_used);
+    for (size_t k = 1; k < used; ++k) {
         float ms = 0.f;
         if (h->ev_kind[k] >= 0 && cudaEventElapsedTime(&ms, h->ev_pool[k - 1], h->ev_pool[k]) == cudaSuccess) {
             h->ms_kind[h->ev_kind[k]] += ms;
@@ -487,16 +490,20 @@ md_status forces_now(md_system *h, bool energy) {
     }
     md_status st = enqueue_rebuild(h, true);
     if (st != MD_OK) return st;
+    const size_t ev_rebuilt = h->ev_used;  // through the rebuild's mark
     st = enqueue_forces(h, FM_STORE, energy, true);
     if (st != MD_OK) return st;
     st = read_status(h);
     if (st != MD_OK) return st;
     if (h->ds_host->status == MD_ERR_LIST_OVERFLOW) {
-        // the gated rebuild overflowed: repair on the host and evaluate again
+        // the gated rebuild overflowed, so the force launch did nothing:
+        // repair on the host (timed as one more rebuild) and evaluate again
+        if (h->timing) h->ev_used = ev_rebuilt;
         st = clear_status(h);
         if (st != MD_OK) return st;
         st = rebuild_now(h, true);
         if (st != MD_OK) return st;
+        MD_CK(mark(h, K_REBUILD));
         st = enqueue_forces(h, FM_STORE, energy, true);
         if (st != MD_OK) return st;
         st = read_status(h);
@@ -1041,10 +1048,15 @@ md_status md_step(md_system *h, int64_t nsteps) {
     MD_CK(mark(h, K_INTEGRATE));
     h->forces_valid = false;
     int64_t sr = 1;
+    // under timing, the first event of every step (its rebuild mark), so that
+    // the launches a list overflow turns into no-ops are not counted
+    std::vector<size_t> ev_at;
+    if (h->timing) ev_at.assign((size_t)nsteps + 1, 0);
     for (int attempt = 0; attempt < 64; ++attempt) {
         for (int64_t s = sr; s <= nsteps; ++s) {
             h->steps_total = base + s;
             h->cur = c0 ^ (int)((s - 1) & 1);
+            if (h->timing) ev_at[s] = h->ev_used;
             if (s < nsteps) {
                 st = enqueue_full_step(h);
                 if (st != MD_OK) return st;
@@ -1058,8 +1070,14 @@ md_status md_step(md_system *h, int64_t nsteps) {
         h->cur = c0 ^ (int)((nsteps - 1) & 1);
         st = read_status(h);
         if (st != MD_OK) return st;
-        if (h->timing) harvest(h);
         const int dst = h->ds_host->status;
+        if (h->timing) {
+            // an overflow in the rebuild before step S stops every later kernel:
+            // keep the intervals up to that rebuild, drop the no-op launches
+            const int64_t S = (int64_t)h->ds_host->steps_done - base + 1;
+            harvest(h, (dst == MD_ERR_LIST_OVERFLOW && S >= 1 && S <= nsteps) ? ev_at[S] + 1
+                                                                               : SIZE_MAX);
+        }
         if (dst == 0) {
             h->steps_total = base + nsteps;
             h->forces_valid = true;
@@ -1081,6 +1099,7 @@ md_status md_step(md_system *h, int64_t nsteps) {
         if (st != MD_OK) return st;
         if (h->p.max_neighbors > 0)
             return fail(h, MD_ERR_LIST_OVERFLOW, "md_step: neighbour count exceeds max_neighbors");
+        MD_CK(mark(h, -1));  // the repair is timed as one more rebuild
         if (h->p.force_variant == MD_FORCE_PAIRED) {
             st = pair_rebuild_now(h);
             if (st != MD_OK) return st;
@@ -1093,11 +1112,13 @@ md_status md_step(md_system *h, int64_t nsteps) {
         st = enqueue_sched_prep(h, false);
         if (st != MD_OK) return st;
         MD_CK(launch_finish_rebuild(h, false));
+        MD_CK(mark(h, K_REBUILD));
         sr = S;
         // re-enqueue steps S..nsteps; the loop's first rebuild is gated off
         for (int64_t s = sr; s <= nsteps; ++s) {
             h->steps_total = base + s;
             h->cur = c0 ^ (int)((s - 1) & 1);
+            if (h->timing) ev_at[s] = h->ev_used;
             if (s > sr) {
                 st = enqueue_rebuild(h, true);
                 if (st != MD_OK) return st;

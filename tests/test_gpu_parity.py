@@ -379,6 +379,44 @@ def test_mixed_energy_tracks_fp64(md):
     assert abs(E[1] - E[0]) < 1e-4 * abs(E[0])
 
 
+
+@pytest.mark.parametrize("stream", ["default", "own"])
+@pytest.mark.parametrize("variant", ["full", "paired"])
+def test_timing_skips_launches_a_list_overflow_voids(md, stream, variant):
+    """A list that overflows in a rebuild inside md_step stops every later
+    launch of the call until the host has grown it and enqueued the steps
+    again.  Per-launch timing counts the work that ran: one force launch per
+    step however many repairs there were, the repairs as rebuilds.  A dilute
+    lattice (spacing 2) is compressed by an inward velocity field, so the
+    neighbour counts outgrow the list's headroom within a few steps."""
+    nc = 12
+    side = 2.0
+    g = np.stack(np.meshgrid(*[np.arange(nc)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    box = np.full(3, nc * side)
+    pos = (g + 0.5) * side
+    vel = -8.0 * (pos - box / 2)
+    fv = md.MD_FORCE_PAIRED if variant == "paired" else md.MD_FORCE_FULL
+    st = torch.cuda.default_stream() if stream == "default" else torch.cuda.Stream()
+    with torch.cuda.stream(st), md.System(pos, vel, box, precision="mixed", stream=st,
+                                          force_variant=fv) as a:
+        md.md_forces(a.h)
+        s0 = a.stats()
+        nsteps = 8
+        md.md_set_timing(a.h, True)
+        a.step(nsteps)
+        s1 = a.stats()
+        md.md_set_timing(a.h, False)
+    grew = (s1["slots"] and s1["slot_max"] > s0["slot_max"]) or s1["cap"] > s0["cap"]
+    print("%s/%s: builds %d -> %d, counts %s, ms %s" % (variant, stream, s0["builds"],
+          s1["builds"], s1["count"], {k: round(v, 3) for k, v in s1["ms"].items()}))
+    assert grew
+    assert s1["count"]["force"] == nsteps
+    assert s1["count"]["integrate"] == 1
+    # one rebuild mark per step, plus one per host repair (at least one)
+    assert s1["count"]["rebuild"] > nsteps
+    assert s1["count"]["rebuild"] - nsteps <= s1["builds"] - s0["builds"]
+
+
 # ------------------------------------------------------------------ errors
 
 def test_invalid_arguments(md):
