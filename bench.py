@@ -287,9 +287,10 @@ def run_gpu(args, rank, world, local):
         args.scheduler = "grid"  # the persistent schedulers drive the Lennard-Jones kernel
     sched = {"grid": md.MD_SCHED_GRID, "paircount": md.MD_SCHED_PAIRCOUNT,
              "mlp": md.MD_SCHED_MLP, "dynamic": md.MD_SCHED_DYNAMIC}[args.scheduler]
-    # the two-atom layout serves one-species Lennard-Jones of one box
+    # the two-atom layout serves one-species Lennard-Jones (batches under the
+    # hardware block scheduler)
     paired = (args.force_variant == "paired" and kw["potential"] == "lj" and
-              "species" not in kw and not ensemble)
+              "species" not in kw and (not ensemble or args.scheduler == "grid"))
     fv = md.MD_FORCE_PAIRED if paired else md.MD_FORCE_FULL
     kw["force_variant"] = fv
 
@@ -358,9 +359,9 @@ def run_gpu(args, rank, world, local):
         if ensemble:
             s0 = mixed.state()[:2]
 
-            def batch_from_s0(code):
+            def batch_from_s0(code, variant):
                 md.md_set_state(mixed.h, s0[0], s0[1])
-                md.md_set_variant(mixed.h, md.MD_FORCE_FULL, code)
+                md.md_set_variant(mixed.h, variant, code)
                 md.md_forces(mixed.h)
                 torch.cuda.synchronize()
 
@@ -369,8 +370,11 @@ def run_gpu(args, rank, world, local):
                                                                  args.compare_steps, args.warmup)
                 # the batch from the same state under each scheduler it supports,
                 # plain device time (graphs on)
-                for name, code in (("grid", md.MD_SCHED_GRID), ("dynamic", md.MD_SCHED_DYNAMIC)):
-                    batch_from_s0(code)
+                legs = [("grid", md.MD_SCHED_GRID, md.MD_FORCE_FULL),
+                        ("dynamic", md.MD_SCHED_DYNAMIC, md.MD_FORCE_FULL),
+                        ("paired_grid", md.MD_SCHED_GRID, md.MD_FORCE_PAIRED)]
+                for name, code, variant in legs:
+                    batch_from_s0(code, variant)
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
@@ -379,8 +383,10 @@ def run_gpu(args, rank, world, local):
                     torch.cuda.synchronize()
                     sched_info["batched_graphs_" + name] = {
                         "atom_steps_per_s": mixed.n * args.compare_steps / (e0.elapsed_time(e1) * 1e-3),
-                        "steps": args.compare_steps}
-            batch_from_s0(sched)
+                        "steps": args.compare_steps,
+                        "layout": "two atoms per thread" if variant == md.MD_FORCE_PAIRED
+                        else "per-atom lists"}
+            batch_from_s0(sched, fv)
         elif kw["potential"] == "lj" and "species" not in kw:
             # the learned part first: per-cell clock64 timings of this state,
             # then the network trained on the GPU

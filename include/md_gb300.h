@@ -67,9 +67,10 @@ enum { MD_FP64 = 0, MD_MIXED = 1 };
  * neighbour position serves two pair evaluations.  The full pair set, the
  * same forces as MD_FORCE_FULL up to float32 rounding.  Its rebuilds make the
  * slot lists only; md_get_neighbors builds per-atom rows on demand from the
- * positions of the last build.  Mixed-precision one-species Lennard-Jones
- * of one box, under any scheduler (the persistent kernel then takes tiles of
- * 32 slots).  MD_FORCE_CLUSTER is a measured alternative (slower on GB300);
+ * positions of the last build.  Mixed-precision one-species Lennard-Jones:
+ * one box under any scheduler (the persistent kernel then takes tiles of 32
+ * slots), or a batch (md_create_batch) under MD_SCHED_GRID, each slot with
+ * its box's geometry.  MD_FORCE_CLUSTER is a measured alternative (slower on GB300);
  * MD_FORCE_PAIRED is faster than the per-atom list on large systems. */
 enum { MD_FORCE_FULL = 0, MD_FORCE_HALF_COLOR = 1, MD_FORCE_HALF_ATOMIC = 2,
        MD_FORCE_CLUSTER = 3, MD_FORCE_PAIRED = 4 };
@@ -186,7 +187,8 @@ md_status md_create_typed(md_system **out, const md_params *p, const md_lj_types
  * n_each).  Every step of the path runs as one launch over all replicas (the
  * cells of all boxes are numbered consecutively), so small replicas do not
  * pay one launch each.  Batches run mixed-precision Lennard-Jones with full
- * lists under MD_SCHED_GRID or MD_SCHED_DYNAMIC; the list is rebuilt for all
+ * lists under MD_SCHED_GRID or MD_SCHED_DYNAMIC, or two atoms per thread
+ * (MD_FORCE_PAIRED) under MD_SCHED_GRID; the list is rebuilt for all
  * replicas when any replica needs it.  All other calls work on the whole
  * batch (original order = the concatenation); md_get_cells reports global
  * cell ids (replica r's cells follow those of replicas 0..r-1, each box in

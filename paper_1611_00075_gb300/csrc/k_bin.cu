@@ -219,15 +219,13 @@ __device__ __forceinline__ float f32_toward_zero(double d) {
 // original-id order.
 __global__ void __launch_bounds__(kSortBlock)
 cell_pair_order_kernel(int ncells, const Grid *__restrict__ grids,
-                       const int32_t *__restrict__ start, const double4 *__restrict__ tabs,
-                       int32_t *__restrict__ key, int32_t *__restrict__ src, const DevStatus *ds,
-                       bool gated) {
+                       const uint16_t *__restrict__ rep, const int32_t *__restrict__ start,
+                       const double4 *__restrict__ tabs, int32_t *__restrict__ key,
+                       int32_t *__restrict__ src, const DevStatus *ds, bool gated) {
     if (chain_off(ds, gated)) return;
     constexpr unsigned full = 0xffffffffu;
     __shared__ int s_lane_of[kSortBlock / 32][32];
     int *lane_of = s_lane_of[threadIdx.x >> 5];
-    const float iwx = (float)grids[0].inv_w[0], iwy = (float)grids[0].inv_w[1],
-                iwz = (float)grids[0].inv_w[2];
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * (kSortBlock / 32);
     for (int c = blockIdx.x * (kSortBlock / 32) + (threadIdx.x >> 5); c < ncells; c += nw) {
@@ -242,6 +240,9 @@ cell_pair_order_kernel(int ncells, const Grid *__restrict__ grids,
         int sv = on ? src[b + lane] : 0;
         const double4 a = on ? tabs[sv] : make_double4(0.0, 0.0, 0.0, 0.0);
         float px = f32_toward_zero(a.x), py = f32_toward_zero(a.y), pz = f32_toward_zero(a.z);
+        // the cell's box (a cell's atoms share it; lane 0 always holds one)
+        const Grid &g = grids[rep ? __shfl_sync(full, (int)rep[sv], 0) : 0];
+        const float iwx = g.inv_wf[0], iwy = g.inv_wf[1], iwz = g.inv_wf[2];
         const unsigned mk =
             morton9(octree_coord(px, iwx), octree_coord(py, iwy), octree_coord(pz, iwz));
         const long long K = on ? (((long long)mk << 32) | (long long)o) : LLONG_MAX;
@@ -357,7 +358,8 @@ cudaError_t launch_bin(md_system *h, bool gated) {
                                      kGridCap * 2);
     if (h->p.force_variant == MD_FORCE_PAIRED)
         cell_pair_order_kernel<<<std::max(sort_blocks, 1), kSortBlock, 0, s>>>(
-            h->g.ncells, h->grids, h->cell_start, h->tmp_abs, h->key, h->src, h->ds, gated);
+            h->g.ncells, h->grids, h->rep, h->cell_start, h->tmp_abs, h->key, h->src, h->ds,
+            gated);
     else
         cell_sort_kernel<<<std::max(sort_blocks, 1), kSortBlock, 0, s>>>(
             h->g.ncells, h->cell_start, h->key, h->src, h->ds, gated);

@@ -108,9 +108,12 @@ __device__ __forceinline__ int scan_cell(int cnt, int b, int e, const float4 *__
 // 3.93 ms at eight and 4.16 ms at nine; the candidate loop unrolled by 4
 // against 4.13 ms by 2 and 4.30 ms by 8 (at eight CTAs).  Packed f32x2
 // distances for the two atoms were slower (4.98 against 4.45 ms).
-template <bool WRITE>
+// MULTI (a batch of boxes): each slot takes the geometry of its atoms' box
+// (cells numbered box after box from the box's cell0).
+template <bool WRITE, bool MULTI = false>
 __global__ void __launch_bounds__(kPairBlock, 7)
-pair_list_kernel(int n, Grid g, float hi, const float4 *__restrict__ xq,
+pair_list_kernel(int n, Grid g, const Grid *__restrict__ grids, const uint16_t *__restrict__ rep,
+                 float hi, const float4 *__restrict__ xq,
                  const int32_t *__restrict__ cell, const int32_t *__restrict__ start,
                  const int32_t *__restrict__ slot_start, const uint32_t *__restrict__ slot_atom,
                  uint32_t *__restrict__ list, int32_t *__restrict__ count, int cap, DevStatus *ds,
@@ -120,7 +123,6 @@ pair_list_kernel(int n, Grid g, float hi, const float4 *__restrict__ xq,
     if (blockIdx.x == 0 && threadIdx.x == 0) ds->pair_slots = nslots;
     unsigned long long tot = 0;
     int overflow = 0, maxc = 0;
-    const float wx = (float)g.w[0], wy = (float)g.w[1], wz = (float)g.w[2];
     const uint32_t pad = (kHomeStencil << kIndexBits) | (uint32_t)n;
     // grid-stride over whole warps, so every lane reaches the reductions below
     const int stride = gridDim.x * blockDim.x;
@@ -135,17 +137,24 @@ pair_list_kernel(int n, Grid g, float hi, const float4 *__restrict__ xq,
                         uz = 0.5f * (q1.z - q0.z);
             const float mx = q0.x + ux, my = q0.y + uy, mz = q0.z + uz;
             const float lim = hi - (ux * ux + uy * uy + uz * uz);
-            const int c = cell[i0];
-            const int cx = c % g.nx, cy = (c / g.nx) % g.ny, cz = c / (g.nx * g.ny);
+            int nx = g.nx, ny = g.ny, nz = g.nz, c0 = 0;
+            float wx = g.wf[0], wy = g.wf[1], wz = g.wf[2];
+            if (MULTI) {
+                const Grid &gb = grids[rep[i0]];
+                nx = gb.nx; ny = gb.ny; nz = gb.nz; c0 = gb.cell0;
+                wx = gb.wf[0]; wy = gb.wf[1]; wz = gb.wf[2];
+            }
+            const int c = cell[i0] - c0;
+            const int cx = c % nx, cy = (c / nx) % ny, cz = c / (nx * ny);
             uint32_t *row = list + list_group(s, cap) + ((s & 31) << 2);
             int cnt = 0;
             for (int dz = -1; dz <= 1; ++dz) {
-                const int zz = (cz + dz + g.nz) % g.nz;
+                const int zz = (cz + dz + nz) % nz;
                 for (int dy = -1; dy <= 1; ++dy) {
-                    const int yy = (cy + dy + g.ny) % g.ny;
+                    const int yy = (cy + dy + ny) % ny;
                     for (int dx = -1; dx <= 1; ++dx) {
-                        const int xx = (cx + dx + g.nx) % g.nx;
-                        const int cn = (zz * g.ny + yy) * g.nx + xx;
+                        const int xx = (cx + dx + nx) % nx;
+                        const int cn = c0 + (zz * ny + yy) * nx + xx;
                         const uint32_t st = (uint32_t)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
                         // the midpoint moved against the cell shift
                         const float sx = mx - (float)dx * wx, sy = my - (float)dy * wy,
@@ -200,16 +209,49 @@ __global__ void pair_dummy_kernel(float4 *xq0, float4 *xq1, int n) {
 // the first's); with float64 chunk accumulators at 72 registers (7 CTAs)
 // 1.498 ms unpacked and 1.551 ms packed (latency-bound).  At 1 M atoms the
 // two layouts tie (porous) or the per-atom kernel leads by 2 % (liquid).
-template <int MODE, bool ENERGY>
+//
+// MULTI (a batch of boxes): a block's slots are consecutive, so their atoms
+// belong to one or two boxes (more only when a box holds fewer slots than a
+// block); the shift tables of those boxes go to shared memory like a single
+// box's, and a block that spans more boxes reads the global R x 27 table.
+template <int MODE, bool ENERGY, bool MULTI = false>
 __global__ void __launch_bounds__(kPairBlock, 9) lj_pair_kernel(ForceArgs a, PairArgs p,
                                                                 int store_f) {
-    __shared__ ShiftTab sh;
-    load_shifts_f32(a.g, &sh);
+    __shared__ ShiftTab sh[MULTI ? 2 : 1];
+    __shared__ int s_r0, s_span;
+    const int nslots = p.slot_start[p.ncells];
+    if (!MULTI) {
+        load_shifts_f32(a.g, &sh[0]);
+    } else {
+        const int sb = blockIdx.x * blockDim.x;
+        const int se = min(nslots, sb + (int)blockDim.x) - 1;
+        const int r0 = sb <= se ? (int)a.rep[p.slot_atom[sb] & ~kSingle] : 0;
+        const int r1 = sb <= se ? (int)a.rep[p.slot_atom[se] & ~kSingle] : 0;
+        if (threadIdx.x < 2 * kStencil) {
+            const int t = threadIdx.x / kStencil, st = threadIdx.x % kStencil;
+            if (t <= r1 - r0) {
+                const float4 v = a.shifts32[kStencil * (r0 + t) + st];
+                sh[t].x[st] = v.x;
+                sh[t].y[st] = v.y;
+                sh[t].z[st] = v.z;
+            }
+        }
+        if (threadIdx.x == 0) {
+            s_r0 = r0;
+            s_span = r1 - r0;
+        }
+    }
     __syncthreads();
     if (a.ds->status != 0) return;
     step_bookkeeping<MODE>(a);
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < p.slot_start[p.ncells]) lj_pair_slot<MODE, ENERGY>(a, p, &sh, s, store_f);
+    if (s >= nslots) return;
+    if (MULTI && s_span <= 1) {
+        const int r = (int)a.rep[p.slot_atom[s] & ~kSingle];
+        lj_pair_slot<MODE, ENERGY, false>(a, p, &sh[r - s_r0], s, store_f);
+    } else {
+        lj_pair_slot<MODE, ENERGY, MULTI>(a, p, &sh[0], s, store_f);
+    }
 }
 
 }  // namespace
@@ -232,14 +274,18 @@ cudaError_t launch_pair_build(md_system *h, bool write, bool gated) {
     pair_reset_kernel<<<1, 1, 0, s>>>(h->ds, gated);
     const int64_t smax = pair_slots_max(h->n, nc);
     const int blocks = (int)std::min<int64_t>((smax + kPairBlock - 1) / kPairBlock, 152 * 16);
-    if (write)
-        pair_list_kernel<true><<<blocks, kPairBlock, 0, s>>>(
-            n, h->g, h->list_hi, h->xq[h->cur], h->cell, h->cell_start, h->ps_start, h->ps_atom,
-            h->ps_list, h->ps_count, h->ps_cap, h->ds, gated);
-    else
-        pair_list_kernel<false><<<blocks, kPairBlock, 0, s>>>(
-            n, h->g, h->list_hi, h->xq[h->cur], h->cell, h->cell_start, h->ps_start, h->ps_atom,
-            h->ps_list, h->ps_count, h->ps_cap, h->ds, gated);
+#define MDG_PAIR_LIST(W, M)                                                                  \
+    pair_list_kernel<W, M><<<blocks, kPairBlock, 0, s>>>(                                    \
+        n, h->g, h->grids, h->rep, h->list_hi, h->xq[h->cur], h->cell, h->cell_start,        \
+        h->ps_start, h->ps_atom, h->ps_list, h->ps_count, h->ps_cap, h->ds, gated)
+    if (h->R > 1) {
+        if (write) MDG_PAIR_LIST(true, true);
+        else MDG_PAIR_LIST(false, true);
+    } else {
+        if (write) MDG_PAIR_LIST(true, false);
+        else MDG_PAIR_LIST(false, false);
+    }
+#undef MDG_PAIR_LIST
     return cudaGetLastError();
 }
 
@@ -255,11 +301,17 @@ cudaError_t launch_pair_forces(md_system *h, int mode, bool energy, bool store_f
     const int sf = store_f ? 1 : 0;
     const int64_t smax = pair_slots_max(h->n, h->g.ncells);
     const int blocks = (int)((smax + kPairBlock - 1) / kPairBlock);
+    const bool multi = h->R > 1;
     cudaStream_t s = h->stream;
-#define MDG_PAIR(M)                                                                   \
-    do {                                                                              \
-        if (energy) lj_pair_kernel<M, true><<<blocks, kPairBlock, 0, s>>>(a, p, sf);  \
-        else lj_pair_kernel<M, false><<<blocks, kPairBlock, 0, s>>>(a, p, sf);        \
+#define MDG_PAIR(M)                                                                         \
+    do {                                                                                    \
+        if (multi) {                                                                        \
+            if (energy) lj_pair_kernel<M, true, true><<<blocks, kPairBlock, 0, s>>>(a, p, sf); \
+            else lj_pair_kernel<M, false, true><<<blocks, kPairBlock, 0, s>>>(a, p, sf);       \
+        } else {                                                                            \
+            if (energy) lj_pair_kernel<M, true><<<blocks, kPairBlock, 0, s>>>(a, p, sf);    \
+            else lj_pair_kernel<M, false><<<blocks, kPairBlock, 0, s>>>(a, p, sf);          \
+        }                                                                                   \
     } while (0)
     switch (mode) {
         case FM_STORE: MDG_PAIR(FM_STORE); break;

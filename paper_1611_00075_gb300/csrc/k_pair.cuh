@@ -82,11 +82,14 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 }
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
 
-template <int MODE, bool ENERGY>
+// MULTI (a batch of boxes, the block's boxes not all in shared memory): the
+// stencil shifts come from the slot's box's row of the global R x 27 table.
+template <int MODE, bool ENERGY, bool MULTI = false>
 __device__ __forceinline__ void lj_pair_slot(const ForceArgs &a, const PairArgs &p,
                                              const ShiftTab *sh, int s, int store_f) {
     const uint32_t sa = p.slot_atom[s];
     const int i0 = (int)(sa & ~kSingle);
+    const float4 *shr = MULTI ? a.shifts32 + kStencil * (int)a.rep[i0] : nullptr;
     const bool two = !(sa & kSingle);
     const float4 q0 = a.xq[i0];
     // a one-atom slot puts its second atom at the dummy's distance
@@ -121,7 +124,8 @@ __device__ __forceinline__ void lj_pair_slot(const ForceArgs &a, const PairArgs 
     auto pair = [&](uint32_t ent) {
         const float4 qj = __ldg(a.xq + (ent & kIndexMask));
         const uint32_t st = ent >> kIndexBits;
-        const float tx = qj.x + sh->x[st], ty = qj.y + sh->y[st], tz = qj.z + sh->z[st];
+        const float4 sf = MULTI ? __ldg(shr + st) : make_float4(sh->x[st], sh->y[st], sh->z[st], 0.f);
+        const float tx = qj.x + sf.x, ty = qj.y + sf.y, tz = qj.z + sf.z;
         const float2 dx = add2(dup2(tx), nqx), dy = add2(dup2(ty), nqy), dz = add2(dup2(tz), nqz);
         const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
         const float2 r2i = make_float2(__fdividef(1.0f, r2.x), __fdividef(1.0f, r2.y));

@@ -784,8 +784,8 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
             return fail(nullptr, MD_ERR_INVALID,
                         W + ": multi-element systems run full lists under MD_SCHED_GRID");
     }
-    if (p->force_variant == MD_FORCE_PAIRED && (R != 1 || ltypes))
-        return fail(nullptr, MD_ERR_INVALID, W + ": two atoms per thread run one one-species box");
+    if (p->force_variant == MD_FORCE_PAIRED && ltypes)
+        return fail(nullptr, MD_ERR_INVALID, W + ": two atoms per thread run one species");
     if (p->force_variant == MD_FORCE_CLUSTER &&
         (R != 1 || p->scheduler != MD_SCHED_GRID || ltypes || n >= ((int64_t)1 << 25)))
         return fail(nullptr, MD_ERR_INVALID,
@@ -798,11 +798,13 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
         return fail(nullptr, MD_ERR_INVALID,
                     W + ": the cluster and two-atom layouts are built for the mixed path");
     if (R > 1 && (p->potential != MD_POT_LJ || p->precision != MD_MIXED ||
-                  p->force_variant != MD_FORCE_FULL ||
-                  (p->scheduler != MD_SCHED_GRID && p->scheduler != MD_SCHED_DYNAMIC)))
+                  (p->force_variant == MD_FORCE_FULL
+                       ? (p->scheduler != MD_SCHED_GRID && p->scheduler != MD_SCHED_DYNAMIC)
+                       : (p->force_variant != MD_FORCE_PAIRED || p->scheduler != MD_SCHED_GRID))))
         return fail(nullptr, MD_ERR_INVALID,
                     W + ": batches run mixed-precision Lennard-Jones with full lists under "
-                        "MD_SCHED_GRID or MD_SCHED_DYNAMIC");
+                        "MD_SCHED_GRID or MD_SCHED_DYNAMIC, or two atoms per thread under "
+                        "MD_SCHED_GRID");
     h = new (std::nothrow) md_system();
     if (!h) return fail(nullptr, MD_ERR_OOM, W + ": host allocation failed");
     h->p = *p;
@@ -825,6 +827,8 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
             g.L[d] = boxes[3 * r + d];
             g.w[d] = boxes[3 * r + d] / nc[d];
             g.inv_w[d] = (double)nc[d] / boxes[3 * r + d];
+            g.wf[d] = (float)g.w[d];
+            g.inv_wf[d] = (float)g.inv_w[d];
         }
         g.nx = nc[0]; g.ny = nc[1]; g.nz = nc[2];
         g.ncells = nc[0] * nc[1] * nc[2];
@@ -1261,10 +1265,12 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
         h->p.precision != MD_MIXED)
         return fail(h, MD_ERR_INVALID,
                     "md_set_variant: the cluster and two-atom layouts are built for the mixed path");
-    if (h->R > 1 && (force_variant != MD_FORCE_FULL ||
-                     (scheduler != MD_SCHED_GRID && scheduler != MD_SCHED_DYNAMIC)))
+    if (h->R > 1 && (force_variant == MD_FORCE_FULL
+                         ? (scheduler != MD_SCHED_GRID && scheduler != MD_SCHED_DYNAMIC)
+                         : (force_variant != MD_FORCE_PAIRED || scheduler != MD_SCHED_GRID)))
         return fail(h, MD_ERR_INVALID,
-                    "md_set_variant: batches run full lists under MD_SCHED_GRID or MD_SCHED_DYNAMIC");
+                    "md_set_variant: batches run full lists under MD_SCHED_GRID or "
+                    "MD_SCHED_DYNAMIC, or two atoms per thread under MD_SCHED_GRID");
     if (force_variant == MD_FORCE_CLUSTER &&
         (scheduler != MD_SCHED_GRID || h->n >= ((int64_t)1 << 25)))
         return fail(h, MD_ERR_INVALID,

@@ -111,6 +111,8 @@ struct Grid {
     double L[3];
     double w[3];        // cell widths L / n
     double inv_w[3];    // n / L
+    float wf[3];        // w and inv_w rounded to float32 (the two-atom layout's
+    float inv_wf[3];    // float32 list build and pairing order)
     const double *ctab; // cell centres (c + 0.5) w: nx for x, then ny for y, then nz for z
 };
 

@@ -64,14 +64,21 @@ def near_cutoff(pos, box, off, ids, rc, delta):
     return bad
 
 
+def variant_code(md, variant):
+    return md.MD_FORCE_PAIRED if variant == "paired" else md.MD_FORCE_FULL
+
+
+@pytest.mark.parametrize("variant", ["full", "paired"])
 @pytest.mark.parametrize("which", ["uneven", "tiny_and_large"])
-def test_batch_cells_lists_forces_match_oracle(md, orc, which):
+def test_batch_cells_lists_forces_match_oracle(md, orc, which, variant):
     """Cells and lists bit-exact, forces and energies within the mixed bars,
-    per replica.  With tiny replicas a block of the force kernel spans more
-    than two boxes and reads the global shift table; otherwise the shift
-    tables of its (at most two) boxes sit in shared memory."""
+    per replica, with per-atom lists and with two atoms per thread (each box's
+    cells in the pairing order, slot lists built with the box's geometry).
+    With tiny replicas a block of the force kernel spans more than two boxes
+    and reads the global shift table; otherwise the shift tables of its (at
+    most two) boxes sit in shared memory."""
     reps = ensemble() if which == "uneven" else tiny_and_large()
-    with md.Batch(reps, precision="mixed") as b:
+    with md.Batch(reps, precision="mixed", force_variant=variant_code(md, variant)) as b:
         nc, cell_of, start = b.cells()
         off, ids = b.neighbors()
         _, _, f = b.state()
@@ -103,23 +110,26 @@ def test_batch_cells_lists_forces_match_oracle(md, orc, which):
     assert len(start) == cell0 + 1
 
 
-def test_batch_dynamics_equal_separate_systems(md):
+@pytest.mark.parametrize("variant", ["full", "paired"])
+def test_batch_dynamics_equal_separate_systems(md, variant):
     """Before the first rebuild a replica in a batch runs exactly the
-    arithmetic it runs alone (same cells, same list order): bit-equal.  Later
+    arithmetic it runs alone (same cells, same list order, and with two atoms
+    per thread the same slots): bit-equal.  Later
     the batch rebuilds every replica whenever one of them needs it; a rebuild
     moves atoms to new cells and changes the float32 rounding of their
     cell-relative coordinates, so the trajectories then separate at the rate
     of the dynamics' own chaos, far below any cross-talk between replicas."""
     reps = ensemble()
+    fv = variant_code(md, variant)
     for nsteps, tol in ((3, 0.0), (60, 1e-4)):
         sep = []
         for pos, vel, box in reps:
-            with md.System(pos, vel, box, precision="mixed") as a:
+            with md.System(pos, vel, box, precision="mixed", force_variant=fv) as a:
                 b0 = a.stats()["builds"]
                 a.step(nsteps)
                 sep.append((a.state()[0].cpu().numpy(), sum(a.energy()),
                             a.stats()["builds"] - b0))
-        with md.Batch(reps, precision="mixed") as b:
+        with md.Batch(reps, precision="mixed", force_variant=fv) as b:
             b0 = b.stats()["builds"]
             b.step(nsteps)
             pos = b.state()[0].cpu().numpy()
@@ -134,9 +144,12 @@ def test_batch_dynamics_equal_separate_systems(md):
             assert abs(ke[r] + pe[r] - sep[r][1]) <= max(tol, 1e-12) * abs(sep[r][1]), (nsteps, r)
 
 
-def test_batch_energy_tracks_oracle(md, orc):
+@pytest.mark.parametrize("variant", ["full", "paired"])
+def test_batch_energy_tracks_oracle(md, orc, variant):
     reps = ensemble(3)
-    with md.Batch(reps, precision="mixed", scheduler=md.MD_SCHED_DYNAMIC) as b:
+    sched = md.MD_SCHED_DYNAMIC if variant == "full" else md.MD_SCHED_GRID
+    with md.Batch(reps, precision="mixed", scheduler=sched,
+                  force_variant=variant_code(md, variant)) as b:
         b.step(40)
         ke, pe = b.energies()
     p = orc.make_params(potential=orc.POT_LJ, dt=0.005)
@@ -151,9 +164,13 @@ def test_batch_rejects_unsupported_modes(md):
         md.Batch(reps, precision="fp64")
     with pytest.raises(md.MDError):
         md.Batch(reps, scheduler=md.MD_SCHED_MLP)
+    with pytest.raises(md.MDError):  # two atoms per thread: the grid launch only
+        md.Batch(reps, force_variant=md.MD_FORCE_PAIRED, scheduler=md.MD_SCHED_DYNAMIC)
     with md.Batch(reps) as b:
         with pytest.raises(md.MDError):
             md.md_set_variant(b.h, md.MD_FORCE_HALF_COLOR, md.MD_SCHED_GRID)
+        with pytest.raises(md.MDError):
+            md.md_set_variant(b.h, md.MD_FORCE_PAIRED, md.MD_SCHED_DYNAMIC)
         with pytest.raises(md.MDError):
             md.md_cost_model(b.h, md.MD_COST_SAMPLE)
 
@@ -187,3 +204,38 @@ def test_graph_replay_equals_plain_launches(md, sched):
             assert torch.equal(x, y)
     assert launches[0] == launches[1]
     assert launches[2] > launches[0]  # the gated chain's launches on steps without a rebuild
+
+
+def test_batch_paired_graph_replay_and_variant_switch(md):
+    """Two atoms per thread in a batch: graph replay, timed launches and plain
+    launches on the default stream agree bit for bit over steps with
+    rebuilds; switching a running batch between the layouts rebuilds its
+    lists and keeps it on the same trajectory within the mixed bar."""
+    reps = ensemble(4)
+    out = []
+    for mode in ("graphs", "timing", "default_stream"):
+        st = torch.cuda.default_stream() if mode == "default_stream" else torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            b = md.Batch(reps, precision="mixed", stream=st, force_variant=md.MD_FORCE_PAIRED)
+            md.md_set_timing(b.h, mode == "timing")
+            b.step(30)
+            b.step(20)
+            out.append(b.state())
+            builds = b.stats()["builds"]
+            b.close()
+        assert builds >= 2
+    for other in out[1:]:
+        for x, y in zip(out[0], other):
+            assert torch.equal(x, y)
+    with md.Batch(reps, precision="mixed") as b:
+        b.step(10)
+        md.md_set_variant(b.h, md.MD_FORCE_PAIRED, md.MD_SCHED_GRID)
+        b.step(10)
+        md.md_set_variant(b.h, md.MD_FORCE_FULL, md.MD_SCHED_GRID)
+        b.step(10)
+        ke, pe = b.energies()
+    with md.Batch(reps, precision="mixed") as c:
+        c.step(30)
+        ke2, pe2 = c.energies()
+    for r in range(len(reps)):
+        assert abs(ke[r] + pe[r] - ke2[r] - pe2[r]) < 1e-4 * abs(ke2[r] + pe2[r]), r
