@@ -288,8 +288,8 @@ def run_gpu(args, rank, world, local):
     sched = {"grid": md.MD_SCHED_GRID, "paircount": md.MD_SCHED_PAIRCOUNT,
              "mlp": md.MD_SCHED_MLP, "dynamic": md.MD_SCHED_DYNAMIC}[args.scheduler]
     # the two-atom layout serves one-species Lennard-Jones (batches under the
-    # hardware block scheduler)
-    paired = (args.force_variant == "paired" and kw["potential"] == "lj" and
+    # hardware block scheduler) and Sutton-Chen
+    paired = (args.force_variant == "paired" and kw["potential"] in ("lj", "sc") and
               "species" not in kw and (not ensemble or args.scheduler == "grid"))
     fv = md.MD_FORCE_PAIRED if paired else md.MD_FORCE_FULL
     kw["force_variant"] = fv
@@ -575,6 +575,13 @@ def run_gpu(args, rank, world, local):
         nphi, npsi = len(s.params["phi_r"]), len(s.params["psi_r"])
         flops = 2 * (12.0 * entries) + pairs * (2 + 5 * npsi) + pairs * (2 + 6 * (nphi + npsi) + 7)
         bytes_ = 2 * 4.0 * entries + 250.0 * n
+    elif kw.get("force_variant") == md.MD_FORCE_PAIRED:
+        # Sutton-Chen over two-atom slots: both passes test each union entry
+        # against both atoms (12 flops each) and read the union list, the
+        # slot's first atom and its length
+        entries = st_e["slot_entries"]
+        flops = 2 * (12.0 * 2 * entries) + 10.0 * pairs + 26.0 * pairs
+        bytes_ = 2 * (4.0 * entries + 8.0 * st_e["slots"]) + 250.0 * n
     else:
         flops = 2 * (12.0 * entries) + 10.0 * pairs + 26.0 * pairs
         bytes_ = 2 * 4.0 * entries + 250.0 * n
@@ -606,7 +613,9 @@ def run_gpu(args, rank, world, local):
                        if args.scheduler != "grid" else
                        ("lj_pair_kernel<FM_FUSED_FULL>" if paired else
                         "lj_mixed_kernel<FM_FUSED_FULL>")) if kw["potential"] == "lj" else
-                      ("eam_force_mixed" if kw["potential"] == "eam" else "sc_force_mixed"),
+                      ("eam_force_mixed" if kw["potential"] == "eam" else
+                       ("sc_density_pair + sc_force_pair" if paired else
+                        "sc_density_mixed + sc_force_mixed")),
             "multi_box": ensemble,
             "peak_source": peak_src,
             "algorithmic_bytes_per_launch": bytes_, "algorithmic_flops_per_launch": flops,

@@ -194,11 +194,12 @@ __global__ void pair_reset_kernel(DevStatus *ds, bool gated) {
 }
 
 // the dummy neighbour of the padding entries, past the last atom of both
-// position buffers
-__global__ void pair_dummy_kernel(float4 *xq0, float4 *xq1, int n) {
+// position buffers and of the many-body passes' (x, F') records
+__global__ void pair_dummy_kernel(float4 *xq0, float4 *xq1, float4 *xqf, int n) {
     const float4 far = make_float4(3.0e18f, 3.0e18f, 3.0e18f, 0.f);
     xq0[n] = far;
     xq1[n] = far;
+    if (xqf) xqf[n] = far;
 }
 
 // Measured on GB300 (porous LJ, 9.8 M atoms, one force launch): this form
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(kPairBlock, 9) lj_pair_kernel(ForceArgs a, Pai
 int64_t pair_slots_max(int64_t n, int ncells) { return (n + ncells) / 2 + 1; }
 
 cudaError_t launch_pair_dummy(md_system *h) {
-    pair_dummy_kernel<<<1, 1, 0, h->stream>>>(h->xq[0], h->xq[1], (int)h->n);
+    pair_dummy_kernel<<<1, 1, 0, h->stream>>>(h->xq[0], h->xq[1], h->xqf, (int)h->n);
     return cudaGetLastError();
 }
 

@@ -791,8 +791,11 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
         return fail(nullptr, MD_ERR_INVALID,
                     W + ": the cluster-pair list runs one one-species box under MD_SCHED_GRID, "
                         "n < 2^25");
-    if (p->force_variant != MD_FORCE_FULL && p->potential != MD_POT_LJ)
-        return fail(nullptr, MD_ERR_INVALID, W + ": half lists are built for Lennard-Jones only");
+    if (p->force_variant != MD_FORCE_FULL && p->potential != MD_POT_LJ &&
+        !(p->force_variant == MD_FORCE_PAIRED && p->potential == MD_POT_SC))
+        return fail(nullptr, MD_ERR_INVALID,
+                    W + ": half lists and cluster pairs are built for Lennard-Jones only, two "
+                        "atoms per thread for Lennard-Jones and Sutton-Chen");
     if ((p->force_variant == MD_FORCE_CLUSTER || p->force_variant == MD_FORCE_PAIRED) &&
         p->precision != MD_MIXED)
         return fail(nullptr, MD_ERR_INVALID,
@@ -890,7 +893,8 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
     }
     if (p->potential == MD_POT_SC || p->potential == MD_POT_EAM) {
         A(dalloc(&h->rho, N)); A(dalloc(&h->dF32, N)); A(dalloc(&h->dF64, N));
-        if (p->precision == MD_MIXED) A(dalloc(&h->xqf, N));
+        // one more entry: the far dummy of the slot lists' padding
+        if (p->precision == MD_MIXED) A(dalloc(&h->xqf, N + 1));
     }
     h->nblocks_n = nblocks(n);
     A(dalloc(&h->partials, (size_t)h->nblocks_n + 1)); A(dalloc(&h->red_out, 4));
@@ -1259,8 +1263,10 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
         return fail(h, MD_ERR_INVALID,
                     "md_set_variant: embedded-atom, multi-element and split (inner/outer) "
                     "systems run full lists under MD_SCHED_GRID");
-    if (force_variant != MD_FORCE_FULL && h->p.potential == MD_POT_SC)
-        return fail(h, MD_ERR_INVALID, "md_set_variant: half lists are built for Lennard-Jones only");
+    if (force_variant != MD_FORCE_FULL && force_variant != MD_FORCE_PAIRED &&
+        h->p.potential == MD_POT_SC)
+        return fail(h, MD_ERR_INVALID,
+                    "md_set_variant: half lists and cluster pairs are built for Lennard-Jones only");
     if ((force_variant == MD_FORCE_CLUSTER || force_variant == MD_FORCE_PAIRED) &&
         h->p.precision != MD_MIXED)
         return fail(h, MD_ERR_INVALID,

@@ -127,16 +127,19 @@ def test_lj_liquid_1m(md, orc, liquid_1m, precision):
         check_forces(orc, prm, f, pos, s.box, idx, ooff, oids, 2.5, 2e-4, 1e-5)
 
 
-def test_sutton_chen_8m(md, orc):
-    """128^3-cell Sutton-Chen fcc (8,388,608 atoms), mixed path, two passes."""
+@pytest.mark.parametrize("variant", ["full", "paired"])
+def test_sutton_chen_8m(md, orc, variant):
+    """128^3-cell Sutton-Chen fcc (8,388,608 atoms), mixed path, two passes,
+    with per-atom lists and with two atoms per thread."""
     s = inputs.sc_fcc(nc=128)
     p = s.params
     prm = orc.make_params(potential=orc.POT_SC, eps=p["eps"], sigma=p["sigma"], c=p["c"],
                           n_exp=p["n_exp"], m_exp=p["m_exp"], rc=p["rc"], skin=p["skin"],
                           dt=p["dt"])
+    fv = md.MD_FORCE_PAIRED if variant == "paired" else md.MD_FORCE_FULL
     with md.System(s.pos, s.vel, s.box, potential="sc", precision="mixed", eps=p["eps"],
                    sigma=p["sigma"], c=p["c"], n_exp=p["n_exp"], m_exp=p["m_exp"], rc=p["rc"],
-                   skin=p["skin"], dt=p["dt"]) as a:
+                   skin=p["skin"], dt=p["dt"], force_variant=fv) as a:
         a.step(10)
         pos = perturbed(s.pos, s.box, 0.03, inputs.SEED_BASE + 313)
         f = load(md, a, pos, s.vel)
