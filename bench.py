@@ -88,9 +88,12 @@ def parse_args(argv):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nc", type=int, default=0,
                     help="fcc cells per side (0 = the workload's own size; smaller for profiling)")
-    ap.add_argument("--force-variant", default="paired", choices=["paired", "full"],
-                    help="force layout of the timed Lennard-Jones steps: two atoms per "
-                         "thread (union lists) or one atom per thread (per-atom lists)")
+    ap.add_argument("--force-variant", default="auto", choices=["auto", "paired", "full"],
+                    help="force layout of the timed steps: two atoms per thread (union "
+                         "lists), one atom per thread (per-atom lists), or auto: the "
+                         "measured faster one for the workload's potential (two atoms per "
+                         "thread for Lennard-Jones and Sutton-Chen, per-atom lists for the "
+                         "embedded-atom potential)")
     ap.add_argument("--no-equilibrate", dest="equilibrate", action="store_false",
                     help="porous: time from the generated state instead of the equilibrated one")
     return ap.parse_args(argv)
@@ -287,10 +290,13 @@ def run_gpu(args, rank, world, local):
         args.scheduler = "grid"  # the persistent schedulers drive the Lennard-Jones kernel
     sched = {"grid": md.MD_SCHED_GRID, "paircount": md.MD_SCHED_PAIRCOUNT,
              "mlp": md.MD_SCHED_MLP, "dynamic": md.MD_SCHED_DYNAMIC}[args.scheduler]
-    # the two-atom layout serves one-species Lennard-Jones (batches under the
-    # hardware block scheduler) and Sutton-Chen
-    paired = (args.force_variant == "paired" and kw["potential"] in ("lj", "sc") and
-              "species" not in kw and (not ensemble or args.scheduler == "grid"))
+    # the two-atom layout serves every one-species potential (batches under
+    # the hardware block scheduler); on the embedded-atom workload it was
+    # measured slower, so auto keeps per-atom lists there
+    two_atom_ok = (kw["potential"] in ("lj", "sc", "eam") and "species" not in kw and
+                   (not ensemble or args.scheduler == "grid"))
+    paired = two_atom_ok and (args.force_variant == "paired" or
+                              (args.force_variant == "auto" and kw["potential"] != "eam"))
     fv = md.MD_FORCE_PAIRED if paired else md.MD_FORCE_FULL
     kw["force_variant"] = fv
 
@@ -575,6 +581,13 @@ def run_gpu(args, rank, world, local):
         nphi, npsi = len(s.params["phi_r"]), len(s.params["psi_r"])
         flops = 2 * (12.0 * entries) + pairs * (2 + 5 * npsi) + pairs * (2 + 6 * (nphi + npsi) + 7)
         bytes_ = 2 * 4.0 * entries + 250.0 * n
+        if kw.get("force_variant") == md.MD_FORCE_PAIRED:
+            # over two-atom slots: each union entry tested against both atoms
+            # in both passes, the union list and 8 B per slot read by each
+            entries = st_e["slot_entries"]
+            flops = 2 * (12.0 * 2 * entries) + pairs * (2 + 5 * npsi) + \
+                pairs * (2 + 6 * (nphi + npsi) + 7)
+            bytes_ = 2 * (4.0 * entries + 8.0 * st_e["slots"]) + 250.0 * n
     elif kw.get("force_variant") == md.MD_FORCE_PAIRED:
         # Sutton-Chen over two-atom slots: both passes test each union entry
         # against both atoms (12 flops each) and read the union list, the
@@ -613,7 +626,8 @@ def run_gpu(args, rank, world, local):
                        if args.scheduler != "grid" else
                        ("lj_pair_kernel<FM_FUSED_FULL>" if paired else
                         "lj_mixed_kernel<FM_FUSED_FULL>")) if kw["potential"] == "lj" else
-                      ("eam_force_mixed" if kw["potential"] == "eam" else
+                      (("eam_density_pair + eam_force_pair" if paired else
+                        "eam_density_mixed + eam_force_mixed") if kw["potential"] == "eam" else
                        ("sc_density_pair + sc_force_pair" if paired else
                         "sc_density_mixed + sc_force_mixed")),
             "multi_box": ensemble,

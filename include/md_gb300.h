@@ -67,10 +67,11 @@ enum { MD_FP64 = 0, MD_MIXED = 1 };
  * neighbour position serves two pair evaluations.  The full pair set, the
  * same forces as MD_FORCE_FULL up to float32 rounding.  Its rebuilds make the
  * slot lists only; md_get_neighbors builds per-atom rows on demand from the
- * positions of the last build.  Mixed-precision one-species Lennard-Jones:
- * one box under any scheduler (the persistent kernel then takes tiles of 32
- * slots), or a batch (md_create_batch) under MD_SCHED_GRID, each slot with
- * its box's geometry.  MD_FORCE_CLUSTER is a measured alternative (slower on GB300);
+ * positions of the last build.  Mixed precision, one species: Lennard-Jones
+ * in one box under any scheduler (the persistent kernel then takes tiles of
+ * 32 slots) or in a batch (md_create_batch) under MD_SCHED_GRID, each slot
+ * with its box's geometry; Sutton-Chen and the embedded-atom potential
+ * (both passes over the slots) under MD_SCHED_GRID.  MD_FORCE_CLUSTER is a measured alternative (slower on GB300);
  * MD_FORCE_PAIRED is faster than the per-atom list on large systems. */
 enum { MD_FORCE_FULL = 0, MD_FORCE_HALF_COLOR = 1, MD_FORCE_HALF_ATOMIC = 2,
        MD_FORCE_CLUSTER = 3, MD_FORCE_PAIRED = 4 };

@@ -769,9 +769,11 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
     if (p->potential == MD_POT_EAM) {
         if (eam_table(p, eam, &eam_t, &why) != MD_OK)
             return fail(nullptr, MD_ERR_INVALID, W + ": " + why);
-        if (p->force_variant != MD_FORCE_FULL || p->scheduler != MD_SCHED_GRID)
+        if ((p->force_variant != MD_FORCE_FULL && p->force_variant != MD_FORCE_PAIRED) ||
+            p->scheduler != MD_SCHED_GRID)
             return fail(nullptr, MD_ERR_INVALID,
-                        W + ": the embedded-atom potential runs full lists under MD_SCHED_GRID");
+                        W + ": the embedded-atom potential runs full lists or two atoms per "
+                            "thread under MD_SCHED_GRID");
     } else if (eam) {
         return fail(nullptr, MD_ERR_INVALID, W + ": an EAM table needs MD_POT_EAM");
     }
@@ -791,11 +793,10 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
         return fail(nullptr, MD_ERR_INVALID,
                     W + ": the cluster-pair list runs one one-species box under MD_SCHED_GRID, "
                         "n < 2^25");
-    if (p->force_variant != MD_FORCE_FULL && p->potential != MD_POT_LJ &&
-        !(p->force_variant == MD_FORCE_PAIRED && p->potential == MD_POT_SC))
+    if (p->force_variant != MD_FORCE_FULL && p->force_variant != MD_FORCE_PAIRED &&
+        p->potential != MD_POT_LJ)
         return fail(nullptr, MD_ERR_INVALID,
-                    W + ": half lists and cluster pairs are built for Lennard-Jones only, two "
-                        "atoms per thread for Lennard-Jones and Sutton-Chen");
+                    W + ": half lists and cluster pairs are built for Lennard-Jones only");
     if ((p->force_variant == MD_FORCE_CLUSTER || p->force_variant == MD_FORCE_PAIRED) &&
         p->precision != MD_MIXED)
         return fail(nullptr, MD_ERR_INVALID,
@@ -1258,13 +1259,19 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
     if (force_variant < MD_FORCE_FULL || force_variant > MD_FORCE_PAIRED ||
         scheduler < MD_SCHED_GRID || scheduler > MD_SCHED_DYNAMIC)
         return fail(h, MD_ERR_INVALID, "md_set_variant: unknown variant or scheduler");
-    if ((h->p.potential == MD_POT_EAM || h->fc.ntypes > 0 || h->ov_on) &&
+    if ((h->fc.ntypes > 0 || h->ov_on) &&
         (force_variant != MD_FORCE_FULL || scheduler != MD_SCHED_GRID))
         return fail(h, MD_ERR_INVALID,
-                    "md_set_variant: embedded-atom, multi-element and split (inner/outer) "
-                    "systems run full lists under MD_SCHED_GRID");
+                    "md_set_variant: multi-element and split (inner/outer) systems run full "
+                    "lists under MD_SCHED_GRID");
+    if (h->p.potential == MD_POT_EAM &&
+        ((force_variant != MD_FORCE_FULL && force_variant != MD_FORCE_PAIRED) ||
+         scheduler != MD_SCHED_GRID))
+        return fail(h, MD_ERR_INVALID,
+                    "md_set_variant: the embedded-atom potential runs full lists or two atoms "
+                    "per thread under MD_SCHED_GRID");
     if (force_variant != MD_FORCE_FULL && force_variant != MD_FORCE_PAIRED &&
-        h->p.potential == MD_POT_SC)
+        h->p.potential != MD_POT_LJ)
         return fail(h, MD_ERR_INVALID,
                     "md_set_variant: half lists and cluster pairs are built for Lennard-Jones only");
     if ((force_variant == MD_FORCE_CLUSTER || force_variant == MD_FORCE_PAIRED) &&

@@ -63,16 +63,26 @@ def check_forces(f, f0, precision):
     assert np.all(err <= tol), (precision, int((err > tol).sum()), float(np.max(err / np.maximum(fn, rms))))
 
 
+# (precision, layout): the float64 path with per-atom lists; the mixed path
+# with per-atom lists and with two atoms per thread (union lists of slots)
+MODES = [("fp64", "full"), ("mixed", "full"), ("mixed", "paired")]
+
+
+def variant(md, layout):
+    return md.MD_FORCE_PAIRED if layout == "paired" else md.MD_FORCE_FULL
+
+
 @pytest.mark.parametrize("table", ["fe_like", "two_psi_pieces"])
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_eam_lists_density_forces_energy(md, orc, precision, table):
+@pytest.mark.parametrize("precision,layout", MODES)
+def test_eam_lists_density_forces_energy(md, orc, precision, layout, table):
     p = P if table == "fe_like" else P2
     t_orc, t_md = tables(orc, md, p)
     s, pos = system()
     rl = p["rc"] + p["skin"]
     off, ids = orc.neighbors_cells(pos, s.box, rl)
     U0, f0, rho0, dF0, e0 = orc.eam_list(pos, s.box, off, ids, t_orc, p["rc"])
-    with md.System(pos, s.vel, s.box, precision=precision, eam=t_md, **kw(p)) as sy:
+    with md.System(pos, s.vel, s.box, precision=precision, eam=t_md,
+                   force_variant=variant(md, layout), **kw(p)) as sy:
         goff, gids = sy.neighbors()
         f = sy.state()[2].cpu().numpy()
         rho = torch.empty(s.n, dtype=torch.float64, device="cuda")
@@ -97,8 +107,8 @@ def test_eam_lists_density_forces_energy(md, orc, precision, table):
     assert abs(ke - 0.5 * np.sum(s.vel ** 2)) <= 1e-12 * ke
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_eam_nve_100_steps(md, orc, precision):
+@pytest.mark.parametrize("precision,layout", MODES)
+def test_eam_nve_100_steps(md, orc, precision, layout):
     """Fe-like bcc, 8^3 cells at T* = 0.018 (dt 0.002): total energy after
     every one of 100 steps within 1e-6 relative of the oracle's float64
     trajectory."""
@@ -107,18 +117,21 @@ def test_eam_nve_100_steps(md, orc, precision):
     prm = orc.make_params(potential=orc.POT_EAM, rc=P["rc"], skin=P["skin"], dt=P["dt"],
                           eam=t_orc)
     E0 = orc.md_run(prm, s.pos, s.vel, s.box, 100)["energies"]
-    with md.System(s.pos, s.vel, s.box, precision=precision, eam=t_md, **kw(P)) as sy:
+    with md.System(s.pos, s.vel, s.box, precision=precision, eam=t_md,
+                   force_variant=variant(md, layout), **kw(P)) as sy:
         es = [sy.energy()]
         for _ in range(100):
             sy.step(1)
             es.append(sy.energy())
     es = np.array(es)
     rel = np.abs(es[:, 0] + es[:, 1] - E0[:, 2]) / np.abs(E0[:, 2])
-    print("EAM %s: max relative total-energy error over 100 steps %.3g" % (precision, rel.max()))
+    print("EAM %s %s: max relative total-energy error over 100 steps %.3g"
+          % (precision, layout, rel.max()))
     assert rel.max() < 1e-6, rel.max()
 
 
-def test_eam_steps_with_rebuilds_against_the_oracle(md, orc):
+@pytest.mark.parametrize("layout", ["full", "paired"])
+def test_eam_steps_with_rebuilds_against_the_oracle(md, orc, layout):
     """A hotter bcc box (T* 0.2) rebuilds its list several times in 300
     mixed-precision steps; the energy stays on the oracle's trajectory and
     the graph-replayed run on a side stream equals the plain one bit for bit."""
@@ -132,7 +145,7 @@ def test_eam_steps_with_rebuilds_against_the_oracle(md, orc):
         ctx = torch.cuda.stream(stream) if stream is not None else torch.cuda.stream(
             torch.cuda.default_stream())
         with ctx, md.System(s.pos, s.vel, s.box, precision="mixed", eam=t_md, stream=stream,
-                            **kw(P2)) as sy:
+                            force_variant=variant(md, layout), **kw(P2)) as sy:
             b0 = sy.stats()["builds"]
             sy.step(300)
             builds = sy.stats()["builds"] - b0

@@ -148,17 +148,20 @@ def test_sutton_chen_8m(md, orc, variant):
     check_forces(orc, prm, f, pos, s.box, idx, ooff, oids, p["rc"], 2e-4, 1e-5)
 
 
-def test_eam_fe126_4m(md, orc):
+@pytest.mark.parametrize("variant", ["full", "paired"])
+def test_eam_fe126_4m(md, orc, variant):
     """126^3-cell bcc under the piecewise embedded-atom potential (4,000,752
-    atoms, the size of the paper's Fe126), mixed path, both passes."""
+    atoms, the size of the paper's Fe126), mixed path, both passes, with
+    per-atom lists and with two atoms per thread."""
     s = inputs.eam_bcc(nc=126)
     p = s.params
     keys = ("phi_r", "phi_a", "psi_r", "psi_a", "F_sqrt", "F_quad")
     t_orc = orc.make_eam(*[p[k] for k in keys])
     prm = orc.make_params(potential=orc.POT_EAM, rc=p["rc"], skin=p["skin"], dt=p["dt"],
                           eam=t_orc)
+    fv = md.MD_FORCE_PAIRED if variant == "paired" else md.MD_FORCE_FULL
     with md.System(s.pos, s.vel, s.box, precision="mixed", eam=md.make_eam(*[p[k] for k in keys]),
-                   rc=p["rc"], skin=p["skin"], dt=p["dt"], mass=p["mass"]) as a:
+                   rc=p["rc"], skin=p["skin"], dt=p["dt"], mass=p["mass"], force_variant=fv) as a:
         assert a.n == 4000752
         a.step(10)
         pos = perturbed(s.pos, s.box, 0.04, inputs.SEED_BASE + 314)
