@@ -485,29 +485,13 @@ __global__ void __launch_bounds__(kEamPairBlock, 8) eam_force_pair(ForceArgs a, 
 
 }  // namespace
 
-// the slot tables and union lists of MD_FORCE_PAIRED
-static PairArgs eam_pair_args(const md_system *h) {
-    PairArgs p;
-    p.slot_start = h->ps_start;
-    p.slot_atom = h->ps_atom;
-    p.list = h->ps_list;
-    p.count = h->ps_count;
-    p.cap = h->ps_cap;
-    p.ncells = h->g.ncells;
-    return p;
-}
-
-static int eam_pair_blocks(const md_system *h) {
-    return (int)((pair_slots_max(h->n, h->g.ncells) + kEamPairBlock - 1) / kEamPairBlock);
-}
-
 cudaError_t launch_eam_density(md_system *h) {
     ForceArgs a = make_force_args(h);
     const int nb = nblocks(a.n);
     const EamTab &t = h->eam;
     if (h->p.force_variant == MD_FORCE_PAIRED) {
-        const PairArgs p = eam_pair_args(h);
-        const int pb = eam_pair_blocks(h);
+        const PairArgs p = make_pair_args(h);
+        const int pb = pair_grid_blocks(h, kEamPairBlock);
         if (t.npsi == 1) eam_density_pair<1><<<pb, kEamPairBlock, 0, h->stream>>>(a, p, t);
         else eam_density_pair<0><<<pb, kEamPairBlock, 0, h->stream>>>(a, p, t);
         return cudaGetLastError();
@@ -528,8 +512,8 @@ cudaError_t launch_eam_force(md_system *h, int mode, bool energy, bool store_f) 
     const EamTab &t = h->eam;
     cudaStream_t s = h->stream;
     if (h->p.force_variant == MD_FORCE_PAIRED) {
-        const PairArgs p = eam_pair_args(h);
-        const int pb = eam_pair_blocks(h);
+        const PairArgs p = make_pair_args(h);
+        const int pb = pair_grid_blocks(h, kEamPairBlock);
         const bool fe = (t.nphi == 7 && t.npsi == 1);
 #define MDG_EAMP(M, E)                                                                  \
     do {                                                                                \

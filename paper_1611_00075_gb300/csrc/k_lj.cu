@@ -719,15 +719,7 @@ cudaError_t launch_lj_persist(md_system *h, int mode, bool store_f, bool dynamic
     sa.cell_cycles = h->cell_cycles;
     sa.cta_cycles = h->cta_cycles;
     sa.rounds = h->sched_rounds;
-    PairArgs pa{};
-    if (paired) {
-        pa.slot_start = h->ps_start;
-        pa.slot_atom = h->ps_atom;
-        pa.list = h->ps_list;
-        pa.count = h->ps_count;
-        pa.cap = h->ps_cap;
-        pa.ncells = h->g.ncells;
-    }
+    const PairArgs pa = paired ? make_pair_args(h) : PairArgs{};
     const int G = h->sched_ctas;
     const int sf = store_f ? 1 : 0;
     cudaStream_t s = h->stream;

@@ -292,16 +292,9 @@ cudaError_t launch_pair_build(md_system *h, bool write, bool gated) {
 
 cudaError_t launch_pair_forces(md_system *h, int mode, bool energy, bool store_f) {
     ForceArgs a = make_force_args(h);
-    PairArgs p;
-    p.slot_start = h->ps_start;
-    p.slot_atom = h->ps_atom;
-    p.list = h->ps_list;
-    p.count = h->ps_count;
-    p.cap = h->ps_cap;
-    p.ncells = h->g.ncells;
+    const PairArgs p = make_pair_args(h);
     const int sf = store_f ? 1 : 0;
-    const int64_t smax = pair_slots_max(h->n, h->g.ncells);
-    const int blocks = (int)((smax + kPairBlock - 1) / kPairBlock);
+    const int blocks = pair_grid_blocks(h, kPairBlock);
     const bool multi = h->R > 1;
     cudaStream_t s = h->stream;
 #define MDG_PAIR(M)                                                                         \

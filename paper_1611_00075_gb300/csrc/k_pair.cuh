@@ -18,6 +18,23 @@ struct PairArgs {
     int cap, ncells;
 };
 
+// The slot tables and union lists of a handle, for the kernels.
+inline PairArgs make_pair_args(const md_system *h) {
+    PairArgs p;
+    p.slot_start = h->ps_start;
+    p.slot_atom = h->ps_atom;
+    p.list = h->ps_list;
+    p.count = h->ps_count;
+    p.cap = h->ps_cap;
+    p.ncells = h->g.ncells;
+    return p;
+}
+
+// Blocks of `block` threads that cover every slot a binning can make.
+inline int pair_grid_blocks(const md_system *h, int block) {
+    return (int)((pair_slots_max(h->n, h->g.ncells) + block - 1) / block);
+}
+
 // Lennard-Jones pair term in float32 for the pair vector e = x_j - x_i:
 // f_i -= fs * e; with ENERGY the shifted pair energy is added to `en`.
 template <bool ENERGY>

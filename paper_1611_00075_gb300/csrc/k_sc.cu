@@ -543,29 +543,13 @@ __global__ void __launch_bounds__(kScPairBlock, 7) sc_force_pair(ForceArgs a, Pa
 
 }  // namespace
 
-// the slot tables and union lists of MD_FORCE_PAIRED
-static PairArgs pair_args(const md_system *h) {
-    PairArgs p;
-    p.slot_start = h->ps_start;
-    p.slot_atom = h->ps_atom;
-    p.list = h->ps_list;
-    p.count = h->ps_count;
-    p.cap = h->ps_cap;
-    p.ncells = h->g.ncells;
-    return p;
-}
-
-static int pair_blocks(const md_system *h) {
-    return (int)((pair_slots_max(h->n, h->g.ncells) + kScPairBlock - 1) / kScPairBlock);
-}
-
 cudaError_t launch_sc_density(md_system *h) {
     ForceArgs a = make_force_args(h);
     const int nb = nblocks(a.n);
     if (h->p.force_variant == MD_FORCE_PAIRED) {
-        const PairArgs p = pair_args(h);
-        if (a.fc.sc_m == 6) sc_density_pair<6><<<pair_blocks(h), kScPairBlock, 0, h->stream>>>(a, p);
-        else sc_density_pair<0><<<pair_blocks(h), kScPairBlock, 0, h->stream>>>(a, p);
+        const PairArgs p = make_pair_args(h);
+        if (a.fc.sc_m == 6) sc_density_pair<6><<<pair_grid_blocks(h, kScPairBlock), kScPairBlock, 0, h->stream>>>(a, p);
+        else sc_density_pair<0><<<pair_grid_blocks(h, kScPairBlock), kScPairBlock, 0, h->stream>>>(a, p);
         return cudaGetLastError();
     }
     if (h->p.precision == MD_MIXED) {
@@ -583,8 +567,8 @@ cudaError_t launch_sc_force(md_system *h, int mode, bool energy, bool store_f) {
     const int sf = store_f ? 1 : 0;
     cudaStream_t s = h->stream;
     if (h->p.force_variant == MD_FORCE_PAIRED) {
-        const PairArgs p = pair_args(h);
-        const int pb = pair_blocks(h);
+        const PairArgs p = make_pair_args(h);
+        const int pb = pair_grid_blocks(h, kScPairBlock);
         const bool cu = (a.fc.sc_n == 9 && a.fc.sc_m == 6);
 #define MDG_SCP(M, E)                                                                   \
     do {                                                                                \
