@@ -46,7 +46,7 @@ FORCE_SOURCES = ("paper_1611_00075_gb300/csrc/k_lj.cu", "paper_1611_00075_gb300/
                  "paper_1611_00075_gb300/csrc/k_pair.cuh")
 PROFILED_TRAFFIC = {
     # kernel: (sources sha1[:16], DRAM bytes per atom, capture)
-    "lj_mixed_persist_paired": ("cd90cc720f1ca226", 365.8,
+    "lj_mixed_persist_paired": ("766f90ca9261abed", 365.8,
                                 "ncu --set full, porous 80^3 cells (1,223,941 atoms) equilibrated "
                                 "as the bench's input, two atoms per thread, one FM_FUSED_FULL "
                                 "launch of the timed range"),
