@@ -293,7 +293,7 @@ def run_gpu(args, rank, world, local):
     # the two-atom layout serves every one-species potential (batches under
     # the hardware block scheduler); on the embedded-atom workload it was
     # measured slower, so auto keeps per-atom lists there
-    two_atom_ok = (kw["potential"] in ("lj", "sc", "eam") and "species" not in kw and
+    two_atom_ok = (kw["potential"] in ("lj", "sc", "eam") and
                    (not ensemble or args.scheduler == "grid"))
     paired = two_atom_ok and (args.force_variant == "paired" or
                               (args.force_variant == "auto" and kw["potential"] != "eam"))
@@ -620,7 +620,8 @@ def run_gpu(args, rank, world, local):
             "frac": (ach_gbs / hbm_peak) if hbm_bound else (ach_flops / fp32_peak),
             "traffic": traffic,
             "traffic_note": traffic_note,
-            "kernel": ("lj_typed_kernel<FM_FUSED_FULL>" if "species" in kw else
+            "kernel": (("lj_typed_pair_kernel<FM_FUSED_FULL>" if paired else
+                        "lj_typed_kernel<FM_FUSED_FULL>") if "species" in kw else
                        ("lj_mixed_persist<FM_FUSED_FULL, two-atom slots> (%s)" if paired else
                         "lj_mixed_persist<FM_FUSED_FULL> (%s)") % args.scheduler
                        if args.scheduler != "grid" else

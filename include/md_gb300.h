@@ -67,11 +67,12 @@ enum { MD_FP64 = 0, MD_MIXED = 1 };
  * neighbour position serves two pair evaluations.  The full pair set, the
  * same forces as MD_FORCE_FULL up to float32 rounding.  Its rebuilds make the
  * slot lists only; md_get_neighbors builds per-atom rows on demand from the
- * positions of the last build.  Mixed precision, one species: Lennard-Jones
+ * positions of the last build.  Mixed precision: one-species Lennard-Jones
  * in one box under any scheduler (the persistent kernel then takes tiles of
  * 32 slots) or in a batch (md_create_batch) under MD_SCHED_GRID, each slot
- * with its box's geometry; Sutton-Chen and the embedded-atom potential
- * (both passes over the slots) under MD_SCHED_GRID.  MD_FORCE_CLUSTER is a measured alternative (slower on GB300);
+ * with its box's geometry; multi-element Lennard-Jones (md_create_typed),
+ * Sutton-Chen and the embedded-atom potential (both passes over the slots)
+ * under MD_SCHED_GRID.  MD_FORCE_CLUSTER is a measured alternative (slower on GB300);
  * MD_FORCE_PAIRED is faster than the per-atom list on large systems. */
 enum { MD_FORCE_FULL = 0, MD_FORCE_HALF_COLOR = 1, MD_FORCE_HALF_ATOMIC = 2,
        MD_FORCE_CLUSTER = 3, MD_FORCE_PAIRED = 4 };
@@ -172,7 +173,9 @@ typedef struct {
 /* md_create for a multi-element Lennard-Jones system: p->potential must be
  * MD_POT_LJ; types_host (copied) holds the species parameters and type_dev
  * (device, n int32 in original order, 0 <= t < ntypes) each atom's species.
- * Full lists under MD_SCHED_GRID, fp64 or mixed precision.  The species
+ * Full lists under MD_SCHED_GRID, fp64 or mixed precision, or two atoms per
+ * thread (MD_FORCE_PAIRED, mixed precision; a slot's atoms may be of two
+ * species, each lane of the pair arithmetic with its own parameters).  The species
  * travels with the atom through binning (two spare bits above the original
  * id in its float32 position word), so the pair loop reads j's species from
  * the position it loads anyway and selects the pair's parameters from the

@@ -290,7 +290,11 @@ cudaError_t launch_pair_build(md_system *h, bool write, bool gated) {
     return cudaGetLastError();
 }
 
+// the multi-element variant (k_pair_typed.cu)
+cudaError_t launch_pair_typed_forces(md_system *h, int mode, bool energy, bool store_f);
+
 cudaError_t launch_pair_forces(md_system *h, int mode, bool energy, bool store_f) {
+    if (h->fc.ntypes > 0) return launch_pair_typed_forces(h, mode, energy, store_f);
     ForceArgs a = make_force_args(h);
     const PairArgs p = make_pair_args(h);
     const int sf = store_f ? 1 : 0;

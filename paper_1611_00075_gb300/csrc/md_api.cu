@@ -782,12 +782,12 @@ static md_status create_impl(md_system **out, const md_params *p, int R, const i
     if (ltypes) {
         if (type_tables(p, ltypes, type_dev, n, &type_t, &types_h, &why) != MD_OK)
             return fail(nullptr, MD_ERR_INVALID, W + ": " + why);
-        if (R != 1 || p->force_variant != MD_FORCE_FULL || p->scheduler != MD_SCHED_GRID)
+        if (R != 1 || (p->force_variant != MD_FORCE_FULL && p->force_variant != MD_FORCE_PAIRED) ||
+            p->scheduler != MD_SCHED_GRID)
             return fail(nullptr, MD_ERR_INVALID,
-                        W + ": multi-element systems run full lists under MD_SCHED_GRID");
+                        W + ": multi-element systems run one box, full lists or two atoms per "
+                            "thread, under MD_SCHED_GRID");
     }
-    if (p->force_variant == MD_FORCE_PAIRED && ltypes)
-        return fail(nullptr, MD_ERR_INVALID, W + ": two atoms per thread run one species");
     if (p->force_variant == MD_FORCE_CLUSTER &&
         (R != 1 || p->scheduler != MD_SCHED_GRID || ltypes || n >= ((int64_t)1 << 25)))
         return fail(nullptr, MD_ERR_INVALID,
@@ -1259,11 +1259,15 @@ md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler)
     if (force_variant < MD_FORCE_FULL || force_variant > MD_FORCE_PAIRED ||
         scheduler < MD_SCHED_GRID || scheduler > MD_SCHED_DYNAMIC)
         return fail(h, MD_ERR_INVALID, "md_set_variant: unknown variant or scheduler");
-    if ((h->fc.ntypes > 0 || h->ov_on) &&
-        (force_variant != MD_FORCE_FULL || scheduler != MD_SCHED_GRID))
+    if (h->ov_on && (force_variant != MD_FORCE_FULL || scheduler != MD_SCHED_GRID))
         return fail(h, MD_ERR_INVALID,
-                    "md_set_variant: multi-element and split (inner/outer) systems run full "
-                    "lists under MD_SCHED_GRID");
+                    "md_set_variant: split (inner/outer) systems run full lists under "
+                    "MD_SCHED_GRID");
+    if (h->fc.ntypes > 0 && ((force_variant != MD_FORCE_FULL && force_variant != MD_FORCE_PAIRED) ||
+                             scheduler != MD_SCHED_GRID))
+        return fail(h, MD_ERR_INVALID,
+                    "md_set_variant: multi-element systems run full lists or two atoms per "
+                    "thread under MD_SCHED_GRID");
     if (h->p.potential == MD_POT_EAM &&
         ((force_variant != MD_FORCE_FULL && force_variant != MD_FORCE_PAIRED) ||
          scheduler != MD_SCHED_GRID))

@@ -171,17 +171,20 @@ def test_eam_fe126_4m(md, orc, variant):
     check_forces(orc, prm, f, pos, s.box, idx, ooff, oids, p["rc"], 2e-4, 1e-5)
 
 
-def test_alloy_4_6m(md, orc):
+@pytest.mark.parametrize("variant", ["full", "paired"])
+def test_alloy_4_6m(md, orc, variant):
     """The Cu-Au-like random alloy on 105^3 fcc cells (4,630,500 atoms, the
-    paper's Alloy size), mixed path with species parameters and masses."""
+    paper's Alloy size), mixed path with species parameters and masses, with
+    per-atom lists and with two atoms per thread."""
     s = inputs.lj_alloy(nc=105)
     p = s.params
     sp = (p["types"], p["t_eps"], p["t_sigma"], p["t_mass"])
     prm = orc.make_params(potential=orc.POT_LJ, rc=p["rc"], skin=p["skin"], dt=p["dt"],
                           types=p["types"], t_eps=p["t_eps"], t_sigma=p["t_sigma"],
                           t_mass=p["t_mass"])
+    fv = md.MD_FORCE_PAIRED if variant == "paired" else md.MD_FORCE_FULL
     with md.System(s.pos, s.vel, s.box, precision="mixed", species=sp, rc=p["rc"],
-                   skin=p["skin"], dt=p["dt"]) as a:
+                   skin=p["skin"], dt=p["dt"], force_variant=fv) as a:
         assert a.n == 4630500
         a.step(10)
         pos = perturbed(s.pos, s.box, 0.04, inputs.SEED_BASE + 315)

@@ -56,12 +56,23 @@ def near_cutoff(pos, box, off, ids, rc, delta):
     return bad
 
 
+# (precision, layout): the float64 path with per-atom lists; the mixed path
+# with per-atom lists and with two atoms per thread (a slot's two atoms may
+# be of different species)
+MODES = [("fp64", "full"), ("mixed", "full"), ("mixed", "paired")]
+
+
+def variant(md, layout):
+    return md.MD_FORCE_PAIRED if layout == "paired" else md.MD_FORCE_FULL
+
+
 @pytest.mark.parametrize("which", ["alloy", "layer"])
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_typed_cells_lists_forces_energy(md, orc, which, precision):
+@pytest.mark.parametrize("precision,layout", MODES)
+def test_typed_cells_lists_forces_energy(md, orc, which, precision, layout):
     s, pos = system(which)
     types, te, ts, tm = species(s)
-    with md.System(pos, s.vel, s.box, precision=precision, species=species(s), **kw(s)) as sy:
+    with md.System(pos, s.vel, s.box, precision=precision, species=species(s),
+                   force_variant=variant(md, layout), **kw(s)) as sy:
         nc, cell_of, start = sy.cells()
         off, ids = sy.neighbors()
         f = sy.state()[2].cpu().numpy()
@@ -90,8 +101,8 @@ def test_typed_cells_lists_forces_energy(md, orc, which, precision):
     assert abs(ke - ke0) <= 1e-12 * ke0
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_typed_nve_100_steps(md, orc, precision):
+@pytest.mark.parametrize("precision,layout", MODES)
+def test_typed_nve_100_steps(md, orc, precision, layout):
     """A 6^3-cell random alloy at T* 0.3 (dt 0.002): total energy after every
     one of 100 steps within 1e-6 relative of the oracle's trajectory, with
     the species' masses in both integrators."""
@@ -100,14 +111,16 @@ def test_typed_nve_100_steps(md, orc, precision):
     prm = orc.make_params(potential=orc.POT_LJ, rc=2.5, skin=0.3, dt=s.params["dt"], types=types,
                           t_eps=te, t_sigma=ts, t_mass=tm)
     E0 = orc.md_run(prm, s.pos, s.vel, s.box, 100)["energies"]
-    with md.System(s.pos, s.vel, s.box, precision=precision, species=species(s), **kw(s)) as sy:
+    with md.System(s.pos, s.vel, s.box, precision=precision, species=species(s),
+                   force_variant=variant(md, layout), **kw(s)) as sy:
         es = [sy.energy()]
         for _ in range(100):
             sy.step(1)
             es.append(sy.energy())
     es = np.array(es)
     rel = np.abs(es[:, 0] + es[:, 1] - E0[:, 2]) / np.abs(E0[:, 2])
-    print("alloy %s: max relative total-energy error over 100 steps %.3g" % (precision, rel.max()))
+    print("alloy %s %s: max relative total-energy error over 100 steps %.3g"
+          % (precision, layout, rel.max()))
     assert rel.max() < 1e-6, rel.max()
 
 
@@ -151,6 +164,11 @@ def test_typed_rejects_bad_input(md):
     with md.System(s.pos, s.vel, s.box, species=species(s), **kw(s)) as sy:
         with pytest.raises(md.MDError):
             md.md_set_variant(sy.h, md.MD_FORCE_HALF_COLOR, md.MD_SCHED_GRID)
+        with pytest.raises(md.MDError):  # two atoms per thread: the grid launch only
+            md.md_set_variant(sy.h, md.MD_FORCE_PAIRED, md.MD_SCHED_MLP)
+        md.md_set_variant(sy.h, md.MD_FORCE_PAIRED, md.MD_SCHED_GRID)
+        sy.step(3)
+        md.md_set_variant(sy.h, md.MD_FORCE_FULL, md.MD_SCHED_GRID)
         with pytest.raises(md.MDError):
             md.md_cost_model(sy.h, md.MD_COST_SAMPLE)
         sy.step(3)
