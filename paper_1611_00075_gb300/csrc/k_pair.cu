@@ -98,8 +98,9 @@ __device__ __forceinline__ int scan_cell(int cnt, int b, int e, const float4 *__
 // |e|^2 + |u|^2 - 2 |e.u|, so the test is |e|^2 - 2 |e.u| < hi - |u|^2 (one
 // difference vector and two dot products instead of two distances).  In
 // float32 the terms stay below about 16 sigma^2, so the rounding error of
-// this form is below 1e-5 sigma^2 against the 2^-14 r_list^2 (5e-4 sigma^2)
-// margin of hi: the list stays a superset of both atoms' r_list spheres.
+// this form is about 1e-5 sigma^2 at most, against the 2^-14 r_list^2
+// (5e-4 sigma^2) margin of hi: the list stays a superset of both atoms'
+// r_list spheres.
 // Only the home cell holds i0 and i1, so only its scan excludes them.
 //
 // Measured on GB300 (porous LJ, 9.8 M atoms, 300 steps from the generated
