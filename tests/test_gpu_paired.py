@@ -422,3 +422,43 @@ def test_sutton_chen_steps_track_the_oracle(md, orc, variant):
     print("Sutton-Chen %s: max relative total-energy error over 50 steps %.3g"
           % (variant, rel.max()))
     assert rel.max() < 1e-6, rel.max()
+
+
+@pytest.mark.parametrize("layout", ["full", "paired"])
+@pytest.mark.parametrize("exps", [(12, 6), (12, 7)])
+def test_sutton_chen_other_exponents(md, orc, exps, layout):
+    """Sutton-Chen exponents other than (9, 6) take the kernels' run-time
+    power path: (12, 6) with both exponents even (no square root), (12, 7)
+    with an odd m.  rho, forces and energy against the oracle with the mixed
+    bars, for per-atom lists and for two atoms per thread."""
+    from cutoff_bounds import sc_straddle_bound
+    n_exp, m_exp = exps
+    s = inputs.sc_fcc(nc=8, n_exp=float(n_exp), m_exp=float(m_exp))
+    pos = np.mod(s.pos + 0.03 * inputs.gaussian(2000 + n_exp + m_exp, s.pos.size)
+                 .reshape(-1, 3), s.box)
+    p = s.params
+    off, ids = orc.neighbors_cells(pos, s.box, p["rc"] + p["skin"])
+    U0, f0, rho0, _ = orc.sc_list(pos, s.box, off, ids, c=p["c"], n_exp=float(n_exp),
+                                  m_exp=float(m_exp))
+    bad = near_cutoff(pos, s.box, off, ids, p["rc"], 1e-5)
+    fv = md.MD_FORCE_PAIRED if layout == "paired" else md.MD_FORCE_FULL
+    with md.System(pos, s.vel, s.box, precision="mixed", force_variant=fv, **sc_kw(s)) as sy:
+        f = sy.state()[2].cpu().numpy()
+        rho = torch.empty(s.n, dtype=torch.float64, device="cuda")
+        md.md_get_density(sy.h, rho, None)
+        ke, pe = sy.energy()
+    ok = ~bad
+    np.testing.assert_allclose(rho.cpu().numpy()[ok], rho0[ok], rtol=2e-6)
+    fn = np.linalg.norm(f0, axis=1)
+    rms = math.sqrt(np.mean(fn * fn))
+    err = np.linalg.norm(f - f0, axis=1)
+    tol = 2e-4 * fn + 1e-5 * max(1.0, rms)
+    assert np.all((err <= tol) | bad), int(((err > tol) & ~bad).sum())
+    slack = sc_straddle_bound(orc, pos, s.box, off, ids, 1e-5, c=p["c"], n_exp=float(n_exp),
+                              m_exp=float(m_exp))
+    # with a0 = 1 and c = 39.432 these exponents make the pair and embedding
+    # energies (about 400 and 460 per atom) nearly cancel: the float32 pair
+    # terms' rounding is held relative to the terms, not to their difference
+    emb = p["eps"] * p["c"] * np.sum(np.sqrt(rho0))
+    scale = abs(U0 + emb) + emb
+    assert abs(pe - U0) <= 2e-6 * scale + slack, (pe, U0, scale, slack)
