@@ -289,10 +289,13 @@ md_status md_get_atom_energy(md_system *h, double *e_dev);
  * when switching between full and half lists, the cell partition for the
  * static schedulers).  Half lists (Newton's third law, each pair once, owned
  * by the lower original id) are built for one-species Lennard-Jones on
- * either path; the cluster and two-atom layouts for its mixed path; the
- * persistent schedulers drive the full-list Lennard-Jones pass of either
- * precision and the two-atom pass, and every other combination runs one
- * thread per atom (per slot, per i-cluster). */
+ * either path and the cluster layout for its mixed path; the two-atom layout
+ * serves the mixed path of every potential (multi-element Lennard-Jones,
+ * Sutton-Chen and the embedded-atom potential, and batches, under
+ * MD_SCHED_GRID); the persistent schedulers drive the one-box, one-species
+ * full-list Lennard-Jones pass of either precision and its two-atom pass,
+ * and every other combination runs one thread per atom (per slot, per
+ * i-cluster). */
 md_status md_set_variant(md_system *h, int32_t force_variant, int32_t scheduler);
 
 /* Colour of every cell of an ncell_host[0] x [1] x [2] grid (each >= 3) as
